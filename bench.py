@@ -1,0 +1,296 @@
+"""Benchmark: noisy shots per second of batched multi-shot simulation with
+shot-branching on one GB300, through the libsv C ABI.
+
+Workload (default): 16-qubit random-SU(4) circuit, depth 16, 2-qubit
+depolarizing p=1e-2 and amplitude damping gamma=5e-3 (Kraus) after every
+gate, final measurement of all qubits, 10^4 shots, batch-shots with
+shot-branching, complex64 amplitudes with float64-grade accumulation.
+
+A step is one whole run of the circuit for all shots (reset, every gate,
+noise sample, fork, and the final sample of every shot).  Steps are timed
+one by one with CUDA events on the stream the library launches on, with an
+L2 flush (a 512 MB write) between them, outside the timed events.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "noisy shots/sec at 10–28 qubits, batched FP32 vs plain FP64; % HBM roofline"
+
+
+def workload(name):
+    from paper_2308_03399_gb300 import workloads as W
+    if name == "cfg2":
+        return W.config2(), 10_000, 2
+    if name == "cfg1":
+        return W.config1(), 1000, 1
+    if name == "cfg3":
+        return W.config3(), 10_000, 3
+    if name == "cfg5":
+        return W.config5(), 2000, 5
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(circ, seed, budget_s=15.0):
+    """The oracle as it stands, on the host's cores, on a bounded sample of
+    the workload's shots (shots are independent, so shots/s scales)."""
+    from oracle import oracle as O
+    oc = O.OracleCircuit(circ)
+    threads = O.max_threads()
+    n = max(threads, 8)
+    t0 = time.perf_counter()
+    O.run_shots(oc, seed, 0, n, threads, want_outcomes=False)
+    dt = time.perf_counter() - t0
+    # grow the sample to about budget_s of work
+    n2 = int(max(n, min(20 * n, n * budget_s / max(dt, 1e-3))))
+    if n2 > n:
+        t0 = time.perf_counter()
+        O.run_shots(oc, seed, 0, n2, threads, want_outcomes=False)
+        dt = time.perf_counter() - t0
+        n = n2
+    return {"value": n / dt, "unit": "shots/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} shots of the same circuit (oracle float64, OpenMP over shots), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    circ, n_shots, seed = workload(args.workload)
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    oc = O.OracleCircuit(circ)
+    threads = O.max_threads()
+    per_step = max(threads, args.ref_shots)
+    for _ in range(args.warmup):
+        O.run_shots(oc, seed, 0, min(per_step, threads), threads, want_outcomes=False)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        O.run_shots(oc, seed, i * per_step, per_step, threads, want_outcomes=False)
+    dt = time.perf_counter() - t0
+    v = per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "shots/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": circ.name, "n_qubits": circ.n_qubits,
+                                            "shots_per_step": per_step, "full_shots": n_shots},
+            "cpu_baseline": {"value": v, "unit": "shots/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} shots per step (of {n_shots}), float64 oracle"},
+            "e2e": {"value": v, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2")
+    ap.add_argument("--mode", default="branch", choices=["branch", "batch", "plain"])
+    ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-shots", type=int, default=32)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2308_03399_gb300 import sv
+
+    circ, n_shots, seed = workload(args.workload)
+    seed = seed + 1000 * rank  # replicas: every rank its own independent shots
+    mode = {"branch": sv.SV_BRANCH, "batch": sv.SV_BATCH, "plain": sv.SV_PLAIN}[args.mode]
+    prec = {"c64": sv.SV_C64, "c128": sv.SV_C128}[args.prec]
+    arrays = circ.to_arrays()
+    cs = sv.circuit_struct(arrays)
+    stream = torch.cuda.current_stream()
+    b = sv.Batch(circ.n_qubits, n_shots, max(1, circ.n_clbits), prec, mode, seed, stream=stream.cuda_stream)
+    use_graph = mode != sv.SV_PLAIN
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        b.run_circuit(cs, use_graph=use_graph)
+    torch.cuda.synchronize()
+    b.stats()
+
+    # ---- timed region: K steps, device time per step ------------------------
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms = []
+    for _ in range(args.steps):
+        flush_buf.fill_(1)  # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run_circuit(cs, use_graph=use_graph)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    st = b.stats()
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n_shots * world * args.steps / (total_ms / 1e3)
+    launches_per_step = st["launches"] / args.steps
+
+    # ---- end to end through the public API with host buffers -----------------
+    b.set_option(sv.SV_OPT_UPLOAD, 1)
+    b.stats()
+    keys = np.zeros(n_shots, np.uint64)
+    e2e_ms = []
+    for _ in range(max(2, args.steps)):
+        flush_buf.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run_circuit(cs, use_graph=use_graph)
+        keys = b.get_keys()  # device -> host read of the step's result
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    st_e2e = b.stats()
+    h2d = st_e2e["h2d_bytes"] / len(e2e_ms)
+    e2e_value = n_shots * world / (float(np.mean(e2e_ms)) / 1e3)
+    b.set_option(sv.SV_OPT_UPLOAD, 0)
+
+    # ---- roofline of the dominant kernel (k_pass), events per launch ---------
+    b.set_option(sv.SV_OPT_PROFILE, 1)
+    b.stats()
+    b.profile()
+    prof_steps = 2
+    for _ in range(prof_steps):
+        flush_buf.fill_(1)
+        b.run_circuit(cs, use_graph=False)
+    prof = b.profile()
+    stp = b.stats()
+    b.set_option(sv.SV_OPT_PROFILE, 0)
+    pass_ms, n_pass = prof["pass"]
+    hbm_peak, peak_kind = peaks()
+    achieved = stp["pass_bytes"] / (pass_ms / 1e3) / 1e9 if pass_ms > 0 else 0.0
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "pass_traffic.json")
+    if os.path.exists(tfile):
+        traffic = json.load(open(tfile)).get(f"{args.workload}:{args.mode}:{args.prec}")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64" if prec == sv.SV_C64 else "c128",
+        "data": "synthetic",
+        "config": {"workload": circ.name, "n_qubits": circ.n_qubits, "depth_ops": circ.n_ops, "shots": n_shots,
+                   "mode": args.mode, "precision": args.prec, "seed": seed, "l2": "flushed between steps (512 MB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "e2e": {"value": e2e_value, "unit": "shots/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(keys.nbytes)},
+        "roofline": {"bound": "hbm", "kernel": "k_pass", "achieved": achieved, "peak": hbm_peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                     "algorithmic_bytes_per_step": stp["pass_bytes"] / prof_steps,
+                     "pass_ms_per_step": pass_ms / prof_steps, "pass_launches_per_step": n_pass / prof_steps,
+                     "share_of_step": pass_ms / max(prof["total"][0], 1e-9)},
+        "profile_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()},
+        "branches_at_end": st["live_branches"],
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(circ, seed)
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

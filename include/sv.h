@@ -1,0 +1,221 @@
+/*
+ * sv.h -- C ABI of libsv: batched multi-shot state-vector simulation of
+ * noisy quantum circuits on one GPU (sm_103a).
+ *
+ * The method (Doi, Horii, Wood, "Efficient techniques to GPU Accelerations of
+ * Multi-Shot Quantum Computing Simulations", arXiv 2308.03399):
+ *   - many shots advance through one circuit in the same kernel launches
+ *     (Section IV-A-1), each with its own classical register and parameter
+ *     buffers (Section IV-A-2);
+ *   - every shot samples its own Pauli noise (Section IV-A-3), Kraus noise
+ *     (Section IV-A-4) and measurement outcomes (Section IV-A-5) on the GPU,
+ *     with no host synchronisation inside a circuit;
+ *   - shot-branching (Section IV-B) keeps one state for all shots that have
+ *     drawn the same outcomes and forks a copy only where they diverge; a
+ *     branch that finds no free memory parks its shots on a waiting list,
+ *     which is re-simulated from |0...0> once the live branches finish.
+ *
+ * Conventions
+ *   - Qubit q is bit q of the amplitude index (little-endian).
+ *   - A k-qubit matrix on qubits[0..k-1] maps bit j of its row/column index
+ *     to qubits[j]; it is row-major complex float64 with re/im interleaved.
+ *   - Every op of a circuit has an ordinal `op`; the shot s draws for op
+ *     from Philox4x32-10 with key (seed lo, seed hi) and counter
+ *     (s lo, s hi, op, 0), u = top 53 bits of the first two words * 2^-53.
+ *     A random op chooses the first entry whose cumulative probability
+ *     exceeds u (Table I); u at or above the last cumulative value takes the
+ *     last entry with nonzero probability.
+ *
+ * Ownership and ordering
+ *   - The library allocates and owns all device memory of a batch (inside
+ *     sv_alloc_batch / sv_run_circuit) and frees it in sv_free_batch.
+ *   - Host pointers passed in are read (or written) only during the call.
+ *   - Work is issued on the batch's CUDA stream in call order; calls that
+ *     return host data (sv_counts, sv_get_*) synchronise that stream.
+ *   - A batch is used by one host thread at a time.
+ *
+ * Errors
+ *   - Every call returns sv_status; nothing crosses the ABI as an exception.
+ *   - sv_last_error() returns a thread-local message for the last failure.
+ *   - Device-side problems (an index out of range, a bounded wait that ran
+ *     out) are recorded in a device error word and reported as SV_EINTERNAL
+ *     or SV_ETIMEOUT by the next synchronising call.
+ */
+#ifndef SV_H
+#define SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sv_batch_s *sv_batch;
+
+typedef enum {
+    SV_OK = 0,
+    SV_EINVAL = 1,       /* bad argument (qubit out of range, non-unitary gate, ...) */
+    SV_ENOMEM = 2,       /* device memory exhausted or budget too small */
+    SV_ECUDA = 3,        /* a CUDA runtime call failed */
+    SV_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
+    SV_EUNSUPPORTED = 5, /* valid but not supported by this build (size limits) */
+    SV_EINTERNAL = 6     /* the device error word was set */
+} sv_status;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_prec;
+
+/* SV_PLAIN:        one state per shot, shots one after another, one launch
+ *                  per op, host reads probabilities back for every Kraus and
+ *                  measurement choice (the conventional form the paper's
+ *                  Section V-B calls "GPU: Base").
+ * SV_BATCH:        one state per shot, every shot in every launch (Section IV-A).
+ * SV_BRANCH:       shot-branching (Section IV-B); the live branches are the
+ *                  batch of every launch (Section VI's combination).
+ * SV_BATCH_BRANCH: same as SV_BRANCH (kept as its own name for callers).   */
+typedef enum { SV_PLAIN = 0, SV_BATCH = 1, SV_BRANCH = 2, SV_BATCH_BRANCH = 3 } sv_mode;
+
+typedef enum { SV_NOISE_PAULI = 0, SV_NOISE_KRAUS = 1 } sv_noise_kind;
+
+/* Op kinds of a flattened circuit (sv_circuit.kind). */
+enum { SV_OP_GATE = 0, SV_OP_PAULI = 1, SV_OP_KRAUS = 2, SV_OP_MEASURE = 3, SV_OP_FINAL = 4 };
+
+/* A flattened circuit as struct-of-arrays (all host pointers, n_ops long
+ * unless stated).  Op i acts on qubits[q_off[i] .. q_off[i]+nq[i]).
+ *   GATE:    data[d_off[i] ..] one 2^k x 2^k matrix; cond_clbit[i] >= 0 makes
+ *            it conditional on classical bit cond_clbit[i] == cond_val[i].
+ *   PAULI:   n_terms[i] cumulative probabilities at data[d_off[i] ..] and
+ *            n_terms[i]*nq[i] characters from "IXYZ" at paulis[s_off[i] ..],
+ *            character j acting on qubits[q_off[i]+j] (Table I form).
+ *   KRAUS:   n_terms[i] matrices of 2^k x 2^k at data[d_off[i] ..].
+ *   MEASURE: nq[i] qubits into classical bits clbits[cl_off[i] ..]; reset[i]
+ *            != 0 returns the measured qubits to |0>.
+ *   FINAL:   sample every qubit; the sampled index is the count key.      */
+typedef struct {
+    int32_t n_qubits, n_clbits, n_ops;
+    const int32_t *kind, *nq, *q_off, *cl_off, *n_terms, *s_off, *cond_clbit, *cond_val, *reset;
+    const int64_t *d_off;
+    const int32_t *qubits, *clbits;
+    const double *data;
+    const uint8_t *paulis;
+} sv_circuit;
+
+/* Batch options (sv_set_option). */
+typedef enum {
+    SV_OPT_LOG = 0,         /* 1: record per-shot outcomes, thresholds and fork events */
+    SV_OPT_TILE_BITS = 1,   /* amplitudes per CTA tile = 2^value (0 = default)          */
+    SV_OPT_MAX_ACTIVE = 2,  /* most distinct qubits fused into one pass (0 = default)   */
+    SV_OPT_MAX_STAGES = 3,  /* most ops fused into one pass (0 = default)               */
+    SV_OPT_THREADS = 4,     /* threads per CTA of the pass kernel (0 = default)         */
+    SV_OPT_GRID = 5,        /* CTAs of the persistent kernels (0 = default)             */
+    SV_OPT_PROFILE = 6,     /* 1: time every launch class with CUDA events              */
+    SV_OPT_SLOT_LIMIT = 7,  /* cap on state slots (0 = as many as fit); forces waiting  */
+    SV_OPT_UPLOAD = 8       /* 1: sv_run_circuit copies the circuit's constants to the
+                               device on every call, even when its graph is cached   */
+} sv_option;
+
+/* Allocate a batch of n_shots shots of an n_qubits register.
+ *   mode            see sv_mode; SV_BATCH needs one state per shot
+ *   seed            Philox key
+ *   mem_budget      bytes of device memory for states (0 = all free memory
+ *                   less a reserve); SV_BRANCH admits forks against it
+ *   cuda_stream     cudaStream_t to run on, or NULL for a private stream
+ * Returns SV_EINVAL for n_qubits outside 1..30, n_shots == 0 or
+ * n_clbits > 64, SV_ENOMEM when not even one state fits.                  */
+sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec prec, sv_mode mode,
+                         uint64_t seed, uint64_t mem_budget, void *cuda_stream, sv_batch *out);
+
+sv_status sv_free_batch(sv_batch b);
+
+sv_status sv_set_option(sv_batch b, sv_option opt, int64_t value);
+
+/* Section IV-A-1: apply one k-qubit gate (k <= 3) to every live state.
+ * mat is host, 2^k x 2^k complex float64.  cond_clbit = -1 for an
+ * unconditional gate; otherwise shots whose classical bit cond_clbit differs
+ * from cond_value are left alone (Section IV-A-5).  SV_EINVAL for repeated or
+ * out-of-range qubits or a matrix that is not unitary within 1e-10.        */
+sv_status sv_apply_gate_batch(sv_batch b, int k, const int *qubits, const double *mat, int cond_clbit,
+                              int cond_value);
+
+/* Sections III-B and IV-A-3/4: every shot samples one term of a noise model
+ * with its own draw for ordinal `op`.
+ *   PAULI: n_terms cumulative probabilities (cum_probs) and n_terms*k chars
+ *          of "IXYZ" (paulis), k <= 4, n_terms <= 64.
+ *   KRAUS: n_terms matrices of 2^k x 2^k (kraus), k <= 2, n_terms <= 16;
+ *          term i is chosen with probability ||K_i psi||^2 and applied as
+ *          K_i psi / ||K_i psi||.  SV_EINVAL if sum K^dagger K != I
+ *          within 1e-10.
+ * In SV_BRANCH modes shots of one branch that choose different terms fork
+ * the branch (Section IV-B-2).                                             */
+sv_status sv_sample_noise(sv_batch b, uint32_t op, sv_noise_kind kind, int k, const int *qubits, int n_terms,
+                          const double *cum_probs, const char *paulis, const double *kraus);
+
+/* Section IV-A-5: measure m <= 4 qubits of every shot into classical bits
+ * clbits[0..m-1] (bit i of the outcome is qubits[i]); reset != 0 returns
+ * the measured qubits to |0>.                                              */
+sv_status sv_measure_batch(sv_batch b, uint32_t op, int m, const int *qubits, const int *clbits, int reset);
+
+/* Section IV-B-2: commit the forks of random op `op`.  The sampling calls
+ * already commit their forks, so this only checks that `op` was the last
+ * random op sampled and returns SV_OK; it exists so that callers written
+ * against a sample-then-branch sequence keep working.                       */
+sv_status sv_branch(sv_batch b, uint32_t op);
+
+/* Section IV-B-2 / Section I: sample every qubit of every live shot with
+ * draw ordinal op_final (one sample per shot from its branch's state) and
+ * return the histogram of sampled indices: keys[0..*n_out) ascending with
+ * counts[]. cap bounds both host arrays; SV_EINVAL if too small.  Shots on
+ * the waiting list are not counted (see sv_waiting).  Synchronises.          */
+sv_status sv_counts(sv_batch b, uint32_t op_final, uint64_t *keys, uint64_t *counts, uint64_t cap,
+                    uint64_t *n_out);
+
+/* Per-shot final keys of the last sv_counts / sv_run_circuit (host array of
+ * n_shots).  Synchronises.                                                  */
+sv_status sv_get_keys(sv_batch b, uint64_t *keys);
+
+/* Shots currently parked on the waiting list (Section IV-B-2). */
+sv_status sv_waiting(sv_batch b, uint64_t *n_waiting);
+
+/* Run a whole circuit for all shots (Sections IV-A and IV-B), restarting
+ * the waiting list until it is empty, and leave per-shot keys for
+ * sv_get_keys.  use_graph != 0 captures the launch sequence into a CUDA
+ * graph once per circuit and replays it.                                    */
+sv_status sv_run_circuit(sv_batch b, const sv_circuit *c, int use_graph);
+
+/* Test / introspection ---------------------------------------------------- */
+
+/* State of the branch that holds `shot`, as 2*len float64 (re, im); len
+ * must be 2^n.  Synchronises.                                               */
+sv_status sv_get_amplitudes(sv_batch b, uint64_t shot, double *out_re_im, uint64_t len);
+
+/* With SV_OPT_LOG: per-shot choice for random op `op` (-1 if the shot did not
+ * reach it) and, if thresholds is non-NULL, 2 float64 per shot: the
+ * cumulative values just below and at the choice.  Synchronises.            */
+sv_status sv_get_outcomes(sv_batch b, uint32_t op, int32_t *per_shot_outcome, double *thresholds);
+
+/* With SV_OPT_LOG: fork events, 5 int64 each: (op, parent branch, child
+ * branch or -1 for the waiting list, outcome, shots).  A parent's own
+ * continuing group is reported with child == parent.  Synchronises.         */
+sv_status sv_get_fork_events(sv_batch b, int64_t *events, uint64_t cap, uint64_t *n_out);
+
+/* Live branches and run statistics since the previous call.  stats (8
+ * doubles): live branches, waiting shots, kernel launches issued, passes,
+ * algorithmic bytes of the pass kernels (each live state read once, and
+ * written once when the pass applies ops), bytes of fork copies, waiting-
+ * list restarts, bytes copied host to device.  Synchronises.               */
+sv_status sv_stats(sv_batch b, double *stats);
+
+/* With SV_OPT_PROFILE: milliseconds spent per launch class (8 doubles:
+ * pass, decide, alloc, copy, final, init, other, total) and launch counts
+ * (8 int64), accumulated since the last call.  Synchronises.                */
+sv_status sv_profile(sv_batch b, double *ms, int64_t *launches);
+
+/* Wait for the batch's stream, at most timeout_ns (0 = no limit). */
+sv_status sv_sync(sv_batch b, uint64_t timeout_ns);
+
+const char *sv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_H */

@@ -1,0 +1,149 @@
+// Internal descriptors shared by the host runtime (sv_runtime.cu) and the
+// kernels (sv_kernels.cu).  Everything a kernel needs travels by value in
+// its parameters, so a launch sequence can be captured into a CUDA graph
+// unchanged.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sv {
+
+constexpr int MAX_TILE_BITS = 12;  // amplitudes of one CTA tile <= 2^12
+constexpr int MAX_STAGES = 40;     // ops fused into one pass
+constexpr int MAX_PEND = 16;       // random ops whose per-branch choice is applied in one pass
+constexpr int MAX_TERMS = 64;      // terms of one random op (Pauli strings)
+constexpr int MAX_RED = 16;        // probabilities reduced by one pass (Kraus terms, 2^m outcomes)
+constexpr int MAX_CHUNKS = 1024;   // reduction partials per state
+constexpr int MAX_STAGE_Q = 4;     // qubits of one stage
+constexpr int MAT_SMEM = 1024;     // complex matrix entries staged in shared memory per pass
+
+// Stage kinds: what one fused op does to a group of 2^k amplitudes.
+enum : int32_t {
+    ST_DENSE = 0,     // shared dense matrix (a gate)
+    ST_DENSE_BR = 1,  // per-branch matrix: term table[sel] * scale (a chosen Kraus matrix)
+    ST_PAULI_BR = 2,  // per-branch Pauli string from its 4 parameters (Section IV-A-3)
+    ST_PROJ_BR = 3    // per-branch projection onto the measured outcome, optional reset
+};
+enum : int32_t { RED_NONE = 0, RED_FORMS = 1, RED_BINS = 2 };
+enum : int32_t { DEC_PAULI = 0, DEC_KRAUS = 1, DEC_MEASURE = 2 };
+
+// error word codes
+enum : int32_t { ERR_NONE = 0, ERR_SLOT = 1, ERR_INDEX = 2, ERR_GROUPS = 3, ERR_TIMEOUT = 4 };
+
+struct Stage {
+    int32_t kind;
+    int32_t k;
+    int32_t pos[MAX_STAGE_Q];  // tile-local bit of stage qubit j (op order)
+    int32_t cond_clbit;        // -1: unconditional
+    int32_t cond_val;
+    int32_t pend;              // pending-choice column (per-branch kinds)
+    int32_t reset;             // ST_PROJ_BR
+    int32_t off;               // pool offset (real units) / ipool offset (ST_PAULI_BR)
+    int32_t stride;            // real units between terms (ST_DENSE_BR)
+    int32_t mat;               // offset of this stage's matrix in the shared-memory matrix area
+};
+
+struct PassDesc {
+    int32_t n;                 // qubits
+    int32_t tb;                // tile bits
+    int32_t run_bits;          // tile-local bits [0, run_bits) are global qubits [0, run_bits)
+    int32_t tile_q[MAX_TILE_BITS];
+    int32_t n_nontile;
+    int32_t nontile_q[32];
+    int32_t chunks;            // reduction chunks per state
+    int32_t tiles_per_chunk;
+    int32_t n_stages;
+    int32_t store;             // write the tile back
+    int32_t mat_elems;         // complex entries of the shared-memory matrix area
+    int32_t red_kind, red_k, red_R, red_off;
+    int32_t red_pos[MAX_STAGE_Q];
+    Stage st[MAX_STAGES];
+};
+
+struct DecideDesc {
+    uint32_t op;
+    int32_t kind;              // DEC_*
+    int32_t R;                 // terms / outcomes
+    int32_t pend;
+    int32_t chunks;            // partials to sum
+    int32_t fork;              // shot-branching on
+    int32_t m;                 // measured qubits
+    int32_t clbit[MAX_STAGE_Q];
+    int32_t* log_sel;          // per shot id, nullable
+    double* log_thr;           // 2 per shot id, nullable
+    double cum[MAX_TERMS];     // Pauli cumulative table
+};
+
+struct FinalDesc {
+    uint32_t op;
+    int32_t chunks;
+    int32_t* log_sel;
+    double* log_thr;
+};
+
+// Device state of a batch (pointers into library-owned device memory).
+struct DevBatch {
+    void* states;              // n_slots * dim amplitudes
+    int64_t dim;
+    int32_t n;
+    int32_t n_slots;
+    int32_t cap_br;            // branch ids per run (= shots)
+    uint64_t seed;
+    int32_t* ctl;              // control words, see CTL_*
+    int32_t* br_slot;
+    int32_t* br_start;
+    int32_t* br_count;
+    uint64_t* br_clbits;
+    int32_t* br_parent;
+    int32_t* br_sel;           // [MAX_PEND][cap_br]
+    double* br_scale;          // [MAX_PEND][cap_br]
+    uint32_t* perm;            // shot ids, grouped by branch
+    uint32_t* perm_tmp;
+    int32_t* shot_sel;         // per perm position
+    int32_t* grp_n;            // per branch: groups after the last decide
+    int32_t* grp_sel;          // [cap_br][MAX_TERMS]
+    int32_t* grp_start;
+    int32_t* grp_cnt;
+    double* grp_scale;
+    uint64_t* grp_clbits;
+    int32_t* free_slots;
+    uint32_t* wait_shots;
+    double* partials;          // [n_slots][max_chunks][MAX_RED]
+    int32_t max_chunks;
+    const void* pool;          // real-typed constants (matrices, forms)
+    const int32_t* ipool;      // integer constants (Pauli parameters)
+    uint64_t* keys;            // per shot id
+    int64_t* fork_log;         // 5 per event, nullable
+    int32_t fork_log_cap;
+    int32_t* pass_log;         // live branches seen by each pass (profiling), nullable
+    int32_t pass_log_cap;
+};
+
+// control words (ctl[])
+enum : int32_t {
+    CTL_NBR = 0,        // live branches
+    CTL_NFREE = 1,      // free slots
+    CTL_NWAIT = 2,      // shots on the waiting list
+    CTL_COPY_FIRST = 3, // first branch created by the last alloc
+    CTL_COPY_END = 4,
+    CTL_ERR = 5,        // error word
+    CTL_ERR_INFO = 6,
+    CTL_NFORK = 7,      // fork events logged
+    CTL_NPASS = 8,      // passes logged
+    CTL_NCOPIED = 9,    // branches created by forks (each one state copy)
+    CTL_WORDS = 16
+};
+
+// launchers (sv_kernels.cu)
+cudaError_t launch_init(const DevBatch& d, int prec, int n_init_slots, int grid, cudaStream_t s);
+cudaError_t launch_reset(const DevBatch& d, int mode_branch, int n_shots_run, int from_wait, int grid,
+                         cudaStream_t s);
+cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s);
+cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int grid, cudaStream_t s);
+cudaError_t launch_alloc(const DevBatch& d, uint32_t op, int pend, cudaStream_t s);
+cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s);
+cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s);
+size_t pass_smem_bytes(int prec, const PassDesc& p, int threads);
+cudaError_t init_kernels();
+
+}  // namespace sv

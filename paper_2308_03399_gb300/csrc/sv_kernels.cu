@@ -1,0 +1,970 @@
+// CUDA kernels of libsv (sm_103a).
+//
+// Data layout in HBM: states are stored one after another (Section IV-A-2),
+// one slot of 2^n amplitudes per live state, complex64 (float2) or
+// complex128 (double2).  A live state is a *branch*: the shots that have drawn
+// the same outcomes so far share it (Section IV-B); in batch mode every shot
+// is its own branch.  Shot ids are kept grouped by branch in `perm`.
+//
+// Kernels
+//   k_pass          one read + (optional) write of every live state, applying
+//                   a fused sequence of ops (gates; each branch's chosen
+//                   Pauli string, Kraus matrix or measurement projection) in
+//                   shared memory, then reducing the probabilities the next
+//                   random op needs.  Persistent over (branch, chunk) items.
+//   k_decide        per branch: sum the reduced probabilities in a fixed
+//                   order (float64), draw every shot's Philox number, choose
+//                   its outcome, and partition the branch's shots by outcome.
+//   k_alloc         one CTA: give every new outcome group a branch id and a
+//                   free slot, in branch order, or park its shots on the
+//                   waiting list when no slot is left.
+//   k_copy          copy parent states into the new branches' slots.
+//   k_final_*       sampling of all qubits from each branch (sampling measure).
+//
+// Reductions are deterministic: every (branch, chunk) partial is produced by
+// one CTA in a fixed order, so a branch's result does not depend on how many
+// other branches run beside it.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+template <class R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
+template <class T> __device__ __forceinline__ T cmul(T a, T b) {
+    T r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <class T> __device__ __forceinline__ void cfma(T& acc, T a, T b) {
+    acc.x += a.x * b.x - a.y * b.y;
+    acc.y += a.x * b.y + a.y * b.x;
+}
+
+// Accumulators.  complex128 states sum in float64.  complex64 states sum in
+// float-float (an unevaluated pair hi + lo updated with Knuth's TwoSum), which
+// carries about 48 bits of precision using only float32 arithmetic; the
+// squares of float32 amplitudes are formed in float32 and summed this way.
+template <class R> struct Acc;
+template <> struct Acc<double> {
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<float> {
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
+    __device__ __forceinline__ void add(float x) {
+        float s = __fadd_rn(hi, x);
+        float bp = __fsub_rn(s, hi);
+        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies with the published multipliers and Weyl key increments.
+// key = (seed lo, seed hi), counter = (shot lo, shot hi, op, 0).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, uint32_t op) {
+    uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+    uint32_t w0 = (uint32_t)shot, w1 = (uint32_t)(shot >> 32), w2 = op, w3 = 0u;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t a_hi = __umulhi(0xD2511F53u, w0), a_lo = 0xD2511F53u * w0;
+        const uint32_t b_hi = __umulhi(0xCD9E8D57u, w2), b_lo = 0xCD9E8D57u * w2;
+        const uint32_t n0 = b_hi ^ w1 ^ key0;
+        const uint32_t n2 = a_hi ^ w3 ^ key1;
+        w0 = n0;
+        w1 = b_lo;
+        w2 = n2;
+        w3 = a_lo;
+        key0 += 0x9E3779B9u;
+        key1 += 0xBB67AE85u;
+    }
+    const uint64_t top53 = ((((uint64_t)w0) << 32) | (uint64_t)w1) >> 11;
+    return (double)top53 * 0x1.0p-53;
+}
+
+// first t with u < cum[t]; past the end, the last t with nonzero probability
+__device__ __forceinline__ int select_cum(double u, const double* cum, int R) {
+    for (int t = 0; t < R; ++t)
+        if (u < cum[t]) return t;
+    for (int t = R - 1; t >= 0; --t) {
+        const double prev = t ? cum[t - 1] : 0.0;
+        if (cum[t] > prev) return t;
+    }
+    return R - 1;
+}
+
+__device__ __forceinline__ void set_err(const DevBatch& d, int code, int info) {
+    if (atomicCAS(&d.ctl[CTL_ERR], 0, code) == 0) d.ctl[CTL_ERR_INFO] = info;
+}
+
+// insert a zero bit at each of the K ascending positions sp[]
+template <int K> __device__ __forceinline__ int insert_zeros(int g, const int* sp) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int p = sp[j];
+        g = ((g >> p) << (p + 1)) | (g & ((1 << p) - 1));
+    }
+    return g;
+}
+
+template <int K> __device__ __forceinline__ void sorted_pos(const int32_t* pos, int* sp) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) sp[j] = pos[j];
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int j = 0; j + 1 < K - i; ++j)
+            if (sp[j] > sp[j + 1]) {
+                const int t = sp[j];
+                sp[j] = sp[j + 1];
+                sp[j + 1] = t;
+            }
+}
+
+// ---------------------------------------------------------------------------
+// stage application on a shared-memory tile of 2^tb amplitudes.  Each thread
+// takes whole groups (the 2^k amplitudes that differ only in the stage's
+// qubits), so threads never touch each other's amplitudes within a stage.
+// ---------------------------------------------------------------------------
+template <int K> struct GroupIdx {
+    int sp[K];
+    int off[1 << K];
+    __device__ __forceinline__ GroupIdx(const int32_t* pos) {
+        sorted_pos<K>(pos, sp);
+#pragma unroll
+        for (int r = 0; r < (1 << K); ++r) {
+            int o = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if ((r >> j) & 1) o |= 1 << pos[j];
+            off[r] = o;
+        }
+    }
+};
+
+// dense 2^K x 2^K matrix (staged in shared memory, already scaled)
+template <class R, int K>
+__device__ __noinline__ void stage_dense(typename Cplx<R>::T* tile, int tb, const int32_t* pos,
+                                         const typename Cplx<R>::T* M) {
+    using T = typename Cplx<R>::T;
+    constexpr int D = 1 << K;
+    const GroupIdx<K> gi(pos);
+    const int groups = 1 << (tb - K);
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+        const int base = insert_zeros<K>(g, gi.sp);
+        T v[D];
+#pragma unroll
+        for (int r = 0; r < D; ++r) v[r] = tile[base | gi.off[r]];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            T acc;
+            acc.x = 0;
+            acc.y = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) cfma(acc, M[r * D + c], v[c]);
+            tile[base | gi.off[r]] = acc;
+        }
+    }
+}
+
+// Pauli string from its parameters (Section IV-A-3): bit flips x, phase
+// flips z, number of Y; out[d] = (-i)^ny (-1)^popcount(z & d) in[d ^ x].
+template <class R, int K>
+__device__ __noinline__ void stage_pauli(typename Cplx<R>::T* tile, int tb, const int32_t* pos, int packed) {
+    using T = typename Cplx<R>::T;
+    constexpr int D = 1 << K;
+    const GroupIdx<K> gi(pos);
+    const int xm = packed & 15, zm = (packed >> 4) & 15, ny = (packed >> 8) & 3;
+    int offx = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        if ((xm >> j) & 1) offx |= 1 << pos[j];
+    T ph;
+    ph.x = (ny == 0) ? (R)1 : (ny == 2 ? (R)-1 : (R)0);
+    ph.y = (ny == 1) ? (R)-1 : (ny == 3 ? (R)1 : (R)0);
+    const int groups = 1 << (tb - K);
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+        const int base = insert_zeros<K>(g, gi.sp);
+        T w[D];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            T t = cmul(ph, tile[base | (gi.off[r] ^ offx)]);
+            if (__popc(zm & r) & 1) {
+                t.x = -t.x;
+                t.y = -t.y;
+            }
+            w[r] = t;
+        }
+#pragma unroll
+        for (int r = 0; r < D; ++r) tile[base | gi.off[r]] = w[r];
+    }
+}
+
+// projection onto measured outcome sel, scaled by 1/sqrt(P(sel)); with reset
+// the kept amplitudes move to the all-zero outcome (Section IV-A-5)
+template <class R, int K>
+__device__ __noinline__ void stage_proj(typename Cplx<R>::T* tile, int tb, const int32_t* pos, int sel, double scale,
+                                        int reset) {
+    using T = typename Cplx<R>::T;
+    constexpr int D = 1 << K;
+    const GroupIdx<K> gi(pos);
+    int offsel = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        if ((sel >> j) & 1) offsel |= 1 << pos[j];
+    const int keep = reset ? 0 : sel;
+    const R sc = (R)scale;
+    const int groups = 1 << (tb - K);
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+        const int base = insert_zeros<K>(g, gi.sp);
+        T t = tile[base | offsel];
+        t.x *= sc;
+        t.y *= sc;
+        T z;
+        z.x = 0;
+        z.y = 0;
+#pragma unroll
+        for (int r = 0; r < D; ++r) tile[base | gi.off[r]] = (r == keep) ? t : z;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void stage_dispatch(typename Cplx<R>::T* tile, int tb, const Stage& st,
+                                               const typename Cplx<R>::T* M, int sel, double scale, int packed) {
+    if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
+        if (st.k == 1) stage_dense<R, 1>(tile, tb, st.pos, M);
+        else if (st.k == 2) stage_dense<R, 2>(tile, tb, st.pos, M);
+        else stage_dense<R, 3>(tile, tb, st.pos, M);
+    } else if (st.kind == ST_PAULI_BR) {
+        if (st.k == 1) stage_pauli<R, 1>(tile, tb, st.pos, packed);
+        else if (st.k == 2) stage_pauli<R, 2>(tile, tb, st.pos, packed);
+        else if (st.k == 3) stage_pauli<R, 3>(tile, tb, st.pos, packed);
+        else stage_pauli<R, 4>(tile, tb, st.pos, packed);
+    } else {
+        if (st.k == 1) stage_proj<R, 1>(tile, tb, st.pos, sel, scale, st.reset);
+        else if (st.k == 2) stage_proj<R, 2>(tile, tb, st.pos, sel, scale, st.reset);
+        else if (st.k == 3) stage_proj<R, 3>(tile, tb, st.pos, sel, scale, st.reset);
+        else stage_proj<R, 4>(tile, tb, st.pos, sel, scale, st.reset);
+    }
+}
+
+// Per-thread accumulators live in shared memory (acc[r * blockDim + tid]):
+// float-float pairs for complex64 states, float64 for complex128.
+template <class R> struct AccSlot;
+template <> struct AccSlot<float> { using T = float2; };
+template <> struct AccSlot<double> { using T = double; };
+
+__device__ __forceinline__ void acc_add(float2* a, float x) {
+    Acc<float> t;
+    t.hi = a->x;
+    t.lo = a->y;
+    t.add(x);
+    a->x = t.hi;
+    a->y = t.lo;
+}
+__device__ __forceinline__ void acc_add(double* a, double x) { *a += x; }
+__device__ __forceinline__ double acc_get(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ double acc_get(double a) { return a; }
+
+// Kraus probabilities: quadratic forms v^dagger F_i v over groups of the
+// Kraus qubits, F_i = K_i^dagger K_i (Section III-B-2 / IV-A-4)
+template <class R, int K>
+__device__ __noinline__ void reduce_forms(const typename Cplx<R>::T* tile, int tb, const int32_t* pos, int Rn,
+                                          const typename Cplx<R>::T* F, typename AccSlot<R>::T* acc) {
+    using T = typename Cplx<R>::T;
+    constexpr int D = 1 << K;
+    const GroupIdx<K> gi(pos);
+    const int groups = 1 << (tb - K);
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+        const int base = insert_zeros<K>(g, gi.sp);
+        T v[D];
+#pragma unroll
+        for (int r = 0; r < D; ++r) v[r] = tile[base | gi.off[r]];
+        for (int f = 0; f < Rn; ++f) {
+            const T* Ff = F + f * D * D;
+            R q = 0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                T fa;
+                fa.x = 0;
+                fa.y = 0;
+#pragma unroll
+                for (int c = 0; c < D; ++c) cfma(fa, Ff[a * D + c], v[c]);
+                q += v[a].x * fa.x + v[a].y * fa.y;  // Re(conj(v_a) (F v)_a)
+            }
+            acc_add(&acc[f * blockDim.x + threadIdx.x], q);
+        }
+    }
+}
+
+// measurement probabilities of the 2^K outcomes of the measured qubits
+// (Section IV-A-5): bin r collects |psi_j|^2 of indices whose measured bits
+// spell r
+template <class R, int K>
+__device__ __noinline__ void reduce_bins(const typename Cplx<R>::T* tile, int tb, const int32_t* pos,
+                                         typename AccSlot<R>::T* acc) {
+    using T = typename Cplx<R>::T;
+    constexpr int D = 1 << K;
+    const GroupIdx<K> gi(pos);
+    const int groups = 1 << (tb - K);
+    typename AccSlot<R>::T a[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) a[r] = acc[r * blockDim.x + threadIdx.x];
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+        const int base = insert_zeros<K>(g, gi.sp);
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            const T v = tile[base | gi.off[r]];
+            acc_add(&a[r], v.x * v.x + v.y * v.y);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r) acc[r * blockDim.x + threadIdx.x] = a[r];
+}
+
+template <class R>
+__device__ __forceinline__ void reduce_dispatch(const typename Cplx<R>::T* tile, int tb, const PassDesc& p,
+                                                const typename Cplx<R>::T* F, typename AccSlot<R>::T* acc) {
+    if (p.red_kind == RED_BINS) {
+        if (p.red_k == 1) reduce_bins<R, 1>(tile, tb, p.red_pos, acc);
+        else if (p.red_k == 2) reduce_bins<R, 2>(tile, tb, p.red_pos, acc);
+        else if (p.red_k == 3) reduce_bins<R, 3>(tile, tb, p.red_pos, acc);
+        else reduce_bins<R, 4>(tile, tb, p.red_pos, acc);
+    } else {
+        if (p.red_k == 1) reduce_forms<R, 1>(tile, tb, p.red_pos, p.red_R, F, acc);
+        else reduce_forms<R, 2>(tile, tb, p.red_pos, p.red_R, F, acc);
+    }
+}
+
+// fixed-order block reduction of one float64 per thread; result in thread 0
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// k_pass
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(256) k_pass(DevBatch d, const __grid_constant__ PassDesc p) {
+    using T = typename Cplx<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tile = reinterpret_cast<T*>(smem_raw);
+    T* mats = tile + (1 << p.tb);
+    using A = typename AccSlot<R>::T;
+    A* acc = reinterpret_cast<A*>(mats + p.mat_elems);
+    int* hi_tab = reinterpret_cast<int*>(acc + (p.red_kind != RED_NONE ? p.red_R * blockDim.x : 0));
+    __shared__ int skip[MAX_STAGES], sel_sh[MAX_STAGES], packed_sh[MAX_STAGES];
+    __shared__ double scale_sh[MAX_STAGES];
+    __shared__ double red_sh[32];
+
+    const int tb = p.tb, run = p.run_bits;
+    const int tsize = 1 << tb;
+    const int run_mask = (1 << run) - 1;
+    const int n_hi = 1 << (tb - run);
+    for (int h = threadIdx.x; h < n_hi; h += blockDim.x) {
+        int o = 0;
+        for (int j = 0; j < tb - run; ++j)
+            if ((h >> j) & 1) o |= 1 << p.tile_q[run + j];
+        hi_tab[h] = o;
+    }
+    const int n_br = d.ctl[CTL_NBR];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && d.pass_log) {
+        const int i = atomicAdd(&d.ctl[CTL_NPASS], 1);
+        if (i < d.pass_log_cap) d.pass_log[i] = n_br;
+    }
+    const int64_t items = (int64_t)n_br * p.chunks;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int b = (int)(it / p.chunks), c = (int)(it % p.chunks);
+        const int slot = d.br_slot[b];
+        if (slot < 0 || slot >= d.n_slots) {
+            if (threadIdx.x == 0) set_err(d, ERR_SLOT, b);
+            continue;
+        }
+        const uint64_t clb = d.br_clbits[b];
+        __syncthreads();  // previous item is done with mats / skip
+        for (int s = threadIdx.x; s < p.n_stages; s += blockDim.x) {
+            const Stage& st = p.st[s];
+            int sk = 0, sel = 0, packed = 0;
+            double scale = 1.0;
+            if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val) sk = 1;
+            if (st.kind != ST_DENSE) {
+                sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
+                scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
+                if (sel < 0) sk = 1;
+                if (st.kind == ST_PAULI_BR && !sk) {
+                    packed = d.ipool[st.off + sel];
+                    if ((packed & 0xff) == 0) sk = 1;  // identity string: nothing to do
+                }
+            }
+            skip[s] = sk;
+            sel_sh[s] = sel;
+            packed_sh[s] = packed;
+            scale_sh[s] = scale;
+        }
+        __syncthreads();
+        const R* pool = reinterpret_cast<const R*>(d.pool);
+        for (int s = 0; s < p.n_stages; ++s) {
+            const Stage& st = p.st[s];
+            if (skip[s] || (st.kind != ST_DENSE && st.kind != ST_DENSE_BR)) continue;
+            const int D2 = 1 << (2 * st.k);
+            const R* src = pool + st.off + (st.kind == ST_DENSE_BR ? (int64_t)sel_sh[s] * st.stride : 0);
+            const R sc = (R)scale_sh[s];
+            for (int e = threadIdx.x; e < D2; e += blockDim.x) {
+                T m;
+                m.x = src[2 * e] * sc;
+                m.y = src[2 * e + 1] * sc;
+                mats[st.mat + e] = m;
+            }
+        }
+        if (p.red_kind == RED_FORMS) {
+            const int D2 = 1 << (2 * p.red_k);
+            const R* src = pool + p.red_off;
+            for (int e = threadIdx.x; e < p.red_R * D2; e += blockDim.x) {
+                T m;
+                m.x = src[2 * e];
+                m.y = src[2 * e + 1];
+                mats[p.mat_elems - p.red_R * D2 + e] = m;
+            }
+        }
+        __syncthreads();
+
+        if (p.red_kind != RED_NONE)
+            for (int e = threadIdx.x; e < p.red_R * (int)blockDim.x; e += blockDim.x) acc[e] = A{};
+        T* gstate = reinterpret_cast<T*>(d.states) + (int64_t)slot * d.dim;
+        for (int t = 0; t < p.tiles_per_chunk; ++t) {
+            const int64_t tn = (int64_t)c * p.tiles_per_chunk + t;
+            int64_t base = 0;
+            for (int j = 0; j < p.n_nontile; ++j)
+                if ((tn >> j) & 1) base |= 1ll << p.nontile_q[j];
+            T* g = gstate + base;
+            if constexpr (sizeof(T) == 8) {  // complex64: two amplitudes per 128-bit access
+                for (int l2 = threadIdx.x; l2 < (tsize >> 1); l2 += blockDim.x) {
+                    const int l = l2 << 1;
+                    const int gi = (l & run_mask) | hi_tab[l >> run];
+                    const float4 v = *reinterpret_cast<const float4*>(g + gi);
+                    *reinterpret_cast<float4*>(tile + l) = v;
+                }
+            } else {
+                for (int l = threadIdx.x; l < tsize; l += blockDim.x) {
+                    const int gi = (l & run_mask) | hi_tab[l >> run];
+                    tile[l] = g[gi];
+                }
+            }
+            __syncthreads();
+            for (int s = 0; s < p.n_stages; ++s) {
+                if (skip[s]) continue;
+                const Stage& st = p.st[s];
+                stage_dispatch<R>(tile, tb, st, mats + st.mat, sel_sh[s], scale_sh[s], packed_sh[s]);
+                __syncthreads();
+            }
+            if (p.red_kind != RED_NONE) {
+                const int D2 = 1 << (2 * p.red_k);
+                reduce_dispatch<R>(tile, tb, p, mats + p.mat_elems - p.red_R * D2, acc);
+            }
+            if (p.store) {
+                if constexpr (sizeof(T) == 8) {
+                    for (int l2 = threadIdx.x; l2 < (tsize >> 1); l2 += blockDim.x) {
+                        const int l = l2 << 1;
+                        const int gi = (l & run_mask) | hi_tab[l >> run];
+                        *reinterpret_cast<float4*>(g + gi) = *reinterpret_cast<const float4*>(tile + l);
+                    }
+                } else {
+                    for (int l = threadIdx.x; l < tsize; l += blockDim.x) {
+                        const int gi = (l & run_mask) | hi_tab[l >> run];
+                        g[gi] = tile[l];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (p.red_kind != RED_NONE) {
+            double* out = d.partials + ((int64_t)slot * d.max_chunks + c) * MAX_RED;
+            for (int r = 0; r < p.red_R; ++r) {
+                const double s = block_sum(acc_get(acc[r * blockDim.x + threadIdx.x]), red_sh);
+                if (threadIdx.x == 0) out[r] = s;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_decide: one CTA per branch (grid-stride)
+// ---------------------------------------------------------------------------
+constexpr int DEC_THREADS = 512;
+
+__global__ void __launch_bounds__(DEC_THREADS) k_decide(DevBatch d, const __grid_constant__ DecideDesc dd) {
+    __shared__ double p_sh[MAX_TERMS], cum_sh[MAX_TERMS];
+    __shared__ int bincnt[MAX_TERMS], binbase[MAX_TERMS], binrun[MAX_TERMS];
+    __shared__ int wcnt[DEC_THREADS / 32][MAX_TERMS];
+    __shared__ int ng_sh, first_sh;
+    const int n_br = d.ctl[CTL_NBR];
+    const int R = dd.R;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int b = blockIdx.x; b < n_br; b += gridDim.x) {
+        const int slot = d.br_slot[b], start = d.br_start[b], cnt = d.br_count[b];
+        __syncthreads();
+        if (tid < R) {
+            double p;
+            if (dd.kind == DEC_PAULI) {
+                p = dd.cum[tid] - (tid ? dd.cum[tid - 1] : 0.0);
+                cum_sh[tid] = dd.cum[tid];
+            } else {
+                const double* pp = d.partials + (int64_t)slot * d.max_chunks * MAX_RED + tid;
+                double s = 0.0;
+                for (int c = 0; c < dd.chunks; ++c) s += pp[(int64_t)c * MAX_RED];
+                p = s;
+            }
+            p_sh[tid] = p;
+            bincnt[tid] = 0;
+            binrun[tid] = 0;
+        }
+        __syncthreads();
+        if (tid == 0 && dd.kind != DEC_PAULI) {
+            double s = 0.0;
+            for (int r = 0; r < R; ++r) {
+                s += p_sh[r];
+                cum_sh[r] = s;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < cnt; i += nth) {
+            const uint32_t s = d.perm[start + i];
+            const double u = philox_uniform(d.seed, s, dd.op);
+            const int sel = select_cum(u, cum_sh, R);
+            d.shot_sel[start + i] = sel;
+            atomicAdd(&bincnt[sel], 1);
+            if (dd.log_sel) dd.log_sel[s] = sel;
+            if (dd.log_thr) {
+                dd.log_thr[2 * (int64_t)s] = sel ? cum_sh[sel - 1] : 0.0;
+                dd.log_thr[2 * (int64_t)s + 1] = cum_sh[sel];
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int ng = 0, acc = 0, first = -1;
+            for (int r = 0; r < R; ++r)
+                if (bincnt[r] > 0) {
+                    binbase[r] = acc;
+                    acc += bincnt[r];
+                    if (first < 0) first = r;
+                    ++ng;
+                }
+            ng_sh = ng;
+            first_sh = first;
+        }
+        __syncthreads();
+        const int ng = ng_sh, first = first_sh;
+        // group records: outcome, scale 1/sqrt(p) (float64), classical bits
+        if (tid == 0) {
+            int g = 0;
+            for (int r = 0; r < R; ++r) {
+                if (bincnt[r] == 0) continue;
+                const int64_t gi = (int64_t)b * MAX_TERMS + g;
+                double scale = 1.0;
+                if (dd.kind != DEC_PAULI) scale = 1.0 / sqrt(p_sh[r]);
+                uint64_t cl = d.br_clbits[b];
+                if (dd.kind == DEC_MEASURE)
+                    for (int j = 0; j < dd.m; ++j) {
+                        const uint64_t bit = (uint64_t)((r >> j) & 1);
+                        cl = (cl & ~(1ull << dd.clbit[j])) | (bit << dd.clbit[j]);
+                    }
+                d.grp_sel[gi] = r;
+                d.grp_start[gi] = start + binbase[r];
+                d.grp_cnt[gi] = bincnt[r];
+                d.grp_scale[gi] = scale;
+                d.grp_clbits[gi] = cl;
+                ++g;
+            }
+            d.grp_n[b] = ng;
+            const int64_t g0 = (int64_t)b * MAX_TERMS;
+            d.br_sel[(int64_t)dd.pend * d.cap_br + b] = first;
+            d.br_scale[(int64_t)dd.pend * d.cap_br + b] = d.grp_scale[g0];
+            d.br_clbits[b] = d.grp_clbits[g0];
+            if (ng > 1 && !dd.fork) set_err(d, ERR_GROUPS, b);
+        }
+        if (ng <= 1 || !dd.fork) continue;
+        // stable partition of the branch's shots by outcome
+        for (int base = 0; base < cnt; base += nth) {
+            const int i = base + tid;
+            const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
+            for (int e = tid; e < (nth >> 5) * MAX_TERMS; e += nth) (&wcnt[0][0])[e] = 0;
+            __syncthreads();
+            const unsigned peers = __match_any_sync(0xffffffffu, sel);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            if (sel >= 0 && rank == 0) wcnt[warp][sel] = __popc(peers);
+            __syncthreads();
+            if (sel >= 0) {
+                int before = 0;
+                for (int w = 0; w < warp; ++w) before += wcnt[w][sel];
+                const int dst = binbase[sel] + binrun[sel] + before + rank;
+                d.perm_tmp[start + dst] = d.perm[start + i];
+            }
+            __syncthreads();
+            if (tid < R) {
+                int tot = 0;
+                for (int w = 0; w < (nth >> 5); ++w) tot += wcnt[w][tid];
+                binrun[tid] += tot;
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < cnt; i += nth) d.perm[start + i] = d.perm_tmp[start + i];
+        if (tid == 0) d.br_count[b] = bincnt[first];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_alloc: one CTA of 1024 threads
+// ---------------------------------------------------------------------------
+__device__ int block_excl_scan(int v, int* sh, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int w = lane < nw ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) sh[lane] = w;
+    }
+    __syncthreads();
+    const int excl = x - v + (warp ? sh[warp - 1] : 0);
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return excl;
+}
+
+__global__ void __launch_bounds__(1024) k_alloc(DevBatch d, uint32_t op, int pend) {
+    __shared__ int sh[32];
+    const int n_br0 = d.ctl[CTL_NBR];
+    const int n_free = d.ctl[CTL_NFREE];
+    const int n_wait0 = d.ctl[CTL_NWAIT];
+    int carry = 0, wcarry = 0;
+    for (int base = 0; base < n_br0; base += blockDim.x) {
+        const int b = base + threadIdx.x;
+        const int gn = (b < n_br0) ? d.grp_n[b] : 1;
+        const int ng = gn > 1 ? gn - 1 : 0;
+        int tot;
+        const int excl = carry + block_excl_scan(ng, sh, &tot);
+        // waiting shots of this branch's groups that find no slot
+        int wshots = 0;
+        for (int g = 1; g < gn; ++g) {
+            const int j = excl + g - 1;
+            if (j >= n_free) wshots += d.grp_cnt[(int64_t)b * MAX_TERMS + g];
+        }
+        int wtot;
+        const int wexcl = wcarry + block_excl_scan(wshots, sh, &wtot);
+        if (b < n_br0 && gn > 1) {
+            const int64_t g0 = (int64_t)b * MAX_TERMS;
+            if (d.fork_log) {
+                const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
+                if (e < d.fork_log_cap) {
+                    int64_t* ev = d.fork_log + 5 * (int64_t)e;
+                    ev[0] = op; ev[1] = b; ev[2] = b; ev[3] = d.grp_sel[g0]; ev[4] = d.grp_cnt[g0];
+                }
+            }
+            int woff = wexcl;
+            for (int g = 1; g < gn; ++g) {
+                const int j = excl + g - 1;
+                const int64_t gi = g0 + g;
+                int child = -1;
+                if (j < n_free) {
+                    child = n_br0 + j;
+                    const int slot = d.free_slots[n_free - 1 - j];
+                    d.br_slot[child] = slot;
+                    d.br_start[child] = d.grp_start[gi];
+                    d.br_count[child] = d.grp_cnt[gi];
+                    d.br_clbits[child] = d.grp_clbits[gi];
+                    d.br_parent[child] = b;
+                    d.grp_n[child] = 1;
+                    for (int q = 0; q < MAX_PEND; ++q) {
+                        d.br_sel[(int64_t)q * d.cap_br + child] = d.br_sel[(int64_t)q * d.cap_br + b];
+                        d.br_scale[(int64_t)q * d.cap_br + child] = d.br_scale[(int64_t)q * d.cap_br + b];
+                    }
+                    d.br_sel[(int64_t)pend * d.cap_br + child] = d.grp_sel[gi];
+                    d.br_scale[(int64_t)pend * d.cap_br + child] = d.grp_scale[gi];
+                } else {
+                    const int cnt = d.grp_cnt[gi], st = d.grp_start[gi];
+                    for (int i = 0; i < cnt; ++i) d.wait_shots[n_wait0 + woff + i] = d.perm[st + i];
+                    woff += cnt;
+                }
+                if (d.fork_log) {
+                    const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
+                    if (e < d.fork_log_cap) {
+                        int64_t* ev = d.fork_log + 5 * (int64_t)e;
+                        ev[0] = op; ev[1] = b; ev[2] = child; ev[3] = d.grp_sel[gi]; ev[4] = d.grp_cnt[gi];
+                    }
+                }
+            }
+        }
+        carry += tot;
+        wcarry += wtot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int admitted = carry < n_free ? carry : n_free;
+        d.ctl[CTL_NBR] = n_br0 + admitted;
+        d.ctl[CTL_NFREE] = n_free - admitted;
+        d.ctl[CTL_NWAIT] = n_wait0 + wcarry;
+        d.ctl[CTL_COPY_FIRST] = n_br0;
+        d.ctl[CTL_COPY_END] = n_br0 + admitted;
+        d.ctl[CTL_NCOPIED] += admitted;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_copy: parent state -> new branch slot (128-bit accesses)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_copy(DevBatch d, int64_t state_vec16) {
+    const int first = d.ctl[CTL_COPY_FIRST], end = d.ctl[CTL_COPY_END];
+    const int nb = end - first;
+    if (nb <= 0) return;
+    const int64_t per_item = 4096;  // 16-byte words per work item (64 KB)
+    const int64_t items_per_state = (state_vec16 + per_item - 1) / per_item;
+    const int64_t items = (int64_t)nb * items_per_state;
+    const uint4* src_all = reinterpret_cast<const uint4*>(d.states);
+    uint4* dst_all = reinterpret_cast<uint4*>(d.states);
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int id = first + (int)(it / items_per_state);
+        const int64_t c = it % items_per_state;
+        const int src_slot = d.br_slot[d.br_parent[id]], dst_slot = d.br_slot[id];
+        const uint4* src = src_all + (int64_t)src_slot * state_vec16;
+        uint4* dst = dst_all + (int64_t)dst_slot * state_vec16;
+        const int64_t lo = c * per_item;
+        const int64_t hi = (lo + per_item < state_vec16) ? lo + per_item : state_vec16;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// final sampling (Section IV-B-2): per branch, prefix of |psi_j|^2 in index
+// order, one draw per shot, first j with u < C_j
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(256) k_final_partials(DevBatch d, FinalDesc f) {
+    using T = typename Cplx<R>::T;
+    __shared__ double red_sh[32];
+    const int n_br = d.ctl[CTL_NBR];
+    const int64_t L = d.dim / f.chunks;
+    const int64_t items = (int64_t)n_br * f.chunks;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int b = (int)(it / f.chunks), c = (int)(it % f.chunks);
+        const int slot = d.br_slot[b];
+        const T* g = reinterpret_cast<const T*>(d.states) + (int64_t)slot * d.dim + c * L;
+        Acc<R> a;
+        a.zero();
+        for (int64_t j = threadIdx.x; j < L; j += blockDim.x) {
+            const T v = g[j];
+            a.add(v.x * v.x + v.y * v.y);
+        }
+        const double s = block_sum(a.get(), red_sh);
+        if (threadIdx.x == 0) d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED] = s;
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_final_sample(DevBatch d, FinalDesc f) {
+    using T = typename Cplx<R>::T;
+    __shared__ double cum[MAX_CHUNKS];
+    const int n_br = d.ctl[CTL_NBR];
+    const int64_t L = d.dim / f.chunks;
+    for (int b = blockIdx.x; b < n_br; b += gridDim.x) {
+        const int slot = d.br_slot[b], start = d.br_start[b], cnt = d.br_count[b];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            const double* pp = d.partials + (int64_t)slot * d.max_chunks * MAX_RED;
+            for (int c = 0; c < f.chunks; ++c) {
+                s += pp[(int64_t)c * MAX_RED];
+                cum[c] = s;
+            }
+        }
+        __syncthreads();
+        const T* g = reinterpret_cast<const T*>(d.states) + (int64_t)slot * d.dim;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t s = d.perm[start + i];
+            const double u = philox_uniform(d.seed, s, f.op);
+            int64_t key = -1;
+            double lo = 0.0, hi = 0.0;
+            // chunk: first c with u < cum[c]
+            int clo = 0, chi = f.chunks;
+            while (clo < chi) {
+                const int mid = (clo + chi) >> 1;
+                if (u < cum[mid]) chi = mid;
+                else clo = mid + 1;
+            }
+            if (clo < f.chunks) {
+                double acc = clo ? cum[clo - 1] : 0.0;
+                const int64_t j0 = (int64_t)clo * L;
+                for (int64_t j = 0; j < L; ++j) {
+                    const T v = g[j0 + j];
+                    const double before = acc;
+                    acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+                    if (u < acc) {
+                        key = j0 + j;
+                        lo = before;
+                        hi = acc;
+                        break;
+                    }
+                }
+            }
+            if (key < 0) {  // u at or past the rounded total: last nonzero entry
+                for (int64_t j = d.dim - 1; j >= 0; --j) {
+                    const T v = g[j];
+                    const double pj = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+                    if (pj > 0) {
+                        key = j;
+                        hi = cum[f.chunks - 1];
+                        lo = hi - pj;
+                        break;
+                    }
+                }
+                if (key < 0) key = d.dim - 1;
+            }
+            d.keys[s] = (uint64_t)key;
+            if (f.log_sel) f.log_sel[s] = (int32_t)key;
+            if (f.log_thr) {
+                f.log_thr[2 * (int64_t)s] = lo;
+                f.log_thr[2 * (int64_t)s + 1] = hi;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// initialisation
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(256) k_init(DevBatch d, int n_init) {
+    using T = typename Cplx<R>::T;
+    const int64_t total = (int64_t)n_init * d.dim;
+    T* s = reinterpret_cast<T*>(d.states);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        T v;
+        v.x = (i % d.dim == 0) ? (R)1 : (R)0;
+        v.y = 0;
+        s[i] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_reset(DevBatch d, int branch_mode, int n_run, int from_wait) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < n_run; i += stride) d.perm[i] = from_wait ? d.wait_shots[i] : (uint32_t)i;
+    const int nb = branch_mode ? 1 : n_run;
+    for (int64_t b = t0; b < nb; b += stride) {
+        d.br_slot[b] = (int)b;
+        d.br_start[b] = branch_mode ? 0 : (int)b;
+        d.br_count[b] = branch_mode ? n_run : 1;
+        d.br_clbits[b] = 0;
+        d.br_parent[b] = -1;
+        d.grp_n[b] = 1;
+        for (int q = 0; q < MAX_PEND; ++q) {
+            d.br_sel[(int64_t)q * d.cap_br + b] = 0;
+            d.br_scale[(int64_t)q * d.cap_br + b] = 1.0;
+        }
+    }
+    const int n_free = d.n_slots - nb;
+    for (int64_t j = t0; j < n_free; j += stride) d.free_slots[j] = d.n_slots - 1 - (int)j;
+    if (t0 == 0) {
+        d.ctl[CTL_NBR] = nb;
+        d.ctl[CTL_NFREE] = n_free;
+        d.ctl[CTL_NWAIT] = 0;
+        d.ctl[CTL_COPY_FIRST] = 0;
+        d.ctl[CTL_COPY_END] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+size_t pass_smem_bytes(int prec, const PassDesc& p, int threads) {
+    const size_t c = prec ? 16 : 8;
+    const size_t acc = p.red_kind != RED_NONE ? (size_t)p.red_R * threads * 8 : 0;
+    return ((size_t)1 << p.tb) * c + (size_t)p.mat_elems * c + acc + ((size_t)1 << (p.tb - p.run_bits)) * 4;
+}
+
+cudaError_t init_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return e;
+}
+
+cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s) {
+    const size_t smem = pass_smem_bytes(prec, p, threads);
+    if (prec) k_pass<double><<<grid, threads, smem, s>>>(d, p);
+    else k_pass<float><<<grid, threads, smem, s>>>(d, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int grid, cudaStream_t s) {
+    k_decide<<<grid, DEC_THREADS, 0, s>>>(d, dd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alloc(const DevBatch& d, uint32_t op, int pend, cudaStream_t s) {
+    k_alloc<<<1, 1024, 0, s>>>(d, op, pend);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s) {
+    const int64_t vec16 = d.dim * (prec ? 16 : 8) / 16;
+    k_copy<<<grid, 256, 0, s>>>(d, vec16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s) {
+    if (prec) {
+        k_final_partials<double><<<grid, 256, 0, s>>>(d, f);
+        k_final_sample<double><<<grid, 256, 0, s>>>(d, f);
+    } else {
+        k_final_partials<float><<<grid, 256, 0, s>>>(d, f);
+        k_final_sample<float><<<grid, 256, 0, s>>>(d, f);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const DevBatch& d, int prec, int n_init_slots, int grid, cudaStream_t s) {
+    if (prec) k_init<double><<<grid, 256, 0, s>>>(d, n_init_slots);
+    else k_init<float><<<grid, 256, 0, s>>>(d, n_init_slots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset(const DevBatch& d, int mode_branch, int n_shots_run, int from_wait, int grid,
+                         cudaStream_t s) {
+    k_reset<<<grid, 256, 0, s>>>(d, mode_branch, n_shots_run, from_wait);
+    return cudaGetLastError();
+}
+
+}  // namespace sv

@@ -1,0 +1,1329 @@
+// Host runtime of libsv: batch memory, the pass scheduler, CUDA-graph
+// capture, and the C ABI declared in include/sv.h.
+//
+// Scheduler.  Ops are not launched one by one.  Gates and the per-branch
+// application of already-sampled noise/measurement choices are queued as
+// *stages*; a queue is flushed as one k_pass launch (one read and one write of
+// every live state) when a random op needs probabilities from the current
+// state (Kraus, measurement), when the tile cannot hold more distinct qubits,
+// or when the state is read.  Pauli choices do not depend on the state
+// (Section IV-A-3) and are sampled without touching it.  Every random op is
+// followed by k_decide, and in shot-branching mode by k_alloc and k_copy, so
+// no host synchronisation happens inside a circuit (Section IV-A-4).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sv.h"
+#include "sv_internal.h"
+
+using namespace sv;
+
+namespace {
+
+thread_local std::string g_err;
+
+sv_status fail(sv_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CU(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(SV_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct PendStage {
+    int kind, k;
+    int q[MAX_STAGE_Q];
+    int cond_clbit, cond_val, pend, reset, off, stride;
+};
+
+enum LType { L_INIT, L_RESET, L_PASS, L_DECIDE, L_ALLOC, L_COPY, L_FINAL };
+enum PClass { P_PASS = 0, P_DECIDE, P_ALLOC, P_COPY, P_FINAL, P_INIT, P_OTHER, P_N };
+
+struct Launch {
+    LType type;
+    int a0 = 0, a1 = 0, a2 = 0;
+    uint32_t op = 0;
+    PassDesc pass;
+    DecideDesc dec;
+    FinalDesc fin;
+};
+
+// Philox4x32-10 on the host (plain per-shot mode draws on the host, as the
+// conventional implementation does); published constants of Salmon et al.
+double host_uniform(uint64_t seed, uint64_t shot, uint32_t op) {
+    uint32_t k[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4] = {(uint32_t)shot, (uint32_t)(shot >> 32), op, 0u};
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t m0 = (uint64_t)0xD2511F53u * x[0];
+        const uint64_t m1 = (uint64_t)0xCD9E8D57u * x[2];
+        const uint32_t y0 = (uint32_t)(m1 >> 32) ^ x[1] ^ k[0];
+        const uint32_t y2 = (uint32_t)(m0 >> 32) ^ x[3] ^ k[1];
+        x[1] = (uint32_t)m1;
+        x[3] = (uint32_t)m0;
+        x[0] = y0;
+        x[2] = y2;
+        k[0] += 0x9E3779B9u;
+        k[1] += 0xBB67AE85u;
+    }
+    const uint64_t top = ((((uint64_t)x[0]) << 32) | x[1]) >> 11;
+    return (double)top * (1.0 / 9007199254740992.0);
+}
+
+int host_select(double u, const double* cum, int n) {
+    for (int t = 0; t < n; ++t)
+        if (u < cum[t]) return t;
+    for (int t = n - 1; t >= 0; --t)
+        if (cum[t] > (t ? cum[t - 1] : 0.0)) return t;
+    return n - 1;
+}
+
+}  // namespace
+
+struct sv_batch_s {
+    int n = 0;
+    uint64_t n_shots = 0;
+    int n_clbits = 0;
+    sv_prec prec = SV_C64;
+    sv_mode mode = SV_BATCH;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t dim = 0;
+    size_t amp_bytes = 8, state_bytes = 0;
+    int n_slots = 0;
+    int tb = 11, chunks = 1, chunks_final = 1;
+    int threads = 256, grid_pass = 0, grid_small = 0, n_sm = 0;
+    int max_active = 8, max_stages = MAX_STAGES;
+    bool branch = false;
+    // device memory
+    std::vector<void*> allocs;
+    DevBatch dev{};
+    void* d_pool = nullptr;
+    int32_t* d_ipool = nullptr;
+    size_t pool_cap = 0, ipool_cap = 0;
+    // host pool (append-only between resets; pinned staging for async upload)
+    std::vector<double> pool;
+    std::vector<int32_t> ipool;
+    size_t pool_up = 0, ipool_up = 0;
+    void* h_pool = nullptr;
+    int32_t* h_ipool = nullptr;
+    // scheduler
+    std::vector<PendStage> pend;
+    uint64_t active = 0;
+    int n_pend = 0;
+    int mat_used = 0;
+    std::vector<Launch>* rec = nullptr;
+    bool started = false;
+    uint32_t last_random = 0xffffffffu;
+    // logging
+    bool log = false;
+    std::map<uint32_t, std::pair<int32_t*, double*>> logs;
+    // statistics
+    uint64_t n_launch = 0, n_passes = 0, restarts = 0;
+    // profiling
+    bool profile = false;
+    double prof_ms[P_N] = {};
+    int64_t prof_cnt[P_N] = {};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+    // graph cache
+    uint64_t graph_hash = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;
+    std::vector<uint8_t> graph_pass_store;
+    std::vector<uint8_t> pass_store;  // per executed pass: writes the state back
+    bool upload_each = false;
+    double h2d_bytes = 0;
+    int slot_limit = 0;
+};
+
+namespace {
+
+template <class T> sv_status dalloc(sv_batch b, T** p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SV_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    b->allocs.push_back(q);
+    *p = reinterpret_cast<T*>(q);
+    return SV_OK;
+}
+
+int pclass(LType t) {
+    switch (t) {
+    case L_PASS: return P_PASS;
+    case L_DECIDE: return P_DECIDE;
+    case L_ALLOC: return P_ALLOC;
+    case L_COPY: return P_COPY;
+    case L_FINAL: return P_FINAL;
+    case L_INIT: return P_INIT;
+    default: return P_OTHER;
+    }
+}
+
+int pass_grid(sv_batch b, const PassDesc& p) {
+    if (b->grid_pass > 0) return b->grid_pass;
+    // k_pass is register-bound at two CTAs of 256 threads per SM; shared
+    // memory (tile + matrices + accumulators) may allow fewer
+    const size_t smem = pass_smem_bytes(b->prec == SV_C128, p, b->threads) + 2048;
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(b->threads == 128 ? 4 : 2, (227 * 1024) / smem));
+    return b->n_sm * per_sm;
+}
+
+cudaError_t exec_one(sv_batch b, const Launch& L) {
+    const int prec = b->prec == SV_C128;
+    switch (L.type) {
+    case L_INIT: return launch_init(b->dev, prec, L.a0, b->n_sm * 4, b->stream);
+    case L_RESET: return launch_reset(b->dev, L.a0, L.a1, L.a2, b->n_sm * 2, b->stream);
+    case L_PASS: return launch_pass(b->dev, prec, L.pass, b->threads, pass_grid(b, L.pass), b->stream);
+    case L_DECIDE: return launch_decide(b->dev, L.dec, b->grid_small, b->stream);
+    case L_ALLOC: return launch_alloc(b->dev, L.op, L.a0, b->stream);
+    case L_COPY: return launch_copy(b->dev, prec, b->n_sm * 4, b->stream);
+    case L_FINAL: return launch_final(b->dev, prec, L.fin, b->grid_small, b->stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+sv_status exec(sv_batch b, const Launch& L) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (b->profile && !b->rec) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, b->stream);
+    }
+    cudaError_t e = exec_one(b, L);
+    if (e != cudaSuccess) return fail(SV_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    if (e0) {
+        cudaEventRecord(e1, b->stream);
+        b->prof_ev.push_back({pclass(L.type), {e0, e1}});
+    }
+    b->n_launch += (L.type == L_FINAL) ? 2 : 1;
+    if (L.type == L_PASS) {
+        b->n_passes += 1;
+        b->pass_store.push_back(L.pass.store ? 1 : 0);
+    }
+    return SV_OK;
+}
+
+sv_status emit(sv_batch b, Launch&& L) {
+    if (b->rec) {
+        b->rec->push_back(std::move(L));
+        return SV_OK;
+    }
+    return exec(b, L);
+}
+
+// ---- pool ------------------------------------------------------------------
+sv_status upload_pool(sv_batch b) {
+    const size_t rsz = b->prec == SV_C128 ? 8 : 4;
+    if (b->pool.size() > b->pool_cap || b->ipool.size() > b->ipool_cap)
+        return fail(SV_ENOMEM, "constant pool full (circuit too large for one batch)");
+    if (b->pool.size() > b->pool_up) {
+        for (size_t i = b->pool_up; i < b->pool.size(); ++i) {
+            if (rsz == 8) reinterpret_cast<double*>(b->h_pool)[i] = b->pool[i];
+            else reinterpret_cast<float*>(b->h_pool)[i] = (float)b->pool[i];
+        }
+        CU(cudaMemcpyAsync((char*)b->d_pool + b->pool_up * rsz, (char*)b->h_pool + b->pool_up * rsz,
+                           (b->pool.size() - b->pool_up) * rsz, cudaMemcpyHostToDevice, b->stream));
+        b->h2d_bytes += (double)(b->pool.size() - b->pool_up) * rsz;
+        b->pool_up = b->pool.size();
+    }
+    if (b->ipool.size() > b->ipool_up) {
+        for (size_t i = b->ipool_up; i < b->ipool.size(); ++i) b->h_ipool[i] = b->ipool[i];
+        CU(cudaMemcpyAsync(b->d_ipool + b->ipool_up, b->h_ipool + b->ipool_up,
+                           (b->ipool.size() - b->ipool_up) * 4, cudaMemcpyHostToDevice, b->stream));
+        b->h2d_bytes += (double)(b->ipool.size() - b->ipool_up) * 4;
+        b->ipool_up = b->ipool.size();
+    }
+    return SV_OK;
+}
+
+sv_status reset_pool(sv_batch b) {
+    CU(cudaStreamSynchronize(b->stream));  // staging buffers are about to be rewritten
+    b->pool.clear();
+    b->ipool.clear();
+    b->pool_up = b->ipool_up = 0;
+    return SV_OK;
+}
+
+int pool_matrix(sv_batch b, const double* m, int k, double scale = 1.0) {
+    const int off = (int)b->pool.size();
+    const int e = 1 << (2 * k);
+    for (int i = 0; i < 2 * e; ++i) b->pool.push_back(m[i] * scale);
+    return off;
+}
+
+// ---- scheduler ---------------------------------------------------------------
+int local_pos(const int* tile_q, int tb, int q) {
+    for (int i = 0; i < tb; ++i)
+        if (tile_q[i] == q) return i;
+    return -1;
+}
+
+// Flush queued stages as one pass; optionally end it with a reduction.
+struct RedSpec {
+    int kind = RED_NONE, k = 0, R = 0, off = 0;
+    int q[MAX_STAGE_Q] = {0, 0, 0, 0};
+};
+
+sv_status emit_pass(sv_batch b, const RedSpec& red) {
+    if (b->pend.empty() && red.kind == RED_NONE) return SV_OK;
+    Launch L;
+    L.type = L_PASS;
+    PassDesc& p = L.pass;
+    memset(&p, 0, sizeof(p));
+    p.n = b->n;
+    p.tb = b->tb;
+    uint64_t act = b->active;
+    for (int j = 0; j < red.k; ++j) act |= 1ull << red.q[j];
+    // tile qubits: every active qubit plus the lowest others
+    std::vector<int> tq;
+    for (int q = 0; q < b->n; ++q)
+        if ((act >> q) & 1) tq.push_back(q);
+    if ((int)tq.size() > p.tb) return fail(SV_EINTERNAL, "pass holds more qubits than a tile");
+    for (int q = 0; q < b->n && (int)tq.size() < p.tb; ++q)
+        if (!((act >> q) & 1)) tq.push_back(q);
+    std::sort(tq.begin(), tq.end());
+    for (int i = 0; i < p.tb; ++i) p.tile_q[i] = tq[i];
+    int run = 0;
+    while (run < p.tb && p.tile_q[run] == run) ++run;
+    p.run_bits = run;
+    p.n_nontile = 0;
+    for (int q = 0; q < b->n; ++q)
+        if (std::find(tq.begin(), tq.end(), q) == tq.end()) p.nontile_q[p.n_nontile++] = q;
+    const int64_t tiles = 1ll << (b->n - p.tb);
+    p.chunks = b->chunks;
+    p.tiles_per_chunk = (int)(tiles / b->chunks);
+    int mat = 0;
+    p.n_stages = (int)b->pend.size();
+    for (int s = 0; s < p.n_stages; ++s) {
+        const PendStage& ps = b->pend[s];
+        Stage& st = p.st[s];
+        st.kind = ps.kind;
+        st.k = ps.k;
+        for (int j = 0; j < ps.k; ++j) st.pos[j] = local_pos(p.tile_q, p.tb, ps.q[j]);
+        st.cond_clbit = ps.cond_clbit;
+        st.cond_val = ps.cond_val;
+        st.pend = ps.pend;
+        st.reset = ps.reset;
+        st.off = ps.off;
+        st.stride = ps.stride;
+        st.mat = 0;
+        if (ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) {
+            st.mat = mat;
+            mat += 1 << (2 * ps.k);
+        }
+    }
+    p.store = p.n_stages > 0;
+    p.red_kind = red.kind;
+    p.red_k = red.k;
+    p.red_R = red.R;
+    p.red_off = red.off;
+    for (int j = 0; j < red.k; ++j) p.red_pos[j] = local_pos(p.tile_q, p.tb, red.q[j]);
+    if (red.kind == RED_FORMS) mat += red.R << (2 * red.k);
+    p.mat_elems = mat;
+    b->pend.clear();
+    b->active = 0;
+    b->n_pend = 0;
+    b->mat_used = 0;
+    return emit(b, std::move(L));
+}
+
+sv_status flush(sv_batch b) { return emit_pass(b, RedSpec()); }
+
+// make room for a stage on qubits q[0..k-1] with `mats` matrix entries
+sv_status make_room(sv_batch b, const int* q, int k, int mats, bool needs_pend) {
+    uint64_t act = b->active;
+    for (int j = 0; j < k; ++j) act |= 1ull << q[j];
+    const int limit = std::min(b->max_active, b->tb);
+    if (__builtin_popcountll(act) > limit || (int)b->pend.size() >= b->max_stages ||
+        b->mat_used + mats > MAT_SMEM - 256 || (needs_pend && b->n_pend >= MAX_PEND))
+        return flush(b);
+    return SV_OK;
+}
+
+void add_stage(sv_batch b, const PendStage& s) {
+    b->pend.push_back(s);
+    for (int j = 0; j < s.k; ++j) b->active |= 1ull << s.q[j];
+    if (s.kind == ST_DENSE || s.kind == ST_DENSE_BR) b->mat_used += 1 << (2 * s.k);
+}
+
+sv_status ensure_started(sv_batch b) {
+    if (b->started) return SV_OK;
+    const int branch = b->branch;
+    Launch r;
+    r.type = L_RESET;
+    r.a0 = branch;
+    r.a1 = (int)b->n_shots;
+    r.a2 = 0;
+    sv_status st = emit(b, std::move(r));
+    if (st) return st;
+    Launch i;
+    i.type = L_INIT;
+    i.a0 = branch ? 1 : (int)b->n_shots;
+    st = emit(b, std::move(i));
+    if (st) return st;
+    b->started = true;
+    return SV_OK;
+}
+
+sv_status check_qubits(sv_batch b, int k, const int* q) {
+    if (!q && k > 0) return fail(SV_EINVAL, "qubits is NULL");
+    for (int j = 0; j < k; ++j) {
+        if (q[j] < 0 || q[j] >= b->n) return fail(SV_EINVAL, "qubit out of range");
+        for (int i = 0; i < j; ++i)
+            if (q[i] == q[j]) return fail(SV_EINVAL, "repeated qubit");
+    }
+    return SV_OK;
+}
+
+sv_status get_log(sv_batch b, uint32_t op, int32_t** sel, double** thr) {
+    *sel = nullptr;
+    *thr = nullptr;
+    if (!b->log) return SV_OK;
+    auto it = b->logs.find(op);
+    if (it == b->logs.end()) {
+        int32_t* s = nullptr;
+        double* t = nullptr;
+        sv_status st = dalloc(b, &s, b->n_shots);
+        if (st) return st;
+        st = dalloc(b, &t, 2 * b->n_shots);
+        if (st) return st;
+        cudaMemsetAsync(s, 0xff, b->n_shots * 4, b->stream);
+        it = b->logs.emplace(op, std::make_pair(s, t)).first;
+    }
+    *sel = it->second.first;
+    *thr = it->second.second;
+    return SV_OK;
+}
+
+// decide (+ fork) for random op `op`; the chosen term is then queued as a stage
+sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cum, int pend, int m,
+                      const int* clbits) {
+    Launch L;
+    L.type = L_DECIDE;
+    DecideDesc& d = L.dec;
+    memset(&d, 0, sizeof(d));
+    d.op = op;
+    d.kind = kind;
+    d.R = R;
+    d.pend = pend;
+    d.chunks = b->chunks;
+    d.fork = b->branch;
+    d.m = m;
+    for (int j = 0; j < m; ++j) d.clbit[j] = clbits[j];
+    if (cum)
+        for (int t = 0; t < R; ++t) d.cum[t] = cum[t];
+    sv_status st = get_log(b, op, &d.log_sel, &d.log_thr);
+    if (st) return st;
+    st = emit(b, std::move(L));
+    if (st) return st;
+    if (b->branch) {
+        Launch a;
+        a.type = L_ALLOC;
+        a.op = op;
+        a.a0 = pend;
+        st = emit(b, std::move(a));
+        if (st) return st;
+        Launch c;
+        c.type = L_COPY;
+        st = emit(b, std::move(c));
+        if (st) return st;
+    }
+    b->last_random = op;
+    return SV_OK;
+}
+
+bool is_unitary(const double* m, int k, double tol) {
+    const int D = 1 << k;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            std::complex<double> s = 0;
+            for (int r = 0; r < D; ++r)
+                s += std::conj(std::complex<double>(m[2 * (r * D + i)], m[2 * (r * D + i) + 1])) *
+                     std::complex<double>(m[2 * (r * D + j)], m[2 * (r * D + j) + 1]);
+            if (std::abs(s - (i == j ? 1.0 : 0.0)) > tol) return false;
+        }
+    return true;
+}
+
+// ---- op implementations (batched modes) --------------------------------------
+sv_status op_gate(sv_batch b, int k, const int* q, const double* mat, int cond_clbit, int cond_val) {
+    sv_status st = check_qubits(b, k, q);
+    if (st) return st;
+    if (k < 1 || k > 3) return fail(SV_EUNSUPPORTED, "gates act on 1 to 3 qubits");
+    if (!mat) return fail(SV_EINVAL, "matrix is NULL");
+    if (cond_clbit >= b->n_clbits || cond_clbit < -1) return fail(SV_EINVAL, "condition bit out of range");
+    if (!is_unitary(mat, k, 1e-10)) return fail(SV_EINVAL, "gate matrix is not unitary");
+    if ((st = ensure_started(b))) return st;
+    if ((st = make_room(b, q, k, 1 << (2 * k), false))) return st;
+    PendStage s{};
+    s.kind = ST_DENSE;
+    s.k = k;
+    for (int j = 0; j < k; ++j) s.q[j] = q[j];
+    s.cond_clbit = cond_clbit;
+    s.cond_val = cond_val;
+    s.off = pool_matrix(b, mat, k);
+    add_stage(b, s);
+    return SV_OK;
+}
+
+int pauli_packed(const char* str, int k) {
+    int xm = 0, zm = 0, ny = 0;
+    for (int j = 0; j < k; ++j) {
+        const char c = str[j];
+        if (c == 'X' || c == 'Y') xm |= 1 << j;
+        if (c == 'Z' || c == 'Y') zm |= 1 << j;
+        if (c == 'Y') ++ny;
+    }
+    return xm | (zm << 4) | ((ny & 3) << 8);
+}
+
+sv_status op_pauli(sv_batch b, uint32_t op, int k, const int* q, int n_terms, const double* cum,
+                   const char* paulis) {
+    sv_status st = check_qubits(b, k, q);
+    if (st) return st;
+    if (k < 1 || k > 4) return fail(SV_EUNSUPPORTED, "Pauli noise acts on 1 to 4 qubits");
+    if (n_terms < 1 || n_terms > MAX_TERMS) return fail(SV_EUNSUPPORTED, "Pauli noise has 1 to 64 terms");
+    if (!cum || !paulis) return fail(SV_EINVAL, "Pauli table is NULL");
+    for (int t = 0; t < n_terms; ++t) {
+        if (t && cum[t] < cum[t - 1]) return fail(SV_EINVAL, "cumulative probabilities decrease");
+        for (int j = 0; j < k; ++j)
+            if (!strchr("IXYZ", paulis[t * k + j]) || !paulis[t * k + j]) return fail(SV_EINVAL, "bad Pauli character");
+    }
+    if ((st = ensure_started(b))) return st;
+    if ((st = make_room(b, q, k, 0, true))) return st;
+    const int pend = b->n_pend++;
+    const int off = (int)b->ipool.size();
+    for (int t = 0; t < n_terms; ++t) b->ipool.push_back(pauli_packed(paulis + t * k, k));
+    if ((st = upload_pool(b))) return st;
+    if ((st = emit_decide(b, op, DEC_PAULI, n_terms, cum, pend, 0, nullptr))) return st;
+    PendStage s{};
+    s.kind = ST_PAULI_BR;
+    s.k = k;
+    for (int j = 0; j < k; ++j) s.q[j] = q[j];
+    s.cond_clbit = -1;
+    s.pend = pend;
+    s.off = off;
+    add_stage(b, s);
+    return SV_OK;
+}
+
+sv_status op_kraus(sv_batch b, uint32_t op, int k, const int* q, int n_terms, const double* kraus) {
+    sv_status st = check_qubits(b, k, q);
+    if (st) return st;
+    if (k < 1 || k > 2) return fail(SV_EUNSUPPORTED, "Kraus noise acts on 1 or 2 qubits");
+    if (n_terms < 1 || n_terms > MAX_RED) return fail(SV_EUNSUPPORTED, "Kraus noise has 1 to 16 matrices");
+    if (!kraus) return fail(SV_EINVAL, "Kraus matrices are NULL");
+    const int D = 1 << k, E = D * D;
+    // forms F_i = K_i^dagger K_i, and the completeness check sum F_i = I
+    std::vector<double> forms(2 * E * n_terms);
+    std::vector<std::complex<double>> tot(E);
+    for (int t = 0; t < n_terms; ++t) {
+        const double* K = kraus + 2 * E * t;
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                std::complex<double> s = 0;
+                for (int r = 0; r < D; ++r)
+                    s += std::conj(std::complex<double>(K[2 * (r * D + i)], K[2 * (r * D + i) + 1])) *
+                         std::complex<double>(K[2 * (r * D + j)], K[2 * (r * D + j) + 1]);
+                forms[2 * (E * t + i * D + j)] = s.real();
+                forms[2 * (E * t + i * D + j) + 1] = s.imag();
+                tot[i * D + j] += s;
+            }
+    }
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j)
+            if (std::abs(tot[i * D + j] - (i == j ? 1.0 : 0.0)) > 1e-10)
+                return fail(SV_EINVAL, "Kraus matrices are not complete (sum K^dagger K != I)");
+    if ((st = ensure_started(b))) return st;
+    // the reduction must see every earlier op: queued stages + forms in one pass
+    uint64_t act = b->active;
+    for (int j = 0; j < k; ++j) act |= 1ull << q[j];
+    if (__builtin_popcountll(act) > std::min(b->max_active, b->tb) ||
+        b->mat_used + n_terms * E > MAT_SMEM - 256)
+        if ((st = flush(b))) return st;
+    RedSpec red;
+    red.kind = RED_FORMS;
+    red.k = k;
+    red.R = n_terms;
+    for (int j = 0; j < k; ++j) red.q[j] = q[j];
+    red.off = (int)b->pool.size();
+    for (double v : forms) b->pool.push_back(v);
+    const int mat_off = (int)b->pool.size();
+    for (int i = 0; i < 2 * E * n_terms; ++i) b->pool.push_back(kraus[i]);
+    if ((st = upload_pool(b))) return st;
+    if ((st = emit_pass(b, red))) return st;
+    const int pend = b->n_pend++;
+    if ((st = emit_decide(b, op, DEC_KRAUS, n_terms, nullptr, pend, 0, nullptr))) return st;
+    PendStage s{};
+    s.kind = ST_DENSE_BR;
+    s.k = k;
+    for (int j = 0; j < k; ++j) s.q[j] = q[j];
+    s.cond_clbit = -1;
+    s.pend = pend;
+    s.off = mat_off;
+    s.stride = 2 * E;
+    if ((st = make_room(b, q, k, E, true))) return st;
+    add_stage(b, s);
+    return SV_OK;
+}
+
+sv_status op_measure(sv_batch b, uint32_t op, int m, const int* q, const int* clbits, int reset) {
+    sv_status st = check_qubits(b, m, q);
+    if (st) return st;
+    if (m < 1 || m > 4) return fail(SV_EUNSUPPORTED, "measurements take 1 to 4 qubits");
+    if (!clbits) return fail(SV_EINVAL, "clbits is NULL");
+    for (int j = 0; j < m; ++j)
+        if (clbits[j] < 0 || clbits[j] >= b->n_clbits) return fail(SV_EINVAL, "classical bit out of range");
+    if ((st = ensure_started(b))) return st;
+    uint64_t act = b->active;
+    for (int j = 0; j < m; ++j) act |= 1ull << q[j];
+    if (__builtin_popcountll(act) > std::min(b->max_active, b->tb))
+        if ((st = flush(b))) return st;
+    RedSpec red;
+    red.kind = RED_BINS;
+    red.k = m;
+    red.R = 1 << m;
+    for (int j = 0; j < m; ++j) red.q[j] = q[j];
+    if ((st = upload_pool(b))) return st;
+    if ((st = emit_pass(b, red))) return st;
+    const int pend = b->n_pend++;
+    if ((st = emit_decide(b, op, DEC_MEASURE, 1 << m, nullptr, pend, m, clbits))) return st;
+    PendStage s{};
+    s.kind = ST_PROJ_BR;
+    s.k = m;
+    for (int j = 0; j < m; ++j) s.q[j] = q[j];
+    s.cond_clbit = -1;
+    s.pend = pend;
+    s.reset = reset ? 1 : 0;
+    add_stage(b, s);
+    return SV_OK;
+}
+
+sv_status op_final(sv_batch b, uint32_t op) {
+    sv_status st = ensure_started(b);
+    if (st) return st;
+    if ((st = upload_pool(b))) return st;
+    if ((st = flush(b))) return st;
+    Launch L;
+    L.type = L_FINAL;
+    memset(&L.fin, 0, sizeof(L.fin));
+    L.fin.op = op;
+    L.fin.chunks = b->chunks_final;
+    if ((st = get_log(b, op, &L.fin.log_sel, &L.fin.log_thr))) return st;
+    return emit(b, std::move(L));
+}
+
+sv_status check_device_error(sv_batch b) {
+    int32_t ctl[CTL_WORDS];
+    CU(cudaMemcpyAsync(ctl, b->dev.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    if (ctl[CTL_ERR] == ERR_TIMEOUT) return fail(SV_ETIMEOUT, "device wait timed out");
+    if (ctl[CTL_ERR] != 0) {
+        char buf[128];
+        snprintf(buf, sizeof(buf), "device error %d (info %d)", ctl[CTL_ERR], ctl[CTL_ERR_INFO]);
+        return fail(SV_EINTERNAL, buf);
+    }
+    return SV_OK;
+}
+
+sv_status read_ctl(sv_batch b, int32_t* ctl) {
+    CU(cudaMemcpyAsync(ctl, b->dev.ctl, sizeof(int32_t) * CTL_WORDS, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return SV_OK;
+}
+
+// one op of a flattened circuit, batched modes
+sv_status circuit_op(sv_batch b, const sv_circuit* c, int i) {
+    const int kind = c->kind[i], k = c->nq[i];
+    const int* q = c->qubits + c->q_off[i];
+    const double* d = c->data + c->d_off[i];
+    switch (kind) {
+    case SV_OP_GATE: return op_gate(b, k, q, d, c->cond_clbit[i], c->cond_val[i]);
+    case SV_OP_PAULI:
+        return op_pauli(b, (uint32_t)i, k, q, c->n_terms[i], d, (const char*)c->paulis + c->s_off[i]);
+    case SV_OP_KRAUS: return op_kraus(b, (uint32_t)i, k, q, c->n_terms[i], d);
+    case SV_OP_MEASURE: return op_measure(b, (uint32_t)i, k, q, c->clbits + c->cl_off[i], c->reset[i]);
+    case SV_OP_FINAL: return op_final(b, (uint32_t)i);
+    }
+    return fail(SV_EINVAL, "unknown op kind");
+}
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
+uint64_t circuit_hash(sv_batch b, const sv_circuit* c) {
+    uint64_t h = 1469598103934665603ull;
+    h = fnv(h, &c->n_qubits, 12);
+    const size_t n = c->n_ops;
+    h = fnv(h, c->kind, 4 * n);
+    h = fnv(h, c->nq, 4 * n);
+    h = fnv(h, c->q_off, 4 * n);
+    h = fnv(h, c->n_terms, 4 * n);
+    h = fnv(h, c->d_off, 8 * n);
+    h = fnv(h, c->cond_clbit, 4 * n);
+    h = fnv(h, c->cond_val, 4 * n);
+    int64_t dmax = 0, qmax = 0;
+    for (size_t i = 0; i < n; ++i) qmax = std::max<int64_t>(qmax, c->q_off[i] + c->nq[i]);
+    h = fnv(h, c->qubits, 4 * qmax);
+    for (size_t i = 0; i < n; ++i) {
+        const int k = c->nq[i];
+        int64_t len = 0;
+        if (c->kind[i] == SV_OP_GATE) len = 2ll << (2 * k);
+        else if (c->kind[i] == SV_OP_PAULI) len = c->n_terms[i];
+        else if (c->kind[i] == SV_OP_KRAUS) len = (int64_t)c->n_terms[i] * (2ll << (2 * k));
+        dmax = std::max<int64_t>(dmax, c->d_off[i] + len);
+    }
+    h = fnv(h, c->data, 8 * dmax);
+    for (size_t i = 0; i < n; ++i)
+        if (c->kind[i] == SV_OP_PAULI) h = fnv(h, c->paulis + c->s_off[i], (size_t)c->n_terms[i] * c->nq[i]);
+    h = fnv(h, &b->mode, sizeof(b->mode));
+    return h;
+}
+
+// plain per-shot form: one state, one launch per op, host-side choices
+sv_status run_plain(sv_batch b, const sv_circuit* c) {
+    sv_status st;
+    const int prec = 1;
+    (void)prec;
+    std::vector<uint64_t> keys(b->n_shots);
+    for (uint64_t shot = 0; shot < b->n_shots; ++shot) {
+        Launch r;
+        r.type = L_RESET;
+        r.a0 = 0;
+        r.a1 = 1;
+        r.a2 = 0;
+        if ((st = exec(b, r))) return st;
+        // perm[0] = shot
+        uint32_t s32 = (uint32_t)shot;
+        CU(cudaMemcpyAsync(b->dev.perm, &s32, 4, cudaMemcpyHostToDevice, b->stream));
+        Launch in;
+        in.type = L_INIT;
+        in.a0 = 1;
+        if ((st = exec(b, in))) return st;
+        uint64_t clreg = 0;
+        for (int i = 0; i < c->n_ops; ++i) {
+            const int kind = c->kind[i], k = c->nq[i];
+            const int* q = c->qubits + c->q_off[i];
+            const double* d = c->data + c->d_off[i];
+            if (kind == SV_OP_GATE) {
+                if (c->cond_clbit[i] >= 0 && (int)((clreg >> c->cond_clbit[i]) & 1) != c->cond_val[i]) continue;
+                if ((st = op_gate(b, k, q, d, -1, 0))) return st;
+                if ((st = upload_pool(b))) return st;
+                if ((st = flush(b))) return st;
+            } else if (kind == SV_OP_PAULI) {
+                const double u = host_uniform(b->seed, shot, (uint32_t)i);
+                const int t = host_select(u, d, c->n_terms[i]);
+                const char* str = (const char*)c->paulis + c->s_off[i] + t * k;
+                if (pauli_packed(str, k) & 0xff) {
+                    // a single-entry table makes the device choice the host's
+                    double one[1] = {2.0};
+                    if ((st = op_pauli(b, (uint32_t)i, k, q, 1, one, str))) return st;
+                    if ((st = flush(b))) return st;
+                }
+            } else if (kind == SV_OP_KRAUS || kind == SV_OP_MEASURE) {
+                // conventional form: one reduction per candidate, read back, compare on the host
+                const int R = kind == SV_OP_KRAUS ? c->n_terms[i] : (1 << k);
+                const int D = 1 << k, E = D * D;
+                std::vector<double> p(R);
+                for (int t = 0; t < R; ++t) {
+                    RedSpec red;
+                    red.k = k;
+                    for (int j = 0; j < k; ++j) red.q[j] = q[j];
+                    if (kind == SV_OP_KRAUS) {
+                        red.kind = RED_FORMS;
+                        red.R = 1;
+                        red.off = (int)b->pool.size();
+                        const double* K = d + 2 * E * t;
+                        for (int a = 0; a < D; ++a)
+                            for (int bb = 0; bb < D; ++bb) {
+                                std::complex<double> s = 0;
+                                for (int r = 0; r < D; ++r)
+                                    s += std::conj(std::complex<double>(K[2 * (r * D + a)], K[2 * (r * D + a) + 1])) *
+                                         std::complex<double>(K[2 * (r * D + bb)], K[2 * (r * D + bb) + 1]);
+                                b->pool.push_back(s.real());
+                                b->pool.push_back(s.imag());
+                            }
+                    } else {
+                        red.kind = RED_BINS;
+                        red.R = 1 << k;
+                    }
+                    if ((st = upload_pool(b))) return st;
+                    if ((st = emit_pass(b, red))) return st;
+                    std::vector<double> part(MAX_RED * b->chunks);
+                    CU(cudaMemcpyAsync(part.data(), b->dev.partials, sizeof(double) * MAX_RED * b->chunks,
+                                       cudaMemcpyDeviceToHost, b->stream));
+                    CU(cudaStreamSynchronize(b->stream));
+                    if (kind == SV_OP_KRAUS) {
+                        double s = 0;
+                        for (int ch = 0; ch < b->chunks; ++ch) s += part[ch * MAX_RED];
+                        p[t] = s;
+                    } else {
+                        for (int o = 0; o < R; ++o) {
+                            double s = 0;
+                            for (int ch = 0; ch < b->chunks; ++ch) s += part[ch * MAX_RED + o];
+                            p[o] = s;
+                        }
+                        break;
+                    }
+                }
+                std::vector<double> cum(R);
+                double acc = 0;
+                for (int t = 0; t < R; ++t) cum[t] = (acc += p[t]);
+                const double u = host_uniform(b->seed, shot, (uint32_t)i);
+                const int t = host_select(u, cum.data(), R);
+                const double scale = 1.0 / std::sqrt(p[t]);
+                if (kind == SV_OP_KRAUS) {
+                    const double* K = d + 2 * E * t;
+                    PendStage s{};
+                    s.kind = ST_DENSE;
+                    s.k = k;
+                    for (int j = 0; j < k; ++j) s.q[j] = q[j];
+                    s.cond_clbit = -1;
+                    s.off = pool_matrix(b, K, k, scale);
+                    add_stage(b, s);
+                } else {
+                    // projection (and reset) as a dense matrix on the measured qubits
+                    std::vector<double> P(2 * E, 0.0);
+                    const int reset = c->reset[i];
+                    P[2 * ((reset ? 0 : t) * D + t)] = scale;
+                    PendStage s{};
+                    s.kind = ST_DENSE;
+                    s.k = k;
+                    for (int j = 0; j < k; ++j) s.q[j] = q[j];
+                    s.cond_clbit = -1;
+                    s.off = pool_matrix(b, P.data(), k);
+                    add_stage(b, s);
+                    const int* cl = c->clbits + c->cl_off[i];
+                    for (int j = 0; j < k; ++j)
+                        clreg = (clreg & ~(1ull << cl[j])) | ((uint64_t)((t >> j) & 1) << cl[j]);
+                }
+                if ((st = upload_pool(b))) return st;
+                if ((st = flush(b))) return st;
+            } else if (kind == SV_OP_FINAL) {
+                if ((st = op_final(b, (uint32_t)i))) return st;
+            }
+        }
+        if ((st = reset_pool(b))) return st;
+    }
+    return SV_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+extern "C" {
+
+const char* sv_last_error(void) { return g_err.c_str(); }
+
+sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec prec, sv_mode mode, uint64_t seed,
+                         uint64_t mem_budget, void* cuda_stream, sv_batch* out) {
+    if (!out) return fail(SV_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 30) return fail(SV_EINVAL, "n_qubits must be 1..30");
+    if (n_shots == 0 || n_shots > (1ull << 31)) return fail(SV_EINVAL, "n_shots must be 1..2^31");
+    if (n_clbits < 0 || n_clbits > 64) return fail(SV_EINVAL, "n_clbits must be 0..64");
+    if (prec != SV_C64 && prec != SV_C128) return fail(SV_EINVAL, "bad precision");
+    if (mode < SV_PLAIN || mode > SV_BATCH_BRANCH) return fail(SV_EINVAL, "bad mode");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SV_ECUDA, "no CUDA device");
+    }
+    sv_batch b = new sv_batch_s();
+    b->n = n_qubits;
+    b->n_shots = n_shots;
+    b->n_clbits = n_clbits;
+    b->prec = prec;
+    b->mode = mode;
+    b->seed = seed;
+    b->branch = mode == SV_BRANCH || mode == SV_BATCH_BRANCH;
+    b->dim = 1ll << n_qubits;
+    b->amp_bytes = prec == SV_C128 ? 16 : 8;
+    b->state_bytes = b->dim * b->amp_bytes;
+    cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    b->grid_small = 2 * b->n_sm;
+    b->tb = std::min(n_qubits, prec == SV_C128 ? 10 : 11);
+    const int64_t tiles = 1ll << (n_qubits - b->tb);
+    b->chunks = (int)std::min<int64_t>(tiles, MAX_CHUNKS);
+    b->chunks_final = (int)std::min<int64_t>(std::max<int64_t>(b->dim / 2048, 1), MAX_CHUNKS);
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return fail(SV_ECUDA, "cudaStreamCreate failed");
+        }
+        b->own_stream = true;
+    }
+    // slots
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const int max_chunks = std::max(b->chunks, b->chunks_final);
+    const size_t per_slot = b->state_bytes + (size_t)max_chunks * MAX_RED * 8;
+    const size_t per_shot = 4 * 8 + MAX_PEND * 12 + (size_t)MAX_TERMS * 32 + 64;
+    const size_t fixed = per_shot * n_shots + (64ull << 20);
+    size_t budget = mem_budget;
+    if (budget == 0) {
+        const size_t reserve = std::max<size_t>(1ull << 30, total_b / 50);
+        budget = free_b > fixed + reserve ? free_b - fixed - reserve : 0;
+    }
+    uint64_t slots = budget / per_slot;
+    if (mode == SV_PLAIN) slots = std::min<uint64_t>(slots, 1);
+    else slots = std::min<uint64_t>(slots, n_shots);
+    if (slots == 0) {
+        sv_free_batch(b);
+        return fail(SV_ENOMEM, "not even one state fits the memory budget");
+    }
+    if (mode == SV_BATCH && slots < n_shots) {
+        sv_free_batch(b);
+        return fail(SV_ENOMEM, "batch mode needs one state per shot; use shot-branching or fewer shots");
+    }
+    b->n_slots = (int)slots;
+    DevBatch& d = b->dev;
+    d.dim = b->dim;
+    d.n = n_qubits;
+    d.n_slots = b->n_slots;
+    d.cap_br = (int)n_shots;
+    d.seed = seed;
+    d.max_chunks = max_chunks;
+    sv_status st = SV_OK;
+    void* states = nullptr;
+    if (cudaMalloc(&states, (size_t)b->n_slots * b->state_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        sv_free_batch(b);
+        return fail(SV_ENOMEM, "cannot allocate the state slots");
+    }
+    b->allocs.push_back(states);
+    d.states = states;
+    const uint64_t S = n_shots;
+    if ((st = dalloc(b, &d.ctl, CTL_WORDS)) || (st = dalloc(b, &d.br_slot, S)) || (st = dalloc(b, &d.br_start, S)) ||
+        (st = dalloc(b, &d.br_count, S)) || (st = dalloc(b, &d.br_clbits, S)) || (st = dalloc(b, &d.br_parent, S)) ||
+        (st = dalloc(b, &d.br_sel, S * MAX_PEND)) || (st = dalloc(b, &d.br_scale, S * MAX_PEND)) ||
+        (st = dalloc(b, &d.perm, S)) || (st = dalloc(b, &d.perm_tmp, S)) || (st = dalloc(b, &d.shot_sel, S)) ||
+        (st = dalloc(b, &d.grp_n, S)) || (st = dalloc(b, &d.grp_sel, S * MAX_TERMS)) ||
+        (st = dalloc(b, &d.grp_start, S * MAX_TERMS)) || (st = dalloc(b, &d.grp_cnt, S * MAX_TERMS)) ||
+        (st = dalloc(b, &d.grp_scale, S * MAX_TERMS)) || (st = dalloc(b, &d.grp_clbits, S * MAX_TERMS)) ||
+        (st = dalloc(b, &d.free_slots, b->n_slots)) || (st = dalloc(b, &d.wait_shots, S)) ||
+        (st = dalloc(b, &d.partials, (size_t)b->n_slots * max_chunks * MAX_RED)) || (st = dalloc(b, &d.keys, S)) ||
+        (st = dalloc(b, &d.pass_log, 1 << 20))) {
+        sv_free_batch(b);
+        return st;
+    }
+    b->pool_cap = 1 << 22;
+    b->ipool_cap = 1 << 20;
+    if (cudaMalloc(&b->d_pool, b->pool_cap * 8) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_ipool, b->ipool_cap * 4) != cudaSuccess ||
+        cudaMallocHost(&b->h_pool, b->pool_cap * 8) != cudaSuccess ||
+        cudaMallocHost((void**)&b->h_ipool, b->ipool_cap * 4) != cudaSuccess) {
+        cudaGetLastError();
+        sv_free_batch(b);
+        return fail(SV_ENOMEM, "cannot allocate the constant pool");
+    }
+    d.pool = b->d_pool;
+    d.ipool = b->d_ipool;
+    d.pass_log_cap = 1 << 20;
+    if (init_kernels() != cudaSuccess) {
+        sv_free_batch(b);
+        return fail(SV_ECUDA, "cannot configure the kernels");
+    }
+    cudaMemsetAsync(d.ctl, 0, CTL_WORDS * 4, b->stream);
+    *out = b;
+    return SV_OK;
+}
+
+sv_status sv_free_batch(sv_batch b) {
+    if (!b) return SV_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    for (auto& e : b->prof_ev) {
+        cudaEventDestroy(e.second.first);
+        cudaEventDestroy(e.second.second);
+    }
+    for (void* p : b->allocs) cudaFree(p);
+    if (b->d_pool) cudaFree(b->d_pool);
+    if (b->d_ipool) cudaFree(b->d_ipool);
+    if (b->h_pool) cudaFreeHost(b->h_pool);
+    if (b->h_ipool) cudaFreeHost(b->h_ipool);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return SV_OK;
+}
+
+sv_status sv_set_option(sv_batch b, sv_option opt, int64_t v) {
+    if (!b) return fail(SV_EINVAL, "batch is NULL");
+    switch (opt) {
+    case SV_OPT_LOG:
+        if (v && !b->dev.fork_log) {
+            b->dev.fork_log_cap = (int)std::min<uint64_t>(4 * b->n_shots + 1024, 1 << 24);
+            sv_status st = dalloc(b, &b->dev.fork_log, 5 * (size_t)b->dev.fork_log_cap);
+            if (st) return st;
+        }
+        b->log = v != 0;
+        if (!v) b->dev.fork_log = nullptr;
+        return SV_OK;
+    case SV_OPT_TILE_BITS:
+        if (v && (v < 2 || v > MAX_TILE_BITS)) return fail(SV_EINVAL, "tile bits must be 2..12");
+        if (b->started) return fail(SV_EINVAL, "set the tile size before the first op");
+        b->tb = std::min<int>(b->n, v ? (int)v : (b->prec == SV_C128 ? 10 : 11));
+        b->chunks = (int)std::min<int64_t>(1ll << (b->n - b->tb), b->dev.max_chunks);
+        return SV_OK;
+    case SV_OPT_MAX_ACTIVE: b->max_active = v ? (int)std::max<int64_t>(4, v) : 8; return SV_OK;
+    case SV_OPT_MAX_STAGES: b->max_stages = v ? (int)std::min<int64_t>(std::max<int64_t>(v, 1), MAX_STAGES) : MAX_STAGES; return SV_OK;
+    case SV_OPT_THREADS:
+        if (v && v != 128 && v != 256) return fail(SV_EINVAL, "threads must be 128 or 256");
+        b->threads = v ? (int)v : 256;
+        return SV_OK;
+    case SV_OPT_GRID: b->grid_pass = (int)std::max<int64_t>(0, v); return SV_OK;
+    case SV_OPT_PROFILE: b->profile = v != 0; return SV_OK;
+    case SV_OPT_UPLOAD: b->upload_each = v != 0; return SV_OK;
+    case SV_OPT_SLOT_LIMIT:
+        if (v < 0) return fail(SV_EINVAL, "slot limit must be >= 0");
+        b->slot_limit = (int)v;
+        if (v && b->branch) b->dev.n_slots = std::min<int>(b->n_slots, (int)v);
+        else b->dev.n_slots = b->n_slots;
+        return SV_OK;
+    }
+    return fail(SV_EINVAL, "unknown option");
+}
+
+sv_status sv_apply_gate_batch(sv_batch b, int k, const int* qubits, const double* mat, int cond_clbit, int cond_value) {
+    if (!b) return fail(SV_EINVAL, "batch is NULL");
+    if (b->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "plain mode runs whole circuits (sv_run_circuit)");
+    sv_status st = op_gate(b, k, qubits, mat, cond_clbit, cond_value);
+    if (st) return st;
+    return upload_pool(b);
+}
+
+sv_status sv_sample_noise(sv_batch b, uint32_t op, sv_noise_kind kind, int k, const int* qubits, int n_terms,
+                          const double* cum_probs, const char* paulis, const double* kraus) {
+    if (!b) return fail(SV_EINVAL, "batch is NULL");
+    if (b->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "plain mode runs whole circuits (sv_run_circuit)");
+    if (kind == SV_NOISE_PAULI) return op_pauli(b, op, k, qubits, n_terms, cum_probs, paulis);
+    if (kind == SV_NOISE_KRAUS) return op_kraus(b, op, k, qubits, n_terms, kraus);
+    return fail(SV_EINVAL, "unknown noise kind");
+}
+
+sv_status sv_measure_batch(sv_batch b, uint32_t op, int m, const int* qubits, const int* clbits, int reset) {
+    if (!b) return fail(SV_EINVAL, "batch is NULL");
+    if (b->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "plain mode runs whole circuits (sv_run_circuit)");
+    return op_measure(b, op, m, qubits, clbits, reset);
+}
+
+sv_status sv_branch(sv_batch b, uint32_t op) {
+    if (!b) return fail(SV_EINVAL, "batch is NULL");
+    if (b->last_random != op) return fail(SV_EINVAL, "op is not the last random op sampled");
+    return SV_OK;
+}
+
+sv_status sv_get_keys(sv_batch b, uint64_t* keys) {
+    if (!b || !keys) return fail(SV_EINVAL, "NULL argument");
+    CU(cudaMemcpyAsync(keys, b->dev.keys, b->n_shots * 8, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return check_device_error(b);
+}
+
+static sv_status histogram(sv_batch b, uint64_t* keys, uint64_t* counts, uint64_t cap, uint64_t* n_out) {
+    int32_t ctl[CTL_WORDS];
+    sv_status st = read_ctl(b, ctl);
+    if (st) return st;
+    std::vector<uint64_t> k(b->n_shots);
+    CU(cudaMemcpyAsync(k.data(), b->dev.keys, b->n_shots * 8, cudaMemcpyDeviceToHost, b->stream));
+    std::vector<uint32_t> perm(b->n_shots);
+    std::vector<int32_t> start(ctl[CTL_NBR]), cnt(ctl[CTL_NBR]);
+    CU(cudaMemcpyAsync(perm.data(), b->dev.perm, b->n_shots * 4, cudaMemcpyDeviceToHost, b->stream));
+    if (ctl[CTL_NBR] > 0) {
+        CU(cudaMemcpyAsync(start.data(), b->dev.br_start, 4 * ctl[CTL_NBR], cudaMemcpyDeviceToHost, b->stream));
+        CU(cudaMemcpyAsync(cnt.data(), b->dev.br_count, 4 * ctl[CTL_NBR], cudaMemcpyDeviceToHost, b->stream));
+    }
+    CU(cudaStreamSynchronize(b->stream));
+    std::vector<uint64_t> live;
+    for (int br = 0; br < ctl[CTL_NBR]; ++br)
+        for (int i = 0; i < cnt[br]; ++i) live.push_back(k[perm[start[br] + i]]);
+    std::sort(live.begin(), live.end());
+    uint64_t n = 0;
+    for (size_t i = 0; i < live.size();) {
+        size_t j = i;
+        while (j < live.size() && live[j] == live[i]) ++j;
+        if (n >= cap) return fail(SV_EINVAL, "cap too small for the histogram");
+        keys[n] = live[i];
+        counts[n] = j - i;
+        ++n;
+        i = j;
+    }
+    *n_out = n;
+    return SV_OK;
+}
+
+sv_status sv_counts(sv_batch b, uint32_t final_op, uint64_t* keys, uint64_t* counts, uint64_t cap, uint64_t* n_out) {
+    if (!b || !keys || !counts || !n_out) return fail(SV_EINVAL, "NULL argument");
+    if (b->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "plain mode runs whole circuits (sv_run_circuit)");
+    sv_status st = op_final(b, final_op);
+    if (st) return st;
+    if ((st = check_device_error(b))) return st;
+    return histogram(b, keys, counts, cap, n_out);
+}
+
+sv_status sv_waiting(sv_batch b, uint64_t* n_waiting) {
+    if (!b || !n_waiting) return fail(SV_EINVAL, "NULL argument");
+    int32_t ctl[CTL_WORDS];
+    sv_status st = read_ctl(b, ctl);
+    if (st) return st;
+    *n_waiting = (uint64_t)ctl[CTL_NWAIT];
+    return SV_OK;
+}
+
+sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
+    if (!b || !c) return fail(SV_EINVAL, "NULL argument");
+    if (c->n_qubits != b->n) return fail(SV_EINVAL, "circuit qubit count differs from the batch");
+    if (c->n_clbits > b->n_clbits) return fail(SV_EINVAL, "circuit needs more classical bits than the batch");
+    sv_status st;
+    if (!b->pend.empty()) return fail(SV_EINVAL, "per-op calls are in progress on this batch");
+    if (b->mode == SV_PLAIN) {
+        b->started = true;
+        if ((st = reset_pool(b))) return st;
+        if ((st = run_plain(b, c))) return st;
+        return check_device_error(b);
+    }
+    // launch list of the op sequence (after the reset / init of the root)
+    const uint64_t h = circuit_hash(b, c);
+    const bool cached = use_graph && b->graph_exec && b->graph_hash == h;
+    std::vector<Launch> launches;
+    if (!cached) {
+        if ((st = reset_pool(b))) return st;
+        b->started = true;  // reset / init are issued below, per run
+        b->rec = &launches;
+        b->n_pend = 0;
+        for (int i = 0; i < c->n_ops && !st; ++i) st = circuit_op(b, c, i);
+        if (!st) st = flush(b);
+        b->rec = nullptr;
+        if (st) return st;
+        if ((st = upload_pool(b))) return st;
+    }
+    if (cached && b->upload_each) {
+        // the circuit's constants cross the bus again (end-to-end timing)
+        b->pool_up = 0;
+        b->ipool_up = 0;
+        if ((st = upload_pool(b))) return st;
+    }
+    const int branch = b->branch;
+    int from_wait = 0;
+    int n_run = (int)b->n_shots;
+    for (int round = 0;; ++round) {
+        Launch r;
+        r.type = L_RESET;
+        r.a0 = branch;
+        r.a1 = n_run;
+        r.a2 = from_wait;
+        if ((st = exec(b, r))) return st;
+        Launch in;
+        in.type = L_INIT;
+        in.a0 = branch ? 1 : n_run;
+        if ((st = exec(b, in))) return st;
+        if (use_graph) {
+            if (!cached && round == 0) {
+                if (b->graph_exec) {
+                    cudaGraphExecDestroy(b->graph_exec);
+                    b->graph_exec = nullptr;
+                }
+                cudaGraph_t g;
+                CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                for (const Launch& L : launches) {
+                    cudaError_t e = exec_one(b, L);
+                    if (e != cudaSuccess) {
+                        cudaStreamEndCapture(b->stream, &g);
+                        return fail(SV_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+                    }
+                }
+                CU(cudaStreamEndCapture(b->stream, &g));
+                CU(cudaGraphInstantiate(&b->graph_exec, g, 0));
+                cudaGraphDestroy(g);
+                b->graph_hash = h;
+                int64_t nl = 0;
+                for (const Launch& L : launches) nl += (L.type == L_FINAL) ? 2 : 1;
+                b->graph_launches = nl;
+                b->graph_pass_store.clear();
+                for (const Launch& L : launches)
+                    if (L.type == L_PASS) b->graph_pass_store.push_back(L.pass.store ? 1 : 0);
+            }
+            CU(cudaGraphLaunch(b->graph_exec, b->stream));
+            b->n_launch += b->graph_launches;
+            b->n_passes += b->graph_pass_store.size();
+            b->pass_store.insert(b->pass_store.end(), b->graph_pass_store.begin(), b->graph_pass_store.end());
+        } else {
+            for (const Launch& L : launches)
+                if ((st = exec(b, L))) return st;
+        }
+        if (!branch) break;
+        int32_t ctl[CTL_WORDS];
+        if ((st = read_ctl(b, ctl))) return st;
+        if (ctl[CTL_ERR]) break;
+        if (ctl[CTL_NWAIT] == 0) break;
+        // waiting list (Section IV-B-2): restart its shots from |0...0>
+        n_run = ctl[CTL_NWAIT];
+        from_wait = 1;
+        b->restarts += 1;
+        if (!use_graph && launches.empty()) break;
+    }
+    b->started = false;
+    return check_device_error(b);
+}
+
+sv_status sv_get_amplitudes(sv_batch b, uint64_t shot, double* out, uint64_t len) {
+    if (!b || !out) return fail(SV_EINVAL, "NULL argument");
+    if (len != (uint64_t)b->dim) return fail(SV_EINVAL, "len must be 2^n");
+    if (shot >= b->n_shots) return fail(SV_EINVAL, "shot out of range");
+    sv_status st = upload_pool(b);
+    if (st) return st;
+    if ((st = flush(b))) return st;
+    int32_t ctl[CTL_WORDS];
+    if ((st = read_ctl(b, ctl))) return st;
+    const int nb = ctl[CTL_NBR];
+    std::vector<uint32_t> perm(b->n_shots);
+    std::vector<int32_t> start(nb), cnt(nb), slot(nb);
+    CU(cudaMemcpyAsync(perm.data(), b->dev.perm, b->n_shots * 4, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaMemcpyAsync(start.data(), b->dev.br_start, 4 * nb, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaMemcpyAsync(cnt.data(), b->dev.br_count, 4 * nb, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaMemcpyAsync(slot.data(), b->dev.br_slot, 4 * nb, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    int sl = -1;
+    for (int br = 0; br < nb && sl < 0; ++br)
+        for (int i = 0; i < cnt[br]; ++i)
+            if (perm[start[br] + i] == shot) {
+                sl = slot[br];
+                break;
+            }
+    if (sl < 0) return fail(SV_EINVAL, "shot is not in a live branch (waiting list)");
+    if (b->prec == SV_C128) {
+        CU(cudaMemcpyAsync(out, (char*)b->dev.states + (size_t)sl * b->state_bytes, b->state_bytes,
+                           cudaMemcpyDeviceToHost, b->stream));
+        CU(cudaStreamSynchronize(b->stream));
+    } else {
+        std::vector<float> tmp(2 * b->dim);
+        CU(cudaMemcpyAsync(tmp.data(), (char*)b->dev.states + (size_t)sl * b->state_bytes, b->state_bytes,
+                           cudaMemcpyDeviceToHost, b->stream));
+        CU(cudaStreamSynchronize(b->stream));
+        for (int64_t i = 0; i < 2 * b->dim; ++i) out[i] = tmp[i];
+    }
+    return check_device_error(b);
+}
+
+sv_status sv_get_outcomes(sv_batch b, uint32_t op, int32_t* sel, double* thr) {
+    if (!b || !sel) return fail(SV_EINVAL, "NULL argument");
+    auto it = b->logs.find(op);
+    if (it == b->logs.end()) return fail(SV_EINVAL, "no log for this op (enable SV_OPT_LOG before sampling)");
+    CU(cudaMemcpyAsync(sel, it->second.first, b->n_shots * 4, cudaMemcpyDeviceToHost, b->stream));
+    if (thr) CU(cudaMemcpyAsync(thr, it->second.second, b->n_shots * 16, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return SV_OK;
+}
+
+sv_status sv_get_fork_events(sv_batch b, int64_t* ev, uint64_t cap, uint64_t* n_out) {
+    if (!b || !n_out) return fail(SV_EINVAL, "NULL argument");
+    if (!b->dev.fork_log) return fail(SV_EINVAL, "enable SV_OPT_LOG first");
+    int32_t ctl[CTL_WORDS];
+    sv_status st = read_ctl(b, ctl);
+    if (st) return st;
+    const uint64_t n = std::min<uint64_t>(ctl[CTL_NFORK], b->dev.fork_log_cap);
+    *n_out = n;
+    if (n > cap) return fail(SV_EINVAL, "cap too small");
+    if (n && ev) {
+        CU(cudaMemcpyAsync(ev, b->dev.fork_log, n * 5 * 8, cudaMemcpyDeviceToHost, b->stream));
+        CU(cudaStreamSynchronize(b->stream));
+    }
+    return SV_OK;
+}
+
+sv_status sv_stats(sv_batch b, double* s) {
+    if (!b || !s) return fail(SV_EINVAL, "NULL argument");
+    int32_t ctl[CTL_WORDS];
+    sv_status st = read_ctl(b, ctl);
+    if (st) return st;
+    // algorithmic bytes of the passes since the last call: every live state
+    // read once, and written once when the pass applies ops
+    const int np = std::min<int>(ctl[CTL_NPASS], b->dev.pass_log_cap);
+    std::vector<int32_t> nbr(np);
+    if (np) CU(cudaMemcpy(nbr.data(), b->dev.pass_log, 4 * np, cudaMemcpyDeviceToHost));
+    double bytes = 0;
+    for (int i = 0; i < np && i < (int)b->pass_store.size(); ++i)
+        bytes += (double)nbr[i] * (double)b->state_bytes * (1.0 + b->pass_store[i]);
+    s[0] = ctl[CTL_NBR];
+    s[1] = ctl[CTL_NWAIT];
+    s[2] = (double)b->n_launch;
+    s[3] = (double)b->n_passes;
+    s[4] = bytes;
+    s[5] = (double)ctl[CTL_NCOPIED] * 2.0 * (double)b->state_bytes;
+    s[6] = (double)b->restarts;
+    s[7] = b->h2d_bytes;
+    b->h2d_bytes = 0;
+    b->n_launch = 0;
+    b->n_passes = 0;
+    b->restarts = 0;
+    b->pass_store.clear();
+    const int32_t zero[2] = {0, 0};
+    CU(cudaMemcpyAsync(b->dev.ctl + CTL_NPASS, zero, 8, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return SV_OK;
+}
+
+sv_status sv_profile(sv_batch b, double* ms, int64_t* cnt) {
+    if (!b || !ms || !cnt) return fail(SV_EINVAL, "NULL argument");
+    CU(cudaStreamSynchronize(b->stream));
+    for (auto& e : b->prof_ev) {
+        float t = 0;
+        cudaEventElapsedTime(&t, e.second.first, e.second.second);
+        b->prof_ms[e.first] += t;
+        b->prof_cnt[e.first] += 1;
+        cudaEventDestroy(e.second.first);
+        cudaEventDestroy(e.second.second);
+    }
+    b->prof_ev.clear();
+    double tot = 0;
+    for (int i = 0; i < 7; ++i) {
+        ms[i] = b->prof_ms[i];
+        cnt[i] = b->prof_cnt[i];
+        tot += ms[i];
+        b->prof_ms[i] = 0;
+        b->prof_cnt[i] = 0;
+    }
+    ms[7] = tot;
+    cnt[7] = 0;
+    return SV_OK;
+}
+
+sv_status sv_sync(sv_batch b, uint64_t timeout_ns) {
+    if (!b) return fail(SV_EINVAL, "batch is NULL");
+    if (timeout_ns == 0) {
+        CU(cudaStreamSynchronize(b->stream));
+        return check_device_error(b);
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    while (cudaStreamQuery(b->stream) == cudaErrorNotReady) {
+        const auto dt = std::chrono::steady_clock::now() - t0;
+        if ((uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(dt).count() > timeout_ns)
+            return fail(SV_ETIMEOUT, "stream did not finish in time");
+    }
+    return check_device_error(b);
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+"""Comparison of the CUDA path with the oracle, shot by shot (test helper).
+
+Rules (bit-exactness with explained mismatches):
+* Pauli choices must match exactly: both sides compare the same float64 draw
+  with the same cumulative table.
+* Kraus, measurement and final-sample choices compare u against thresholds
+  computed from the state.  A mismatch is *flagged* (not failed) only when
+  the two sides' values of the boundary threshold between the two outcomes
+  differ by at most tol_c and u lies between them (1e-9 padding); the
+  oracle then follows the GPU's choice (override) and the comparison goes on.
+* Final amplitudes agree within tol_amp along the matched history.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import oracle as O
+from paper_2308_03399_gb300 import sv
+from paper_2308_03399_gb300 import workloads as W
+
+TOL = {sv.SV_C128: dict(c=1e-10, amp=1e-12), sv.SV_C64: dict(c=1e-5, amp=1e-5)}
+
+
+def run_gpu(circ, seed, n_shots, mode, prec, use_graph=True, opts=None, want_amps=(), log=True):
+    arrays = circ.to_arrays()
+    cs = sv.circuit_struct(arrays)
+    with sv.Batch(circ.n_qubits, n_shots, max(1, circ.n_clbits), prec, mode, seed) as b:
+        if log:
+            b.set_option(sv.SV_OPT_LOG, 1)
+        for k, v in (opts or {}).items():
+            b.set_option(k, v)
+        b.run_circuit(cs, use_graph=use_graph)
+        res = dict(keys=b.get_keys(), stats=b.stats())
+        if log:
+            res["sel"], res["thr"] = {}, {}
+            for op in circ.random_ops():
+                s, t = b.get_outcomes(op, thresholds=True)
+                res["sel"][op], res["thr"][op] = s, t
+            if mode in (sv.SV_BRANCH, sv.SV_BATCH_BRANCH):
+                res["forks"] = b.get_fork_events()
+        res["amps"] = {s: b.get_amplitudes(s) for s in want_amps}
+    return res
+
+
+def compare_shots(circ, seed, gpu, shots, prec, check_amps=True):
+    """Compare the GPU's logs of `shots` with the oracle.  Returns counts of
+    checked draws and flagged draws; raises AssertionError on an unexplained
+    mismatch."""
+    tol = TOL[prec]
+    oc = O.OracleCircuit(circ)
+    kinds = circ.to_arrays()["kind"]
+    rops = circ.random_ops()
+    n_draws = n_flag = 0
+    for s in shots:
+        overrides = {}
+        ref = O.run_shot(oc, seed, int(s))
+        for op in rops:
+            g = int(gpu["sel"][op][s])
+            c = int(ref["outcome"][op])
+            n_draws += 1
+            if g == c:
+                continue
+            assert kinds[op] != W.PAULI, f"shot {s} op {op}: Pauli choice {g} != oracle {c}"
+            glo, ghi = gpu["thr"][op][s]
+            if g < c:
+                bg, bc = ghi, ref["c_lo"][op]
+            else:
+                bg, bc = glo, ref["c_hi"][op]
+            u = ref["u"][op]
+            ok = abs(bg - bc) <= tol["c"] and min(bg, bc) - 1e-9 <= u <= max(bg, bc) + 1e-9
+            assert ok, (f"shot {s} op {op} kind {kinds[op]}: GPU {g} (thr {glo:.17g},{ghi:.17g}) vs oracle {c} "
+                        f"(thr {ref['c_lo'][op]:.17g},{ref['c_hi'][op]:.17g}) u={u:.17g}")
+            n_flag += 1
+            overrides[op] = g
+            ref = O.run_shot(oc, seed, int(s), overrides=overrides)
+        fin = [op for op in rops if kinds[op] == W.FINAL]
+        if fin:
+            assert int(gpu["keys"][s]) == int(gpu["sel"][fin[0]][s])
+        if check_amps and s in gpu.get("amps", {}):
+            st = O.run_shot(oc, seed, int(s), overrides=overrides, want_state=True)["state"]
+            err = np.abs(gpu["amps"][s] - st).max()
+            assert err <= tol["amp"], f"shot {s}: amplitude error {err:.3g} > {tol['amp']}"
+    return n_draws, n_flag
+
+
+def gpu_tree_records(forks):
+    """Fork events grouped per (op, parent): sorted (outcome, shots) lists."""
+    by = {}
+    for op, parent, child, outcome, cnt in forks.tolist():
+        by.setdefault((op, parent), []).append((outcome, cnt))
+    return sorted((op, tuple(sorted(v))) for (op, _), v in by.items())
+
+
+def canonical_tree_records(sel, rops, n_shots):
+    """The canonical tree (oracle.branch_tree) of the same logs in the same
+    grouped form."""
+    kinds_final = set()
+    outc = np.full((n_shots, max(rops) + 1), -1, np.int64)
+    for op in rops:
+        outc[:, op] = sel[op]
+    recs = O.branch_tree(outc, rops)
+    by = {}
+    for op, parent, child, outcome in recs:
+        by.setdefault((op, parent), []).append((outcome, len(child)))
+    del kinds_final
+    return sorted((op, tuple(sorted(v))) for (op, _), v in by.items())

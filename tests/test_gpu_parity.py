@@ -1,0 +1,170 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every case runs on seeded synthetic circuits and compares, shot by shot, the
+GPU's choice for every random op with the oracle's (Pauli exactly; state-
+dependent choices exactly unless flagged by the threshold rule), the final
+keys, and the final amplitudes (1e-12 complex128, 1e-5 complex64)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2308_03399_gb300 import sv
+from paper_2308_03399_gb300 import workloads as W
+from tests.parity import canonical_tree_records, compare_shots, gpu_tree_records, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+MODES = [sv.SV_BATCH, sv.SV_BRANCH]
+PRECS = [sv.SV_C64, sv.SV_C128]
+
+SMALL = {
+    "brickwork": lambda: W.brickwork(6, 6, 0.05, 0.1, seed=21),
+    "su4_kraus": lambda: W.random_su4(5, 4, 0.1, 0.1, seed=22),
+    "midmeasure": lambda: W.midcircuit_measure(6, 3, 0.05, [0, 3], seed=23),
+    "qft_kraus": lambda: W.qft(5, 0.05, seed=24, kraus=True),
+}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", list(SMALL))
+def test_small_circuits_match_oracle(name, mode, prec):
+    c = SMALL[name]()
+    n_shots = 300
+    gpu = run_gpu(c, 7, n_shots, mode, prec, want_amps=range(0, n_shots, 37))
+    n, flagged = compare_shots(c, 7, gpu, range(n_shots), prec)
+    assert flagged <= max(2, n // 1000)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_and_branch_logs_identical(prec):
+    c = W.random_su4(6, 5, 0.08, 0.1, seed=31)
+    a = run_gpu(c, 3, 400, sv.SV_BATCH, prec)
+    b = run_gpu(c, 3, 400, sv.SV_BRANCH, prec)
+    assert np.array_equal(a["keys"], b["keys"])
+    for op in c.random_ops():
+        assert np.array_equal(a["sel"][op], b["sel"][op]), op
+        assert np.array_equal(a["thr"][op], b["thr"][op]), op
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fork_events_form_the_canonical_tree(prec):
+    c = W.midcircuit_measure(5, 3, 0.05, [1, 3], seed=41)
+    n_shots = 500
+    gpu = run_gpu(c, 5, n_shots, sv.SV_BRANCH, prec)
+    rops = [op for op in c.random_ops() if c.ops[op].kind != W.FINAL]
+    assert gpu_tree_records(gpu["forks"]) == canonical_tree_records(gpu["sel"], rops, n_shots)
+    compare_shots(c, 5, gpu, range(0, n_shots, 7), prec, check_amps=False)
+
+
+@pytest.mark.parametrize("prec,n", [(sv.SV_C64, 14), (sv.SV_C128, 13)])
+def test_several_tiles_and_chunks(prec, n):
+    # 8 tiles per state: stages and reductions span tile and chunk borders
+    c = W.random_su4(n, 3, 0.05, 0.05, seed=51)
+    gpu = run_gpu(c, 9, 40, sv.SV_BRANCH, prec, want_amps=[0, 17, 39])
+    compare_shots(c, 9, gpu, range(40), prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_tiles_force_many_passes(prec):
+    # 4-amplitude tiles: almost every op gets its own pass
+    c = W.brickwork(7, 4, 0.05, 0.1, seed=61)
+    gpu = run_gpu(c, 2, 120, sv.SV_BATCH, prec, opts={sv.SV_OPT_TILE_BITS: 3, sv.SV_OPT_MAX_ACTIVE: 4},
+                  want_amps=[0, 5])
+    compare_shots(c, 2, gpu, range(120), prec)
+
+
+def test_waiting_list_restarts_match_oracle():
+    c = W.random_su4(6, 4, 0.1, 0.15, seed=71)
+    gpu = run_gpu(c, 4, 200, sv.SV_BRANCH, sv.SV_C128, opts={sv.SV_OPT_SLOT_LIMIT: 3})
+    assert gpu["stats"]["restarts"] > 0
+    assert (gpu["forks"][:, 2] == -1).any()
+    compare_shots(c, 4, gpu, range(200), sv.SV_C128, check_amps=False)
+
+
+def test_plain_per_shot_form_matches_oracle():
+    c = W.midcircuit_measure(5, 2, 0.05, [0, 2], seed=81)
+    gpu = run_gpu(c, 6, 40, sv.SV_PLAIN, sv.SV_C128, log=False)
+    keys, _, _ = O.run_shots(c, 6, 0, 40, want_outcomes=False)
+    assert np.array_equal(gpu["keys"], keys)
+    c = W.random_su4(4, 3, 0.1, 0.1, seed=82)
+    gpu = run_gpu(c, 6, 40, sv.SV_PLAIN, sv.SV_C128, log=False)
+    keys, _, _ = O.run_shots(c, 6, 0, 40, want_outcomes=False)
+    assert np.array_equal(gpu["keys"], keys)
+
+
+def test_graph_and_direct_launches_agree():
+    c = W.random_su4(7, 3, 0.05, 0.1, seed=91)
+    a = run_gpu(c, 1, 100, sv.SV_BRANCH, sv.SV_C64, use_graph=True)
+    b = run_gpu(c, 1, 100, sv.SV_BRANCH, sv.SV_C64, use_graph=False)
+    assert np.array_equal(a["keys"], b["keys"])
+
+
+def test_per_op_calls_match_run_circuit():
+    c = W.midcircuit_measure(5, 2, 0.05, [1, 4], seed=92)
+    ref = run_gpu(c, 8, 64, sv.SV_BRANCH, sv.SV_C64, log=False)
+    with sv.Batch(5, 64, c.n_clbits, sv.SV_C64, sv.SV_BRANCH, 8) as b:
+        for i, o in enumerate(c.ops):
+            if o.kind == W.GATE:
+                b.apply_gate_batch(o.qubits, o.mat, o.cond_clbit, o.cond_val)
+            elif o.kind == W.PAULI:
+                b.sample_noise_pauli(i, o.qubits, o.cum, o.strings)
+                b.branch(i)
+            elif o.kind == W.MEASURE:
+                b.measure_batch(i, o.qubits, o.clbits, o.reset)
+            elif o.kind == W.FINAL:
+                cnt = b.counts(i)
+        keys = b.get_keys()
+    assert np.array_equal(keys, ref["keys"])
+    assert sum(cnt.values()) == 64
+
+
+def test_edge_cases_one_qubit_one_shot():
+    c = W.Circuit(1)
+    c.gate([0], W.H)
+    c.kraus([0], W.amplitude_damping(0.3))
+    c.depolarizing([0], 0.2)
+    c.final()
+    for mode in MODES:
+        for prec in PRECS:
+            gpu = run_gpu(c, 11, 1, mode, prec, want_amps=[0])
+            compare_shots(c, 11, gpu, [0], prec)
+
+
+def test_bad_arguments_are_rejected():
+    with sv.Batch(3, 4, 1, sv.SV_C64, sv.SV_BATCH, 1) as b:
+        with pytest.raises(sv.SvError):
+            b.apply_gate_batch([3], np.eye(2))
+        with pytest.raises(sv.SvError):
+            b.apply_gate_batch([0, 0], np.eye(4))
+        with pytest.raises(sv.SvError):
+            b.apply_gate_batch([0], np.array([[1, 1], [0, 1]]))
+        with pytest.raises(sv.SvError):
+            b.sample_noise_kraus(0, [0], [np.eye(2) * 0.5])
+    with pytest.raises(sv.SvError):
+        sv.Batch(31, 1)
+
+
+def test_config1_all_shots_complex128():
+    c = W.config1()
+    gpu = run_gpu(c, 1, 1000, sv.SV_BATCH, sv.SV_C128, want_amps=[0, 999])
+    n, flagged = compare_shots(c, 1, gpu, range(1000), sv.SV_C128)
+    assert flagged == 0
+
+
+def test_config2_sampled_shots_and_tree():
+    c = W.config2()
+    n_shots = 10_000
+    gpu = run_gpu(c, 2, n_shots, sv.SV_BRANCH, sv.SV_C64, want_amps=[0, 4321])
+    rng = np.random.default_rng(0)
+    shots = sorted(set(rng.choice(n_shots, 12, replace=False).tolist()) | {0, 4321})
+    compare_shots(c, 2, gpu, shots, sv.SV_C64)
+    rops = [op for op in c.random_ops() if c.ops[op].kind != W.FINAL]
+    assert gpu_tree_records(gpu["forks"]) == canonical_tree_records(gpu["sel"], rops, n_shots)
+
+
+def test_config3_sampled_shots():
+    c = W.config3()
+    n_shots = 256
+    gpu = run_gpu(c, 3, n_shots, sv.SV_BRANCH, sv.SV_C64, want_amps=[0])
+    compare_shots(c, 3, gpu, [0, 101, 255], sv.SV_C64)
