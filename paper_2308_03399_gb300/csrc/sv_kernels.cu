@@ -381,6 +381,11 @@ __global__ void __launch_bounds__(256) k_pass(DevBatch d, const __grid_constant_
 
     const int tb = p.tb, run = p.run_bits;
     const int tsize = 1 << tb;
+    // complex64 tiles need qubit 0 inside the tile (pairs move as 128 bits)
+    if (sizeof(T) == 8 && run < 1) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(d, ERR_INDEX, -1);
+        return;
+    }
     const int run_mask = (1 << run) - 1;
     const int n_hi = 1 << (tb - run);
     for (int h = threadIdx.x; h < n_hi; h += blockDim.x) {

@@ -290,7 +290,9 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
     p.tb = b->tb;
     uint64_t act = b->active;
     for (int j = 0; j < red.k; ++j) act |= 1ull << red.q[j];
-    // tile qubits: every active qubit plus the lowest others
+    // tile qubits: qubit 0 (complex64 tiles move amplitude pairs 2j, 2j+1
+    // with one 128-bit access), every active qubit, then the lowest others
+    act |= 1ull;
     std::vector<int> tq;
     for (int q = 0; q < b->n; ++q)
         if ((act >> q) & 1) tq.push_back(q);
@@ -345,12 +347,16 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
 
 sv_status flush(sv_batch b) { return emit_pass(b, RedSpec()); }
 
+// qubits of a pass fit one tile (which always holds qubit 0)
+bool fits(sv_batch b, uint64_t act) {
+    return __builtin_popcountll(act | 1ull) <= b->tb && __builtin_popcountll(act) <= b->max_active;
+}
+
 // make room for a stage on qubits q[0..k-1] with `mats` matrix entries
 sv_status make_room(sv_batch b, const int* q, int k, int mats, bool needs_pend) {
     uint64_t act = b->active;
     for (int j = 0; j < k; ++j) act |= 1ull << q[j];
-    const int limit = std::min(b->max_active, b->tb);
-    if (__builtin_popcountll(act) > limit || (int)b->pend.size() >= b->max_stages ||
+    if (!fits(b, act) || (int)b->pend.size() >= b->max_stages ||
         b->mat_used + mats > MAT_SMEM - 256 || (needs_pend && b->n_pend >= MAX_PEND))
         return flush(b);
     return SV_OK;
@@ -554,8 +560,7 @@ sv_status op_kraus(sv_batch b, uint32_t op, int k, const int* q, int n_terms, co
     // the reduction must see every earlier op: queued stages + forms in one pass
     uint64_t act = b->active;
     for (int j = 0; j < k; ++j) act |= 1ull << q[j];
-    if (__builtin_popcountll(act) > std::min(b->max_active, b->tb) ||
-        b->mat_used + n_terms * E > MAT_SMEM - 256)
+    if (!fits(b, act) || b->mat_used + n_terms * E > MAT_SMEM - 256)
         if ((st = flush(b))) return st;
     RedSpec red;
     red.kind = RED_FORMS;
@@ -593,7 +598,7 @@ sv_status op_measure(sv_batch b, uint32_t op, int m, const int* q, const int* cl
     if ((st = ensure_started(b))) return st;
     uint64_t act = b->active;
     for (int j = 0; j < m; ++j) act |= 1ull << q[j];
-    if (__builtin_popcountll(act) > std::min(b->max_active, b->tb))
+    if (!fits(b, act))
         if ((st = flush(b))) return st;
     RedSpec red;
     red.kind = RED_BINS;
