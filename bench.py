@@ -163,6 +163,8 @@ def main():
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-shots", type=int, default=32)
+    ap.add_argument("--shots", type=int, default=0, help="override the workload's shot count (profiling)")
+    ap.add_argument("--timed-only", action="store_true", help="skip the end-to-end and roofline phases")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -183,6 +185,8 @@ def main():
     from paper_2308_03399_gb300 import sv
 
     circ, n_shots, seed = workload(args.workload)
+    if args.shots:
+        n_shots = args.shots
     seed = seed + 1000 * rank  # replicas: every rank its own independent shots
     mode = {"branch": sv.SV_BRANCH, "batch": sv.SV_BATCH, "plain": sv.SV_PLAIN}[args.mode]
     prec = {"c64": sv.SV_C64, "c128": sv.SV_C128}[args.prec]
@@ -226,6 +230,12 @@ def main():
         total_ms = float(t.item())
     value = n_shots * world * args.steps / (total_ms / 1e3)
     launches_per_step = st["launches"] / args.steps
+    if args.timed_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "shots/s", "ms_per_step": total_ms / args.steps,
+                              "shots": n_shots, "workload": circ.name, "clocks": clk}), flush=True)
+        b.close()
+        return
 
     # ---- end to end through the public API with host buffers -----------------
     b.set_option(sv.SV_OPT_UPLOAD, 1)

@@ -107,6 +107,7 @@ struct DevBatch {
     double* grp_scale;
     uint64_t* grp_clbits;
     int32_t* free_slots;
+    int32_t* fork_list;        // branches that fork at the current random op
     uint32_t* wait_shots;
     double* partials;          // [n_slots][max_chunks][MAX_RED]
     int32_t max_chunks;
@@ -131,6 +132,7 @@ enum : int32_t {
     CTL_NFORK = 7,      // fork events logged
     CTL_NPASS = 8,      // passes logged
     CTL_NCOPIED = 9,    // branches created by forks (each one state copy)
+    CTL_NFL = 10,       // forking branches listed by the last decide
     CTL_WORDS = 16
 };
 

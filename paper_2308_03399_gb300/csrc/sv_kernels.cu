@@ -32,6 +32,8 @@
 
 namespace sv {
 
+constexpr int PASS_NBUF_H = 4;  // ring buffers of k_pass (PASS_NBUF below)
+
 template <class R> struct Cplx;
 template <> struct Cplx<float> { using T = float2; };
 template <> struct Cplx<double> { using T = double2; };
@@ -280,6 +282,14 @@ __device__ __forceinline__ void acc_add(double* a, double x) { *a += x; }
 __device__ __forceinline__ double acc_get(float2 a) { return (double)a.x + (double)a.y; }
 __device__ __forceinline__ double acc_get(double a) { return a; }
 
+// shared-memory layout of k_pass: ring buffers | matrices | accumulators |
+// run offsets | mbarriers
+__host__ __device__ inline size_t pass_bytes_before_bars(const PassDesc& p, int threads, size_t amp) {
+    const size_t acc = p.red_kind != RED_NONE ? (size_t)p.red_R * threads * 8 : 0;
+    return (size_t)PASS_NBUF_H * ((size_t)1 << p.tb) * amp + (size_t)p.mat_elems * amp + acc +
+           ((size_t)1 << (p.tb - p.run_bits)) * 4;
+}
+
 // Kraus probabilities: quadratic forms v^dagger F_i v over groups of the
 // Kraus qubits, F_i = K_i^dagger K_i (Section III-B-2 / IV-A-4)
 template <class R, int K>
@@ -364,254 +374,352 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // ---------------------------------------------------------------------------
-// k_pass
+// bulk asynchronous copies (TMA bulk engine) and mbarriers
 // ---------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(256) k_pass(DevBatch d, const __grid_constant__ PassDesc p) {
-    using T = typename Cplx<R>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* tile = reinterpret_cast<T*>(smem_raw);
-    T* mats = tile + (1 << p.tb);
-    using A = typename AccSlot<R>::T;
-    A* acc = reinterpret_cast<A*>(mats + p.mat_elems);
-    int* hi_tab = reinterpret_cast<int*>(acc + (p.red_kind != RED_NONE ? p.red_R * blockDim.x : 0));
-    __shared__ int skip[MAX_STAGES], sel_sh[MAX_STAGES], packed_sh[MAX_STAGES];
-    __shared__ double scale_sh[MAX_STAGES];
-    __shared__ double red_sh[32];
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: gives up (error word) instead of spinning forever
+__device__ __forceinline__ bool mbar_wait(const DevBatch& d, uint64_t* bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 24); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    set_err(d, ERR_TIMEOUT, 1);
+    return false;
+}
 
+// ---------------------------------------------------------------------------
+// k_pass: every CTA owns a contiguous range of (branch, chunk) units and
+// streams their tiles through a ring of PASS_NBUF shared-memory buffers.
+// Warp 0 fetches tile k+2 with bulk copies (one per contiguous run of the
+// tile) while all warps apply the stages to tile k; finished tiles go back
+// with bulk stores.  Reductions accumulate per thread and are combined per
+// chunk in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int PASS_NBUF = PASS_NBUF_H;
+constexpr int PASS_AHEAD = 2;
+
+template <class R>
+__global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_constant__ PassDesc p) {
+    using T = typename Cplx<R>::T;
+    using A = typename AccSlot<R>::T;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tb = p.tb, run = p.run_bits;
     const int tsize = 1 << tb;
+    const int n_runs = 1 << (tb - run);
+    const bool red = p.red_kind != RED_NONE;
+    T* bufs = reinterpret_cast<T*>(smem_raw);
+    T* mats = bufs + PASS_NBUF * tsize;
+    A* acc = reinterpret_cast<A*>(mats + p.mat_elems);
+    int* hi_tab = reinterpret_cast<int*>(acc + (red ? p.red_R * (int)blockDim.x : 0));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + ((pass_bytes_before_bars(p, blockDim.x, sizeof(T)) + 7) & ~7ull));
+    __shared__ int skip[MAX_STAGES], sel_sh[MAX_STAGES], packed_sh[MAX_STAGES];
+    __shared__ double scale_sh[MAX_STAGES];
+    __shared__ double wsum[8][MAX_RED];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
     // complex64 tiles need qubit 0 inside the tile (pairs move as 128 bits)
     if (sizeof(T) == 8 && run < 1) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_err(d, ERR_INDEX, -1);
         return;
-    }
-    const int run_mask = (1 << run) - 1;
-    const int n_hi = 1 << (tb - run);
-    for (int h = threadIdx.x; h < n_hi; h += blockDim.x) {
-        int o = 0;
-        for (int j = 0; j < tb - run; ++j)
-            if ((h >> j) & 1) o |= 1 << p.tile_q[run + j];
-        hi_tab[h] = o;
     }
     const int n_br = d.ctl[CTL_NBR];
     if (blockIdx.x == 0 && threadIdx.x == 0 && d.pass_log) {
         const int i = atomicAdd(&d.ctl[CTL_NPASS], 1);
         if (i < d.pass_log_cap) d.pass_log[i] = n_br;
     }
-    const int64_t items = (int64_t)n_br * p.chunks;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-        const int b = (int)(it / p.chunks), c = (int)(it % p.chunks);
-        const int slot = d.br_slot[b];
-        if (slot < 0 || slot >= d.n_slots) {
-            if (threadIdx.x == 0) set_err(d, ERR_SLOT, b);
-            continue;
-        }
-        const uint64_t clb = d.br_clbits[b];
-        __syncthreads();  // previous item is done with mats / skip
-        for (int s = threadIdx.x; s < p.n_stages; s += blockDim.x) {
-            const Stage& st = p.st[s];
-            int sk = 0, sel = 0, packed = 0;
-            double scale = 1.0;
-            if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val) sk = 1;
-            if (st.kind != ST_DENSE) {
-                sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
-                scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
-                if (sel < 0) sk = 1;
-                if (st.kind == ST_PAULI_BR && !sk) {
-                    packed = d.ipool[st.off + sel];
-                    if ((packed & 0xff) == 0) sk = 1;  // identity string: nothing to do
-                }
-            }
-            skip[s] = sk;
-            sel_sh[s] = sel;
-            packed_sh[s] = packed;
-            scale_sh[s] = scale;
-        }
-        __syncthreads();
-        const R* pool = reinterpret_cast<const R*>(d.pool);
-        for (int s = 0; s < p.n_stages; ++s) {
-            const Stage& st = p.st[s];
-            if (skip[s] || (st.kind != ST_DENSE && st.kind != ST_DENSE_BR)) continue;
-            const int D2 = 1 << (2 * st.k);
-            const R* src = pool + st.off + (st.kind == ST_DENSE_BR ? (int64_t)sel_sh[s] * st.stride : 0);
-            const R sc = (R)scale_sh[s];
-            for (int e = threadIdx.x; e < D2; e += blockDim.x) {
-                T m;
-                m.x = src[2 * e] * sc;
-                m.y = src[2 * e + 1] * sc;
-                mats[st.mat + e] = m;
-            }
-        }
-        if (p.red_kind == RED_FORMS) {
-            const int D2 = 1 << (2 * p.red_k);
-            const R* src = pool + p.red_off;
-            for (int e = threadIdx.x; e < p.red_R * D2; e += blockDim.x) {
-                T m;
-                m.x = src[2 * e];
-                m.y = src[2 * e + 1];
-                mats[p.mat_elems - p.red_R * D2 + e] = m;
-            }
-        }
-        __syncthreads();
+    const int64_t units = (int64_t)n_br * p.chunks;
+    const int64_t tpc = p.tiles_per_chunk;
+    const int64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
+    const int64_t t0 = u0 * tpc, nt = (u1 - u0) * tpc;
+    if (nt <= 0) return;
 
-        if (p.red_kind != RED_NONE)
-            for (int e = threadIdx.x; e < p.red_R * (int)blockDim.x; e += blockDim.x) acc[e] = A{};
-        T* gstate = reinterpret_cast<T*>(d.states) + (int64_t)slot * d.dim;
-        for (int t = 0; t < p.tiles_per_chunk; ++t) {
-            const int64_t tn = (int64_t)c * p.tiles_per_chunk + t;
-            int64_t base = 0;
-            for (int j = 0; j < p.n_nontile; ++j)
-                if ((tn >> j) & 1) base |= 1ll << p.nontile_q[j];
-            T* g = gstate + base;
-            if constexpr (sizeof(T) == 8) {  // complex64: two amplitudes per 128-bit access
-                for (int l2 = threadIdx.x; l2 < (tsize >> 1); l2 += blockDim.x) {
-                    const int l = l2 << 1;
-                    const int gi = (l & run_mask) | hi_tab[l >> run];
-                    const float4 v = *reinterpret_cast<const float4*>(g + gi);
-                    *reinterpret_cast<float4*>(tile + l) = v;
+    for (int h = threadIdx.x; h < n_runs; h += blockDim.x) {
+        int o = 0;
+        for (int j = 0; j < tb - run; ++j)
+            if ((h >> j) & 1) o |= 1 << p.tile_q[run + j];
+        hi_tab[h] = o;
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PASS_NBUF; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    T* const states = reinterpret_cast<T*>(d.states);
+    const uint32_t run_bytes = (uint32_t)(sizeof(T) << run);
+    // global address of tile i (of this CTA's sequence)
+    auto tile_ptr = [&](int64_t i) -> T* {
+        const int64_t unit = i / tpc;
+        const int b = (int)(unit / p.chunks);
+        const int64_t tn = (unit % p.chunks) * tpc + i % tpc;
+        int slot = d.br_slot[b];
+        if (slot < 0 || slot >= d.n_slots) {
+            set_err(d, ERR_SLOT, b);
+            slot = 0;
+        }
+        int64_t base = 0;
+        for (int j = 0; j < p.n_nontile; ++j)
+            if ((tn >> j) & 1) base |= 1ll << p.nontile_q[j];
+        return states + (int64_t)slot * d.dim + base;
+    };
+    // warp 0: fetch tile k (k-th of this CTA) into its ring buffer
+    auto fetch = [&](int64_t k) {
+        const int s = (int)(k % PASS_NBUF);
+        T* src = tile_ptr(t0 + k);
+        if (lane == 0) mbar_expect_tx(&bars[s], (uint32_t)(sizeof(T) << tb));
+        __syncwarp();
+        for (int j = lane; j < n_runs; j += 32)
+            bulk_load(bufs + (size_t)s * tsize + ((size_t)j << run), src + hi_tab[j], run_bytes, &bars[s]);
+    };
+    if (warp == 0)
+        for (int64_t k = 0; k < PASS_AHEAD && k < nt; ++k) fetch(k);
+
+    int cur_b = -1;
+    bool ok = true;
+    for (int64_t k = 0; k < nt && ok; ++k) {
+        const int64_t i = t0 + k;
+        const int s = (int)(k % PASS_NBUF);
+        if (warp == 0 && k + PASS_AHEAD < nt) {
+            bulk_wait_read1();  // the store of tile k-2 has left the buffer
+            __syncwarp();
+            fence_proxy_async();
+            fetch(k + PASS_AHEAD);
+        }
+        const int64_t unit = i / tpc;
+        const int b = (int)(unit / p.chunks);
+        const int c = (int)(unit % p.chunks);
+        if (b != cur_b) {
+            const uint64_t clb = d.br_clbits[b];
+            __syncthreads();
+            for (int st_i = threadIdx.x; st_i < p.n_stages; st_i += blockDim.x) {
+                const Stage& st = p.st[st_i];
+                int sk = 0, sel = 0, packed = 0;
+                double scale = 1.0;
+                if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val) sk = 1;
+                if (st.kind != ST_DENSE) {
+                    sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
+                    scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
+                    if (sel < 0) sk = 1;
+                    if (st.kind == ST_PAULI_BR && !sk) {
+                        packed = d.ipool[st.off + sel];
+                        if ((packed & 0xff) == 0) sk = 1;  // identity string: nothing to do
+                    }
                 }
-            } else {
-                for (int l = threadIdx.x; l < tsize; l += blockDim.x) {
-                    const int gi = (l & run_mask) | hi_tab[l >> run];
-                    tile[l] = g[gi];
+                skip[st_i] = sk;
+                sel_sh[st_i] = sel;
+                packed_sh[st_i] = packed;
+                scale_sh[st_i] = scale;
+            }
+            __syncthreads();
+            const R* pool = reinterpret_cast<const R*>(d.pool);
+            for (int st_i = 0; st_i < p.n_stages; ++st_i) {
+                const Stage& st = p.st[st_i];
+                if (skip[st_i] || (st.kind != ST_DENSE && st.kind != ST_DENSE_BR)) continue;
+                const int D2 = 1 << (2 * st.k);
+                const R* src = pool + st.off + (st.kind == ST_DENSE_BR ? (int64_t)sel_sh[st_i] * st.stride : 0);
+                const R sc = (R)scale_sh[st_i];
+                for (int e = threadIdx.x; e < D2; e += blockDim.x) {
+                    T m;
+                    m.x = src[2 * e] * sc;
+                    m.y = src[2 * e + 1] * sc;
+                    mats[st.mat + e] = m;
+                }
+            }
+            if (p.red_kind == RED_FORMS) {
+                const int D2 = 1 << (2 * p.red_k);
+                const R* src = pool + p.red_off;
+                for (int e = threadIdx.x; e < p.red_R * D2; e += blockDim.x) {
+                    T m;
+                    m.x = src[2 * e];
+                    m.y = src[2 * e + 1];
+                    mats[p.mat_elems - p.red_R * D2 + e] = m;
                 }
             }
             __syncthreads();
-            for (int s = 0; s < p.n_stages; ++s) {
-                if (skip[s]) continue;
-                const Stage& st = p.st[s];
-                stage_dispatch<R>(tile, tb, st, mats + st.mat, sel_sh[s], scale_sh[s], packed_sh[s]);
-                __syncthreads();
-            }
-            if (p.red_kind != RED_NONE) {
-                const int D2 = 1 << (2 * p.red_k);
-                reduce_dispatch<R>(tile, tb, p, mats + p.mat_elems - p.red_R * D2, acc);
-            }
-            if (p.store) {
-                if constexpr (sizeof(T) == 8) {
-                    for (int l2 = threadIdx.x; l2 < (tsize >> 1); l2 += blockDim.x) {
-                        const int l = l2 << 1;
-                        const int gi = (l & run_mask) | hi_tab[l >> run];
-                        *reinterpret_cast<float4*>(g + gi) = *reinterpret_cast<const float4*>(tile + l);
-                    }
-                } else {
-                    for (int l = threadIdx.x; l < tsize; l += blockDim.x) {
-                        const int gi = (l & run_mask) | hi_tab[l >> run];
-                        g[gi] = tile[l];
-                    }
-                }
-            }
+            cur_b = b;
+        }
+        if (red && i % tpc == 0)
+            for (int r = 0; r < p.red_R; ++r) acc[r * blockDim.x + threadIdx.x] = A{};
+        if (!mbar_wait(d, &bars[s], (uint32_t)((k / PASS_NBUF) & 1))) ok = false;
+        T* tile = bufs + (size_t)s * tsize;
+        for (int st_i = 0; st_i < p.n_stages; ++st_i) {
+            if (skip[st_i]) continue;
+            const Stage& st = p.st[st_i];
+            stage_dispatch<R>(tile, tb, st, mats + st.mat, sel_sh[st_i], scale_sh[st_i], packed_sh[st_i]);
             __syncthreads();
         }
-        if (p.red_kind != RED_NONE) {
-            double* out = d.partials + ((int64_t)slot * d.max_chunks + c) * MAX_RED;
+        if (red) {
+            const int D2 = 1 << (2 * p.red_k);
+            reduce_dispatch<R>(tile, tb, p, mats + p.mat_elems - p.red_R * D2, acc);
+        }
+        __syncthreads();
+        if (p.store && warp == 0) {
+            T* dst = tile_ptr(i);
+            fence_proxy_async();
+            for (int j = lane; j < n_runs; j += 32)
+                bulk_store(dst + hi_tab[j], tile + ((size_t)j << run), run_bytes);
+            bulk_commit();
+        }
+        if (red && i % tpc == tpc - 1) {
+            // fixed-order combination: lanes by shuffles, warps in order
+            const int slot = d.br_slot[b];
             for (int r = 0; r < p.red_R; ++r) {
-                const double s = block_sum(acc_get(acc[r * blockDim.x + threadIdx.x]), red_sh);
-                if (threadIdx.x == 0) out[r] = s;
+                double v = acc_get(acc[r * blockDim.x + threadIdx.x]);
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) wsum[warp][r] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < p.red_R && slot >= 0 && slot < d.n_slots) {
+                double v = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += wsum[w][threadIdx.x];
+                d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED + threadIdx.x] = v;
             }
         }
     }
+    if (warp == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
-// k_decide: one CTA per branch (grid-stride)
+// k_decide: per branch, probabilities (fixed-order float64 sums of the
+// partials), one Philox draw per shot, the shot's choice, and a stable
+// partition of the branch's shots by choice.  Branches with more than
+// DEC_SMALL shots take a whole CTA (k_decide_big); the others one warp
+// (k_decide_small).  Forking branches are appended to a list for k_alloc.
 // ---------------------------------------------------------------------------
 constexpr int DEC_THREADS = 512;
+constexpr int DEC_SMALL = 64;
 
-__global__ void __launch_bounds__(DEC_THREADS) k_decide(DevBatch d, const __grid_constant__ DecideDesc dd) {
+// probabilities and cumulative table of branch b into p_out / cum_out
+__device__ __forceinline__ void decide_probs(const DevBatch& d, const DecideDesc& dd, int slot, int r,
+                                             double* p_out, double* cum_out) {
+    if (dd.kind == DEC_PAULI) {
+        p_out[r] = dd.cum[r] - (r ? dd.cum[r - 1] : 0.0);
+        cum_out[r] = dd.cum[r];
+    } else {
+        const double* pp = d.partials + (int64_t)slot * d.max_chunks * MAX_RED + r;
+        double s = 0.0;
+        for (int c = 0; c < dd.chunks; ++c) s += pp[(int64_t)c * MAX_RED];
+        p_out[r] = s;
+    }
+}
+
+// group records of branch b (one thread): outcome, 1/sqrt(p) in float64,
+// classical bits; the branch itself keeps the smallest outcome
+__device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, int start, const int* bincnt,
+                              const int* binbase, const double* p) {
+    int g = 0;
+    int64_t g0 = (int64_t)b * MAX_TERMS;
+    for (int r = 0; r < dd.R; ++r) {
+        if (bincnt[r] == 0) continue;
+        const int64_t gi = g0 + g;
+        const double scale = dd.kind == DEC_PAULI ? 1.0 : 1.0 / sqrt(p[r]);
+        uint64_t cl = d.br_clbits[b];
+        if (dd.kind == DEC_MEASURE)
+            for (int j = 0; j < dd.m; ++j) {
+                const uint64_t bit = (uint64_t)((r >> j) & 1);
+                cl = (cl & ~(1ull << dd.clbit[j])) | (bit << dd.clbit[j]);
+            }
+        d.grp_sel[gi] = r;
+        d.grp_start[gi] = start + binbase[r];
+        d.grp_cnt[gi] = bincnt[r];
+        d.grp_scale[gi] = scale;
+        d.grp_clbits[gi] = cl;
+        ++g;
+    }
+    d.grp_n[b] = g;
+    d.br_sel[(int64_t)dd.pend * d.cap_br + b] = d.grp_sel[g0];
+    d.br_scale[(int64_t)dd.pend * d.cap_br + b] = d.grp_scale[g0];
+    d.br_clbits[b] = d.grp_clbits[g0];
+    if (g > 1) {
+        if (!dd.fork) set_err(d, ERR_GROUPS, b);
+        else d.fork_list[atomicAdd(&d.ctl[CTL_NFL], 1)] = b;
+    }
+}
+
+__device__ __forceinline__ int draw_choice(const DevBatch& d, const DecideDesc& dd, uint32_t shot, const double* cum) {
+    const double u = philox_uniform(d.seed, shot, dd.op);
+    const int sel = select_cum(u, cum, dd.R);
+    if (dd.log_sel) dd.log_sel[shot] = sel;
+    if (dd.log_thr) {
+        dd.log_thr[2 * (int64_t)shot] = sel ? cum[sel - 1] : 0.0;
+        dd.log_thr[2 * (int64_t)shot + 1] = cum[sel];
+    }
+    return sel;
+}
+
+__global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __grid_constant__ DecideDesc dd) {
     __shared__ double p_sh[MAX_TERMS], cum_sh[MAX_TERMS];
     __shared__ int bincnt[MAX_TERMS], binbase[MAX_TERMS], binrun[MAX_TERMS];
     __shared__ int wcnt[DEC_THREADS / 32][MAX_TERMS];
-    __shared__ int ng_sh, first_sh;
+    __shared__ int ng_sh;
     const int n_br = d.ctl[CTL_NBR];
     const int R = dd.R;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
     for (int b = blockIdx.x; b < n_br; b += gridDim.x) {
-        const int slot = d.br_slot[b], start = d.br_start[b], cnt = d.br_count[b];
+        const int cnt = d.br_count[b];
+        if (cnt <= DEC_SMALL) continue;
+        const int slot = d.br_slot[b], start = d.br_start[b];
         __syncthreads();
         if (tid < R) {
-            double p;
-            if (dd.kind == DEC_PAULI) {
-                p = dd.cum[tid] - (tid ? dd.cum[tid - 1] : 0.0);
-                cum_sh[tid] = dd.cum[tid];
-            } else {
-                const double* pp = d.partials + (int64_t)slot * d.max_chunks * MAX_RED + tid;
-                double s = 0.0;
-                for (int c = 0; c < dd.chunks; ++c) s += pp[(int64_t)c * MAX_RED];
-                p = s;
-            }
-            p_sh[tid] = p;
+            decide_probs(d, dd, slot, tid, p_sh, cum_sh);
             bincnt[tid] = 0;
             binrun[tid] = 0;
         }
         __syncthreads();
         if (tid == 0 && dd.kind != DEC_PAULI) {
-            double s = 0.0;
-            for (int r = 0; r < R; ++r) {
-                s += p_sh[r];
-                cum_sh[r] = s;
-            }
+            double acc = 0.0;
+            for (int r = 0; r < R; ++r) cum_sh[r] = (acc += p_sh[r]);
         }
         __syncthreads();
         for (int i = tid; i < cnt; i += nth) {
-            const uint32_t s = d.perm[start + i];
-            const double u = philox_uniform(d.seed, s, dd.op);
-            const int sel = select_cum(u, cum_sh, R);
+            const int sel = draw_choice(d, dd, d.perm[start + i], cum_sh);
             d.shot_sel[start + i] = sel;
             atomicAdd(&bincnt[sel], 1);
-            if (dd.log_sel) dd.log_sel[s] = sel;
-            if (dd.log_thr) {
-                dd.log_thr[2 * (int64_t)s] = sel ? cum_sh[sel - 1] : 0.0;
-                dd.log_thr[2 * (int64_t)s + 1] = cum_sh[sel];
-            }
         }
         __syncthreads();
         if (tid == 0) {
-            int ng = 0, acc = 0, first = -1;
+            int ng = 0, acc = 0;
             for (int r = 0; r < R; ++r)
                 if (bincnt[r] > 0) {
                     binbase[r] = acc;
                     acc += bincnt[r];
-                    if (first < 0) first = r;
                     ++ng;
                 }
             ng_sh = ng;
-            first_sh = first;
+            decide_groups(d, dd, b, start, bincnt, binbase, p_sh);
         }
         __syncthreads();
-        const int ng = ng_sh, first = first_sh;
-        // group records: outcome, scale 1/sqrt(p) (float64), classical bits
-        if (tid == 0) {
-            int g = 0;
-            for (int r = 0; r < R; ++r) {
-                if (bincnt[r] == 0) continue;
-                const int64_t gi = (int64_t)b * MAX_TERMS + g;
-                double scale = 1.0;
-                if (dd.kind != DEC_PAULI) scale = 1.0 / sqrt(p_sh[r]);
-                uint64_t cl = d.br_clbits[b];
-                if (dd.kind == DEC_MEASURE)
-                    for (int j = 0; j < dd.m; ++j) {
-                        const uint64_t bit = (uint64_t)((r >> j) & 1);
-                        cl = (cl & ~(1ull << dd.clbit[j])) | (bit << dd.clbit[j]);
-                    }
-                d.grp_sel[gi] = r;
-                d.grp_start[gi] = start + binbase[r];
-                d.grp_cnt[gi] = bincnt[r];
-                d.grp_scale[gi] = scale;
-                d.grp_clbits[gi] = cl;
-                ++g;
-            }
-            d.grp_n[b] = ng;
-            const int64_t g0 = (int64_t)b * MAX_TERMS;
-            d.br_sel[(int64_t)dd.pend * d.cap_br + b] = first;
-            d.br_scale[(int64_t)dd.pend * d.cap_br + b] = d.grp_scale[g0];
-            d.br_clbits[b] = d.grp_clbits[g0];
-            if (ng > 1 && !dd.fork) set_err(d, ERR_GROUPS, b);
-        }
-        if (ng <= 1 || !dd.fork) continue;
-        // stable partition of the branch's shots by outcome
+        if (ng_sh <= 1 || !dd.fork) continue;
         for (int base = 0; base < cnt; base += nth) {
             const int i = base + tid;
             const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
@@ -624,8 +732,7 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide(DevBatch d, const __grid
             if (sel >= 0) {
                 int before = 0;
                 for (int w = 0; w < warp; ++w) before += wcnt[w][sel];
-                const int dst = binbase[sel] + binrun[sel] + before + rank;
-                d.perm_tmp[start + dst] = d.perm[start + i];
+                d.perm_tmp[start + binbase[sel] + binrun[sel] + before + rank] = d.perm[start + i];
             }
             __syncthreads();
             if (tid < R) {
@@ -636,13 +743,82 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide(DevBatch d, const __grid
             __syncthreads();
         }
         for (int i = tid; i < cnt; i += nth) d.perm[start + i] = d.perm_tmp[start + i];
-        if (tid == 0) d.br_count[b] = bincnt[first];
+        if (tid == 0) d.br_count[b] = d.grp_cnt[(int64_t)b * MAX_TERMS];
+    }
+}
+
+constexpr int DECS_WARPS = 8;
+
+__global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, const __grid_constant__ DecideDesc dd) {
+    __shared__ double p_sh[DECS_WARPS][MAX_TERMS], cum_sh[DECS_WARPS][MAX_TERMS];
+    __shared__ int bincnt[DECS_WARPS][MAX_TERMS], binbase[DECS_WARPS][MAX_TERMS], binrun[DECS_WARPS][MAX_TERMS];
+    const int n_br = d.ctl[CTL_NBR];
+    const int R = dd.R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* p = p_sh[warp];
+    double* cum = cum_sh[warp];
+    int* bc = bincnt[warp];
+    int* bb = binbase[warp];
+    int* br = binrun[warp];
+    const int gw = blockIdx.x * DECS_WARPS + warp, nw = gridDim.x * DECS_WARPS;
+    for (int b = gw; b < n_br; b += nw) {
+        const int cnt = d.br_count[b];
+        if (cnt > DEC_SMALL) continue;
+        const int slot = d.br_slot[b], start = d.br_start[b];
+        for (int r = lane; r < R; r += 32) {
+            decide_probs(d, dd, slot, r, p, cum);
+            bc[r] = 0;
+            br[r] = 0;
+        }
+        __syncwarp();
+        if (lane == 0 && dd.kind != DEC_PAULI) {
+            double acc = 0.0;
+            for (int r = 0; r < R; ++r) cum[r] = (acc += p[r]);
+        }
+        __syncwarp();
+        for (int i = lane; i < cnt; i += 32) {
+            const int sel = draw_choice(d, dd, d.perm[start + i], cum);
+            d.shot_sel[start + i] = sel;
+            atomicAdd(&bc[sel], 1);
+        }
+        __syncwarp();
+        int ng = 0;
+        if (lane == 0) {
+            int acc = 0;
+            for (int r = 0; r < R; ++r)
+                if (bc[r] > 0) {
+                    bb[r] = acc;
+                    acc += bc[r];
+                    ++ng;
+                }
+            decide_groups(d, dd, b, start, bc, bb, p);
+        }
+        ng = __shfl_sync(0xffffffffu, ng, 0);
+        __syncwarp();
+        if (ng <= 1 || !dd.fork) continue;
+        for (int base = 0; base < cnt; base += 32) {
+            const int i = base + lane;
+            const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, sel);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            if (sel >= 0) d.perm_tmp[start + bb[sel] + br[sel] + rank] = d.perm[start + i];
+            __syncwarp();
+            if (sel >= 0 && rank == 0) br[sel] += __popc(peers);
+            __syncwarp();
+        }
+        for (int i = lane; i < cnt; i += 32) d.perm[start + i] = d.perm_tmp[start + i];
+        if (lane == 0) d.br_count[b] = d.grp_cnt[(int64_t)b * MAX_TERMS];
+        __syncwarp();
     }
 }
 
 // ---------------------------------------------------------------------------
-// k_alloc: one CTA of 1024 threads
+// k_alloc: one CTA of 1024 threads.  The forking branches (listed by the
+// decide kernels) are sorted by id, so new branch ids and slots are handed
+// out in branch order whatever order the list was written in.
 // ---------------------------------------------------------------------------
+constexpr int ALLOC_SORT_MAX = 8192;
+
 __device__ int block_excl_scan(int v, int* sh, int* total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int x = v;
@@ -671,25 +847,49 @@ __device__ int block_excl_scan(int v, int* sh, int* total) {
 
 __global__ void __launch_bounds__(1024) k_alloc(DevBatch d, uint32_t op, int pend) {
     __shared__ int sh[32];
+    __shared__ int list[ALLOC_SORT_MAX];
     const int n_br0 = d.ctl[CTL_NBR];
     const int n_free = d.ctl[CTL_NFREE];
     const int n_wait0 = d.ctl[CTL_NWAIT];
+    const int n_list = d.ctl[CTL_NFL];
+    const bool use_list = n_list <= ALLOC_SORT_MAX;
+    int n_items = n_br0;
+    if (use_list) {
+        int np2 = 1;
+        while (np2 < n_list) np2 <<= 1;
+        for (int i = threadIdx.x; i < np2; i += blockDim.x) list[i] = i < n_list ? d.fork_list[i] : 0x7fffffff;
+        __syncthreads();
+        for (int k = 2; k <= np2; k <<= 1)  // bitonic sort, ascending
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const int a = list[i], c = list[l];
+                        const bool up = (i & k) == 0;
+                        if ((a > c) == up) {
+                            list[i] = c;
+                            list[l] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        n_items = n_list;
+    }
     int carry = 0, wcarry = 0;
-    for (int base = 0; base < n_br0; base += blockDim.x) {
-        const int b = base + threadIdx.x;
-        const int gn = (b < n_br0) ? d.grp_n[b] : 1;
+    for (int base = 0; base < n_items; base += blockDim.x) {
+        const int idx = base + threadIdx.x;
+        const int b = idx < n_items ? (use_list ? list[idx] : idx) : -1;
+        const int gn = b >= 0 ? d.grp_n[b] : 1;
         const int ng = gn > 1 ? gn - 1 : 0;
         int tot;
         const int excl = carry + block_excl_scan(ng, sh, &tot);
-        // waiting shots of this branch's groups that find no slot
         int wshots = 0;
-        for (int g = 1; g < gn; ++g) {
-            const int j = excl + g - 1;
-            if (j >= n_free) wshots += d.grp_cnt[(int64_t)b * MAX_TERMS + g];
-        }
+        for (int g = 1; g < gn; ++g)
+            if (excl + g - 1 >= n_free) wshots += d.grp_cnt[(int64_t)b * MAX_TERMS + g];
         int wtot;
         const int wexcl = wcarry + block_excl_scan(wshots, sh, &wtot);
-        if (b < n_br0 && gn > 1) {
+        if (b >= 0 && gn > 1) {
             const int64_t g0 = (int64_t)b * MAX_TERMS;
             if (d.fork_log) {
                 const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
@@ -705,8 +905,7 @@ __global__ void __launch_bounds__(1024) k_alloc(DevBatch d, uint32_t op, int pen
                 int child = -1;
                 if (j < n_free) {
                     child = n_br0 + j;
-                    const int slot = d.free_slots[n_free - 1 - j];
-                    d.br_slot[child] = slot;
+                    d.br_slot[child] = d.free_slots[n_free - 1 - j];
                     d.br_start[child] = d.grp_start[gi];
                     d.br_count[child] = d.grp_cnt[gi];
                     d.br_clbits[child] = d.grp_clbits[gi];
@@ -744,6 +943,7 @@ __global__ void __launch_bounds__(1024) k_alloc(DevBatch d, uint32_t op, int pen
         d.ctl[CTL_COPY_FIRST] = n_br0;
         d.ctl[CTL_COPY_END] = n_br0 + admitted;
         d.ctl[CTL_NCOPIED] += admitted;
+        d.ctl[CTL_NFL] = 0;
     }
 }
 
@@ -803,6 +1003,7 @@ __global__ void __launch_bounds__(256) k_final_sample(DevBatch d, FinalDesc f) {
     __shared__ double cum[MAX_CHUNKS];
     const int n_br = d.ctl[CTL_NBR];
     const int64_t L = d.dim / f.chunks;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int b = blockIdx.x; b < n_br; b += gridDim.x) {
         const int slot = d.br_slot[b], start = d.br_start[b], cnt = d.br_count[b];
         __syncthreads();
@@ -816,34 +1017,45 @@ __global__ void __launch_bounds__(256) k_final_sample(DevBatch d, FinalDesc f) {
         }
         __syncthreads();
         const T* g = reinterpret_cast<const T*>(d.states) + (int64_t)slot * d.dim;
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        // one warp per shot: the chunk by binary search over chunk totals, then
+        // 32 amplitudes at a time with a warp prefix sum (float64)
+        for (int i = warp; i < cnt; i += nwarps) {
             const uint32_t s = d.perm[start + i];
             const double u = philox_uniform(d.seed, s, f.op);
-            int64_t key = -1;
-            double lo = 0.0, hi = 0.0;
-            // chunk: first c with u < cum[c]
             int clo = 0, chi = f.chunks;
             while (clo < chi) {
                 const int mid = (clo + chi) >> 1;
                 if (u < cum[mid]) chi = mid;
                 else clo = mid + 1;
             }
+            int64_t key = -1;
+            double lo = 0.0, hi = 0.0;
             if (clo < f.chunks) {
                 double acc = clo ? cum[clo - 1] : 0.0;
                 const int64_t j0 = (int64_t)clo * L;
-                for (int64_t j = 0; j < L; ++j) {
-                    const T v = g[j0 + j];
-                    const double before = acc;
-                    acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-                    if (u < acc) {
-                        key = j0 + j;
-                        lo = before;
-                        hi = acc;
-                        break;
+                for (int64_t blk = 0; blk < L && key < 0; blk += 32) {
+                    double pj = 0.0;
+                    if (blk + lane < L) {
+                        const T v = g[j0 + blk + lane];
+                        pj = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
                     }
+                    double incl = pj;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const double y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const double val = acc + incl;
+                    const unsigned hit = __ballot_sync(0xffffffffu, (blk + lane < L) && u < val);
+                    if (hit) {
+                        const int first = __ffs(hit) - 1;
+                        key = j0 + blk + first;
+                        hi = __shfl_sync(0xffffffffu, val, first);
+                        lo = hi - __shfl_sync(0xffffffffu, pj, first);
+                    }
+                    acc += __shfl_sync(0xffffffffu, incl, 31);
                 }
             }
-            if (key < 0) {  // u at or past the rounded total: last nonzero entry
+            if (key < 0 && lane == 0) {  // u at or past the rounded total: last nonzero entry
                 for (int64_t j = d.dim - 1; j >= 0; --j) {
                     const T v = g[j];
                     const double pj = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
@@ -856,11 +1068,13 @@ __global__ void __launch_bounds__(256) k_final_sample(DevBatch d, FinalDesc f) {
                 }
                 if (key < 0) key = d.dim - 1;
             }
-            d.keys[s] = (uint64_t)key;
-            if (f.log_sel) f.log_sel[s] = (int32_t)key;
-            if (f.log_thr) {
-                f.log_thr[2 * (int64_t)s] = lo;
-                f.log_thr[2 * (int64_t)s + 1] = hi;
+            if (lane == 0) {
+                d.keys[s] = (uint64_t)key;
+                if (f.log_sel) f.log_sel[s] = (int32_t)key;
+                if (f.log_thr) {
+                    f.log_thr[2 * (int64_t)s] = lo;
+                    f.log_thr[2 * (int64_t)s + 1] = hi;
+                }
             }
         }
     }
@@ -902,6 +1116,7 @@ __global__ void __launch_bounds__(256) k_reset(DevBatch d, int branch_mode, int 
     const int n_free = d.n_slots - nb;
     for (int64_t j = t0; j < n_free; j += stride) d.free_slots[j] = d.n_slots - 1 - (int)j;
     if (t0 == 0) {
+        d.ctl[CTL_NFL] = 0;
         d.ctl[CTL_NBR] = nb;
         d.ctl[CTL_NFREE] = n_free;
         d.ctl[CTL_NWAIT] = 0;
@@ -914,9 +1129,7 @@ __global__ void __launch_bounds__(256) k_reset(DevBatch d, int branch_mode, int 
 // launchers
 // ---------------------------------------------------------------------------
 size_t pass_smem_bytes(int prec, const PassDesc& p, int threads) {
-    const size_t c = prec ? 16 : 8;
-    const size_t acc = p.red_kind != RED_NONE ? (size_t)p.red_R * threads * 8 : 0;
-    return ((size_t)1 << p.tb) * c + (size_t)p.mat_elems * c + acc + ((size_t)1 << (p.tb - p.run_bits)) * 4;
+    return ((pass_bytes_before_bars(p, threads, prec ? 16 : 8) + 7) & ~(size_t)7) + PASS_NBUF * 8;
 }
 
 cudaError_t init_kernels() {
@@ -934,7 +1147,10 @@ cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int thre
 }
 
 cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int grid, cudaStream_t s) {
-    k_decide<<<grid, DEC_THREADS, 0, s>>>(d, dd);
+    // small branches first: a branch the big kernel partitions may end up
+    // with DEC_SMALL shots or fewer and must not be decided twice
+    k_decide_small<<<grid, DECS_WARPS * 32, 0, s>>>(d, dd);
+    k_decide_big<<<grid, DEC_THREADS, 0, s>>>(d, dd);
     return cudaGetLastError();
 }
 

@@ -211,7 +211,7 @@ sv_status exec(sv_batch b, const Launch& L) {
         cudaEventRecord(e1, b->stream);
         b->prof_ev.push_back({pclass(L.type), {e0, e1}});
     }
-    b->n_launch += (L.type == L_FINAL) ? 2 : 1;
+    b->n_launch += (L.type == L_FINAL || L.type == L_DECIDE) ? 2 : 1;
     if (L.type == L_PASS) {
         b->n_passes += 1;
         b->pass_store.push_back(L.pass.store ? 1 : 0);
@@ -930,6 +930,7 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
         (st = dalloc(b, &d.grp_start, S * MAX_TERMS)) || (st = dalloc(b, &d.grp_cnt, S * MAX_TERMS)) ||
         (st = dalloc(b, &d.grp_scale, S * MAX_TERMS)) || (st = dalloc(b, &d.grp_clbits, S * MAX_TERMS)) ||
         (st = dalloc(b, &d.free_slots, b->n_slots)) || (st = dalloc(b, &d.wait_shots, S)) ||
+        (st = dalloc(b, &d.fork_list, S)) ||
         (st = dalloc(b, &d.partials, (size_t)b->n_slots * max_chunks * MAX_RED)) || (st = dalloc(b, &d.keys, S)) ||
         (st = dalloc(b, &d.pass_log, 1 << 20))) {
         sv_free_batch(b);
@@ -1165,7 +1166,7 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
                 cudaGraphDestroy(g);
                 b->graph_hash = h;
                 int64_t nl = 0;
-                for (const Launch& L : launches) nl += (L.type == L_FINAL) ? 2 : 1;
+                for (const Launch& L : launches) nl += (L.type == L_FINAL || L.type == L_DECIDE) ? 2 : 1;
                 b->graph_launches = nl;
                 b->graph_pass_store.clear();
                 for (const Launch& L : launches)
