@@ -210,6 +210,31 @@ sv_status sv_stats(sv_batch b, double *stats);
  * (8 int64), accumulated since the last call.  Synchronises.                */
 sv_status sv_profile(sv_batch b, double *ms, int64_t *launches);
 
+/* Final sampling that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as
+ * a host framework that owns a fixed device-memory budget and forbids its
+ * plug-ins to allocate, or a latency-critical loop where cudaMalloc's
+ * implicit synchronisation would stall the device.  It draws one key per
+ * state exactly as sv_counts / sv_run_circuit do (same Philox draw, same
+ * chunked float64 prefix), from states and into keys the caller provides:
+ *   states   device, n_states consecutive states of 2^n_qubits amplitudes
+ *            (float2 for SV_C64, double2 for SV_C128), read only
+ *   shots    device, n_states shot ids: state i draws with counter
+ *            (shots[i], op)
+ *   keys     device, n_states outputs (sampled indices)
+ *   cuda_stream  stream to run on (NULL = default stream); asynchronous
+ * Scratch is a static 1 MiB device array (131072 float64 partial sums) that
+ * every GPU loading the library holds until exit; n_states x chunks (chunks
+ * = min(max(2^n_qubits / 2048, 1), 1024)) above that limit gives
+ * SV_EINVAL.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents (every value read is written first in the same
+ * call); calls whose work overlaps on the GPU race on it.                    */
+sv_status sv_final_sample_noalloc(const void *states, sv_prec prec, int n_qubits, uint32_t n_states,
+                                  const uint32_t *shots, uint64_t seed, uint32_t op, uint64_t *keys,
+                                  void *cuda_stream);
+
 /* Wait for the batch's stream, at most timeout_ns (0 = no limit). */
 sv_status sv_sync(sv_batch b, uint64_t timeout_ns);
 

@@ -91,6 +91,11 @@ int host_select(double u, const double* cum, int n) {
 
 }  // namespace
 
+namespace sv {
+// message for sv_last_error() from other translation units of the library
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace sv
+
 struct sv_batch_s {
     int n = 0;
     uint64_t n_shots = 0;
