@@ -110,8 +110,10 @@ typedef enum {
     SV_OPT_GRID = 5,        /* CTAs of the persistent kernels (0 = default)             */
     SV_OPT_PROFILE = 6,     /* 1: time every launch class with CUDA events              */
     SV_OPT_SLOT_LIMIT = 7,  /* cap on state slots (0 = as many as fit); forces waiting  */
-    SV_OPT_UPLOAD = 8       /* 1: sv_run_circuit copies the circuit's constants to the
+    SV_OPT_UPLOAD = 8,      /* 1: sv_run_circuit copies the circuit's constants to the
                                device on every call, even when its graph is cached   */
+    SV_OPT_PASS_PATH = 9    /* 0: passes of <= 4 qubits run in registers, others in
+                               shared-memory tiles; 1: shared-memory tiles only      */
 } sv_option;
 
 /* Allocate a batch of n_shots shots of an n_qubits register.

@@ -57,6 +57,7 @@ struct PassDesc {
     int32_t mat_elems;         // complex entries of the shared-memory matrix area
     int32_t red_kind, red_k, red_R, red_off;
     int32_t red_pos[MAX_STAGE_Q];
+    int32_t reg_wp;            // > 0: register path (k_pass_reg), group of 2^reg_wp amplitudes
     Stage st[MAX_STAGES];
 };
 
@@ -146,6 +147,8 @@ cudaError_t launch_alloc(const DevBatch& d, uint32_t op, int pend, cudaStream_t 
 cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s);
 cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s);
 size_t pass_smem_bytes(int prec, const PassDesc& p, int threads);
+size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads);
+int pass_reg_blocks_per_sm(int prec, int wp, size_t smem);
 cudaError_t init_kernels();
 
 }  // namespace sv

@@ -609,6 +609,344 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
 }
 
 // ---------------------------------------------------------------------------
+// k_pass_reg: register-resident variant for passes whose qubits (plus qubit
+// 0) number WP <= 4.  Each lane holds whole groups of 2^WP amplitudes (the
+// amplitudes that differ only in the pass's qubits), loads them straight
+// from HBM as 128-bit pairs (qubit 0 is group bit 0), applies every fused
+// stage in registers, accumulates the reduction in registers, and stores.
+// One warp owns a (branch, chunk) unit; a unit's partial is combined by
+// warp shuffles in a fixed order, so no block barrier is needed.
+// Stage and reduction positions are group-bit indices (0..WP-1); runtime
+// positions are mapped onto compile-time register indices by a switch.
+// ---------------------------------------------------------------------------
+template <class T, int G, int J>
+__device__ __forceinline__ void reg_apply1(T* v, const T* M) {
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+        if (r & (1 << J)) continue;
+        const int r1 = r | (1 << J);
+        const T a = v[r], b = v[r1];
+        T x, y;
+        x.x = M[0].x * a.x - M[0].y * a.y + M[1].x * b.x - M[1].y * b.y;
+        x.y = M[0].x * a.y + M[0].y * a.x + M[1].x * b.y + M[1].y * b.x;
+        y.x = M[2].x * a.x - M[2].y * a.y + M[3].x * b.x - M[3].y * b.y;
+        y.y = M[2].x * a.y + M[2].y * a.x + M[3].x * b.y + M[3].y * b.x;
+        v[r] = x;
+        v[r1] = y;
+    }
+}
+
+// 2-qubit matrix, matrix bit 0 on group bit J0, matrix bit 1 on group bit J1
+template <class T, int G, int J0, int J1>
+__device__ __forceinline__ void reg_apply2(T* v, const T* M) {
+    T m[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) m[e] = M[e];
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+        if (r & ((1 << J0) | (1 << J1))) continue;
+        const int i[4] = {r, r | (1 << J0), r | (1 << J1), r | (1 << J0) | (1 << J1)};
+        T a[4], o[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a[c] = v[i[c]];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T acc;
+            acc.x = 0;
+            acc.y = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cfma(acc, m[q * 4 + c], a[c]);
+            o[q] = acc;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[i[c]] = o[c];
+    }
+}
+
+template <class T, int G, int J>
+__device__ __forceinline__ void reg_flip(T* v) {
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+        if (r & (1 << J)) continue;
+        const T t = v[r];
+        v[r] = v[r | (1 << J)];
+        v[r | (1 << J)] = t;
+    }
+}
+
+template <class T, int G>
+__device__ __forceinline__ void reg_flip_dyn(T* v, int j) {
+    switch (j) {
+    case 0: reg_flip<T, G, 0>(v); break;
+    case 1: if constexpr (G > 2) reg_flip<T, G, 1>(v); break;
+    case 2: if constexpr (G > 4) reg_flip<T, G, 2>(v); break;
+    default: if constexpr (G > 8) reg_flip<T, G, 3>(v); break;
+    }
+}
+
+template <class T, int G>
+__device__ __forceinline__ void reg_apply1_dyn(T* v, int j, const T* M) {
+    switch (j) {
+    case 0: reg_apply1<T, G, 0>(v, M); break;
+    case 1: if constexpr (G > 2) reg_apply1<T, G, 1>(v, M); break;
+    case 2: if constexpr (G > 4) reg_apply1<T, G, 2>(v, M); break;
+    default: if constexpr (G > 8) reg_apply1<T, G, 3>(v, M); break;
+    }
+}
+
+template <class T, int G>
+__device__ __forceinline__ void reg_apply2_dyn(T* v, int j0, int j1, const T* M) {
+    const int code = j0 * 4 + j1;
+    switch (code) {
+    case 1: if constexpr (G > 2) reg_apply2<T, G, 0, 1>(v, M); break;
+    case 4: if constexpr (G > 2) reg_apply2<T, G, 1, 0>(v, M); break;
+    case 2: if constexpr (G > 4) reg_apply2<T, G, 0, 2>(v, M); break;
+    case 8: if constexpr (G > 4) reg_apply2<T, G, 2, 0>(v, M); break;
+    case 6: if constexpr (G > 4) reg_apply2<T, G, 1, 2>(v, M); break;
+    case 9: if constexpr (G > 4) reg_apply2<T, G, 2, 1>(v, M); break;
+    case 3: if constexpr (G > 8) reg_apply2<T, G, 0, 3>(v, M); break;
+    case 12: if constexpr (G > 8) reg_apply2<T, G, 3, 0>(v, M); break;
+    case 7: if constexpr (G > 8) reg_apply2<T, G, 1, 3>(v, M); break;
+    case 13: if constexpr (G > 8) reg_apply2<T, G, 3, 1>(v, M); break;
+    case 11: if constexpr (G > 8) reg_apply2<T, G, 2, 3>(v, M); break;
+    default: if constexpr (G > 8) reg_apply2<T, G, 3, 2>(v, M); break;
+    }
+}
+
+// quadratic forms of one-qubit Kraus terms over the pairs along group bit J
+template <class R, int G, int J>
+__device__ __forceinline__ void reg_forms1(const typename Cplx<R>::T* v, const typename Cplx<R>::T* F, int Rn,
+                                           Acc<R>* acc) {
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+        if (r & (1 << J)) continue;
+        const auto a = v[r], b = v[r | (1 << J)];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            if (f >= Rn) break;
+            const auto* Ff = F + 4 * f;
+            // Re(conj(a)(F00 a + F01 b) + conj(b)(F10 a + F11 b))
+            const R fa_x = Ff[0].x * a.x - Ff[0].y * a.y + Ff[1].x * b.x - Ff[1].y * b.y;
+            const R fa_y = Ff[0].x * a.y + Ff[0].y * a.x + Ff[1].x * b.y + Ff[1].y * b.x;
+            const R fb_x = Ff[2].x * a.x - Ff[2].y * a.y + Ff[3].x * b.x - Ff[3].y * b.y;
+            const R fb_y = Ff[2].x * a.y + Ff[2].y * a.x + Ff[3].x * b.y + Ff[3].y * b.x;
+            acc[f].add(a.x * fa_x + a.y * fa_y + b.x * fb_x + b.y * fb_y);
+        }
+    }
+}
+
+template <class R, int G>
+__device__ __forceinline__ void reg_forms1_dyn(const typename Cplx<R>::T* v, int j, const typename Cplx<R>::T* F,
+                                               int Rn, Acc<R>* acc) {
+    switch (j) {
+    case 0: reg_forms1<R, G, 0>(v, F, Rn, acc); break;
+    case 1: if constexpr (G > 2) reg_forms1<R, G, 1>(v, F, Rn, acc); break;
+    case 2: if constexpr (G > 4) reg_forms1<R, G, 2>(v, F, Rn, acc); break;
+    default: if constexpr (G > 8) reg_forms1<R, G, 3>(v, F, Rn, acc); break;
+    }
+}
+
+constexpr int REG_MAX_RED = 4;
+
+template <class R, int WP>
+__global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_constant__ PassDesc p) {
+    using T = typename Cplx<R>::T;
+    constexpr int G = 1 << WP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    // per-warp shared memory: matrices | stage choice | stage packed | stage scale
+    const int mat_stride = (p.mat_elems + 1) & ~1;
+    T* mats = reinterpret_cast<T*>(smem_raw) + (size_t)warp * mat_stride;
+    int* w_sel = reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) + (size_t)nwarps * mat_stride) +
+                 warp * 2 * MAX_STAGES;
+    int* w_packed = w_sel + MAX_STAGES;
+
+    const int n_br = d.ctl[CTL_NBR];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && d.pass_log) {
+        const int i = atomicAdd(&d.ctl[CTL_NPASS], 1);
+        if (i < d.pass_log_cap) d.pass_log[i] = n_br;
+    }
+    // group offsets: element e of a group sits at base + off[e]
+    int off[G];
+#pragma unroll
+    for (int e = 0; e < G; ++e) {
+        int o = 0;
+#pragma unroll
+        for (int j = 0; j < WP; ++j)
+            if ((e >> j) & 1) o |= 1 << p.tile_q[j];
+        off[e] = o;
+    }
+    const int64_t units = (int64_t)n_br * p.chunks;
+    const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, tw = (int64_t)gridDim.x * nwarps;
+    const int64_t u0 = units * gw / tw, u1 = units * (gw + 1) / tw;
+    const int64_t gpu = (d.dim >> WP) / p.chunks;  // groups per unit
+    const bool red = p.red_kind != RED_NONE;
+    T* const states = reinterpret_cast<T*>(d.states);
+    const R* pool = reinterpret_cast<const R*>(d.pool);
+    int cur_b = -1;
+    uint64_t skipmask = 0;
+    for (int64_t u = u0; u < u1; ++u) {
+        const int b = (int)(u / p.chunks);
+        const int c = (int)(u % p.chunks);
+        const int slot = d.br_slot[b];
+        if (slot < 0 || slot >= d.n_slots) {
+            if (lane == 0) set_err(d, ERR_SLOT, b);
+            continue;
+        }
+        if (b != cur_b) {
+            const uint64_t clb = d.br_clbits[b];
+            skipmask = 0;
+            __syncwarp();
+            for (int s = 0; s < p.n_stages; ++s) {
+                const Stage& st = p.st[s];
+                int sk = 0, sel = 0, packed = 0;
+                double scale = 1.0;
+                if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val) sk = 1;
+                if (st.kind != ST_DENSE) {
+                    sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
+                    scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
+                    if (sel < 0) sk = 1;
+                    if (st.kind == ST_PAULI_BR && !sk) {
+                        packed = d.ipool[st.off + sel];
+                        if ((packed & 0xff) == 0) sk = 1;
+                    }
+                }
+                if (sk) skipmask |= 1ull << s;
+                if (lane == 0) {
+                    w_sel[s] = sel;
+                    w_packed[s] = packed;
+                }
+                if (!sk && (st.kind == ST_DENSE || st.kind == ST_DENSE_BR)) {
+                    const int D2 = 1 << (2 * st.k);
+                    const R* src = pool + st.off + (st.kind == ST_DENSE_BR ? (int64_t)sel * st.stride : 0);
+                    const R sc = (R)scale;
+                    for (int e = lane; e < D2; e += 32) {
+                        T m;
+                        m.x = src[2 * e] * sc;
+                        m.y = src[2 * e + 1] * sc;
+                        mats[st.mat + e] = m;
+                    }
+                } else if (!sk && st.kind == ST_PROJ_BR && lane == 0) {
+                    T m;
+                    m.x = (R)scale;
+                    m.y = 0;
+                    mats[st.mat] = m;
+                }
+            }
+            if (p.red_kind == RED_FORMS) {
+                const R* src = pool + p.red_off;
+                for (int e = lane; e < p.red_R * 4; e += 32) {
+                    T m;
+                    m.x = src[2 * e];
+                    m.y = src[2 * e + 1];
+                    mats[p.mat_elems - p.red_R * 4 + e] = m;
+                }
+            }
+            __syncwarp();
+            cur_b = b;
+        }
+        Acc<R> acc[REG_MAX_RED];
+#pragma unroll
+        for (int r = 0; r < REG_MAX_RED; ++r) acc[r].zero();
+        T* gstate = states + (int64_t)slot * d.dim;
+        for (int64_t gi = lane; gi < gpu; gi += 32) {
+            // base: the group index with zeros inserted at the group qubits
+            int64_t base = (int64_t)c * gpu + gi;
+#pragma unroll
+            for (int j = 0; j < WP; ++j) {
+                const int q = p.tile_q[j];
+                base = ((base >> q) << (q + 1)) | (base & ((1ll << q) - 1));
+            }
+            T* g = gstate + base;
+            T v[G];
+            if constexpr (sizeof(T) == 8) {
+#pragma unroll
+                for (int e = 0; e < G; e += 2) {
+                    const float4 x = *reinterpret_cast<const float4*>(g + off[e]);
+                    v[e].x = x.x;
+                    v[e].y = x.y;
+                    v[e + 1].x = x.z;
+                    v[e + 1].y = x.w;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < G; ++e) v[e] = g[off[e]];
+            }
+            for (int s = 0; s < p.n_stages; ++s) {
+                if ((skipmask >> s) & 1) continue;
+                const Stage& st = p.st[s];
+                if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
+                    if (st.k == 1) reg_apply1_dyn<T, G>(v, st.pos[0], mats + st.mat);
+                    else reg_apply2_dyn<T, G>(v, st.pos[0], st.pos[1], mats + st.mat);
+                } else if (st.kind == ST_PAULI_BR) {
+                    const int packed = w_packed[s];
+                    int zg = 0;
+                    for (int j = 0; j < st.k; ++j) {
+                        if ((packed >> j) & 1) reg_flip_dyn<T, G>(v, st.pos[j]);
+                        if ((packed >> (4 + j)) & 1) zg |= 1 << st.pos[j];
+                    }
+                    const int ny = (packed >> 8) & 3;
+#pragma unroll
+                    for (int e = 0; e < G; ++e) {
+                        // (-i)^ny, then the sign of the destination index
+                        T t = v[e];
+                        if (ny & 1) {
+                            const R x = t.x;
+                            t.x = t.y;
+                            t.y = -x;
+                        }
+                        const bool neg = ((ny >> 1) & 1) ^ (__popc(zg & e) & 1);
+                        if (neg) {
+                            t.x = -t.x;
+                            t.y = -t.y;
+                        }
+                        v[e] = t;
+                    }
+                } else {  // ST_PROJ_BR
+                    const int sel = w_sel[s];
+                    const R sc = mats[st.mat].x;
+#pragma unroll
+                    for (int e = 0; e < G; ++e) {
+                        int o = 0;
+                        for (int j = 0; j < st.k; ++j) o |= ((e >> st.pos[j]) & 1) << j;
+                        if (o == sel) {
+                            v[e].x *= sc;
+                            v[e].y *= sc;
+                        } else {
+                            v[e].x = 0;
+                            v[e].y = 0;
+                        }
+                    }
+                    if (st.reset)
+                        for (int j = 0; j < st.k; ++j)
+                            if ((sel >> j) & 1) reg_flip_dyn<T, G>(v, st.pos[j]);
+                }
+            }
+            if (red) reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - p.red_R * 4, p.red_R, acc);
+            if (p.store) {
+                if constexpr (sizeof(T) == 8) {
+#pragma unroll
+                    for (int e = 0; e < G; e += 2)
+                        *reinterpret_cast<float4*>(g + off[e]) = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < G; ++e) g[off[e]] = v[e];
+                }
+            }
+        }
+        if (red) {
+#pragma unroll
+            for (int r = 0; r < REG_MAX_RED; ++r) {
+                if (r >= p.red_R) break;
+                double x = acc[r].get();
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0) d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED + r] = x;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_decide: per branch, probabilities (fixed-order float64 sums of the
 // partials), one Philox draw per shot, the shot's choice, and a stable
 // partition of the branch's shots by choice.  Branches with more than
@@ -1139,7 +1477,47 @@ cudaError_t init_kernels() {
     return e;
 }
 
+int pass_reg_blocks_per_sm(int prec, int wp, size_t smem) {
+    int n = 0;
+    const void* f = nullptr;
+    switch (wp * 2 + prec) {
+    case 2: f = (const void*)k_pass_reg<float, 1>; break;
+    case 3: f = (const void*)k_pass_reg<double, 1>; break;
+    case 4: f = (const void*)k_pass_reg<float, 2>; break;
+    case 5: f = (const void*)k_pass_reg<double, 2>; break;
+    case 6: f = (const void*)k_pass_reg<float, 3>; break;
+    case 7: f = (const void*)k_pass_reg<double, 3>; break;
+    case 8: f = (const void*)k_pass_reg<float, 4>; break;
+    default: f = (const void*)k_pass_reg<double, 4>; break;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 256, smem) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n > 0 ? n : 1;
+}
+
+size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads) {
+    const size_t c = prec ? 16 : 8;
+    const size_t nw = threads / 32;
+    return nw * ((size_t)((p.mat_elems + 1) & ~1) * c + 2 * MAX_STAGES * 4);
+}
+
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s) {
+    if (p.reg_wp > 0) {
+        const size_t smem = pass_reg_smem_bytes(prec, p, 256);
+        switch (p.reg_wp * 2 + prec) {
+        case 2: k_pass_reg<float, 1><<<grid, 256, smem, s>>>(d, p); break;
+        case 3: k_pass_reg<double, 1><<<grid, 256, smem, s>>>(d, p); break;
+        case 4: k_pass_reg<float, 2><<<grid, 256, smem, s>>>(d, p); break;
+        case 5: k_pass_reg<double, 2><<<grid, 256, smem, s>>>(d, p); break;
+        case 6: k_pass_reg<float, 3><<<grid, 256, smem, s>>>(d, p); break;
+        case 7: k_pass_reg<double, 3><<<grid, 256, smem, s>>>(d, p); break;
+        case 8: k_pass_reg<float, 4><<<grid, 256, smem, s>>>(d, p); break;
+        default: k_pass_reg<double, 4><<<grid, 256, smem, s>>>(d, p); break;
+        }
+        return cudaGetLastError();
+    }
     const size_t smem = pass_smem_bytes(prec, p, threads);
     if (prec) k_pass<double><<<grid, threads, smem, s>>>(d, p);
     else k_pass<float><<<grid, threads, smem, s>>>(d, p);

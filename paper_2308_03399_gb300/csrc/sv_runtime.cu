@@ -150,6 +150,8 @@ struct sv_batch_s {
     std::vector<uint8_t> pass_store;  // per executed pass: writes the state back
     bool upload_each = false;
     double h2d_bytes = 0;
+    int pass_path = 0;  // 0 auto, 1 shared-memory tiles only
+    std::map<int, int> reg_occ;
     int slot_limit = 0;
 };
 
@@ -182,6 +184,20 @@ int pclass(LType t) {
 
 int pass_grid(sv_batch b, const PassDesc& p) {
     if (b->grid_pass > 0) return b->grid_pass;
+    if (p.reg_wp > 0) {
+        const int prec = b->prec == SV_C128;
+        const size_t smem = pass_reg_smem_bytes(prec, p, 256);
+        const int key = p.reg_wp * 2 + prec;
+        auto it = b->reg_occ.find(key * 4096 + (int)(smem / 64));
+        int per_sm;
+        if (it == b->reg_occ.end()) {
+            per_sm = pass_reg_blocks_per_sm(prec, p.reg_wp, smem);
+            b->reg_occ[key * 4096 + (int)(smem / 64)] = per_sm;
+        } else {
+            per_sm = it->second;
+        }
+        return b->n_sm * per_sm;
+    }
     // k_pass is register-bound at two CTAs of 256 threads per SM; shared
     // memory (tile + matrices + accumulators) may allow fewer
     const size_t smem = pass_smem_bytes(b->prec == SV_C128, p, b->threads) + 2048;
@@ -285,6 +301,19 @@ struct RedSpec {
     int q[MAX_STAGE_Q] = {0, 0, 0, 0};
 };
 
+// can a pass run in registers (k_pass_reg)?  its qubits plus qubit 0 <= 4,
+// dense stages <= 2 qubits, and no reduction or <= 4 one-qubit forms
+int reg_width(sv_batch b, const RedSpec& red, uint64_t act) {
+    if (b->pass_path == 1) return 0;
+    const int wp = __builtin_popcountll(act | 1ull);
+    if (wp > 4) return 0;
+    for (const PendStage& ps : b->pend)
+        if ((ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) && ps.k > 2) return 0;
+    if (red.kind == RED_BINS) return 0;
+    if (red.kind == RED_FORMS && (red.k != 1 || red.R > 4)) return 0;
+    return wp;
+}
+
 sv_status emit_pass(sv_batch b, const RedSpec& red) {
     if (b->pend.empty() && red.kind == RED_NONE) return SV_OK;
     Launch L;
@@ -295,8 +324,11 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
     p.tb = b->tb;
     uint64_t act = b->active;
     for (int j = 0; j < red.k; ++j) act |= 1ull << red.q[j];
-    // tile qubits: qubit 0 (complex64 tiles move amplitude pairs 2j, 2j+1
-    // with one 128-bit access), every active qubit, then the lowest others
+    const int wp = reg_width(b, red, act);
+    if (wp > 0) p.tb = wp;
+    // tile (or register group) qubits: qubit 0 (complex64 moves amplitude
+    // pairs 2j, 2j+1 with one 128-bit access), every active qubit, then the
+    // lowest others
     act |= 1ull;
     std::vector<int> tq;
     for (int q = 0; q < b->n; ++q)
@@ -312,9 +344,14 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
     p.n_nontile = 0;
     for (int q = 0; q < b->n; ++q)
         if (std::find(tq.begin(), tq.end(), q) == tq.end()) p.nontile_q[p.n_nontile++] = q;
-    const int64_t tiles = 1ll << (b->n - p.tb);
     p.chunks = b->chunks;
-    p.tiles_per_chunk = (int)(tiles / b->chunks);
+    p.reg_wp = wp;
+    if (wp > 0) {
+        p.tiles_per_chunk = 1;
+    } else {
+        const int64_t tiles = 1ll << (b->n - p.tb);
+        p.tiles_per_chunk = (int)(tiles / b->chunks);
+    }
     int mat = 0;
     p.n_stages = (int)b->pend.size();
     for (int s = 0; s < p.n_stages; ++s) {
@@ -333,6 +370,9 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
         if (ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) {
             st.mat = mat;
             mat += 1 << (2 * ps.k);
+        } else if (ps.kind == ST_PROJ_BR && wp > 0) {
+            st.mat = mat;  // the register path keeps the scale here
+            mat += 1;
         }
     }
     p.store = p.n_stages > 0;
@@ -1008,6 +1048,10 @@ sv_status sv_set_option(sv_batch b, sv_option opt, int64_t v) {
     case SV_OPT_GRID: b->grid_pass = (int)std::max<int64_t>(0, v); return SV_OK;
     case SV_OPT_PROFILE: b->profile = v != 0; return SV_OK;
     case SV_OPT_UPLOAD: b->upload_each = v != 0; return SV_OK;
+    case SV_OPT_PASS_PATH:
+        if (v < 0 || v > 1) return fail(SV_EINVAL, "pass path must be 0 (auto) or 1 (shared-memory tiles)");
+        b->pass_path = (int)v;
+        return SV_OK;
     case SV_OPT_SLOT_LIMIT:
         if (v < 0) return fail(SV_EINVAL, "slot limit must be >= 0");
         b->slot_limit = (int)v;

@@ -37,6 +37,28 @@ def test_small_circuits_match_oracle(name, mode, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["su4_kraus", "midmeasure", "qft_kraus"])
+def test_shared_memory_tile_path_matches_oracle(name, prec):
+    # the same circuits with every pass forced onto shared-memory tiles
+    c = SMALL[name]()
+    gpu = run_gpu(c, 13, 200, sv.SV_BRANCH, prec, opts={sv.SV_OPT_PASS_PATH: 1}, want_amps=[0, 99])
+    compare_shots(c, 13, gpu, range(200), prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_register_and_tile_paths_agree_on_config2_prefix(prec):
+    # first 3 layers of config 2 at 16 qubits: every pass fits the register
+    # path; forcing shared-memory tiles must give the same choices
+    c = W.random_su4(16, 3, 1e-2, 5e-3, seed=2)
+    a = run_gpu(c, 2, 300, sv.SV_BRANCH, prec, want_amps=[0, 7])
+    b = run_gpu(c, 2, 300, sv.SV_BRANCH, prec, opts={sv.SV_OPT_PASS_PATH: 1}, want_amps=[0, 7])
+    compare_shots(c, 2, a, range(0, 300, 3), prec)
+    compare_shots(c, 2, b, range(0, 300, 3), prec)
+    for s in (0, 7):
+        assert np.abs(a["amps"][s] - b["amps"][s]).max() < (1e-5 if prec == sv.SV_C64 else 1e-12)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_batch_and_branch_logs_identical(prec):
     c = W.random_su4(6, 5, 0.08, 0.1, seed=31)
     a = run_gpu(c, 3, 400, sv.SV_BATCH, prec)
