@@ -112,8 +112,11 @@ typedef enum {
     SV_OPT_SLOT_LIMIT = 7,  /* cap on state slots (0 = as many as fit); forces waiting  */
     SV_OPT_UPLOAD = 8,      /* 1: sv_run_circuit copies the circuit's constants to the
                                device on every call, even when its graph is cached   */
-    SV_OPT_PASS_PATH = 9    /* 0: passes of <= 4 qubits run in registers, others in
+    SV_OPT_PASS_PATH = 9,   /* 0: passes of <= 4 qubits run in registers, others in
                                shared-memory tiles; 1: shared-memory tiles only      */
+    SV_OPT_JOINT_KRAUS = 10 /* 1 (default): sv_run_circuit decides two back-to-back
+                               one-qubit Kraus ops on different qubits from one pass
+                               (joint probabilities ||K2_j K1_i psi||^2)             */
 } sv_option;
 
 /* Allocate a batch of n_shots shots of an n_qubits register.

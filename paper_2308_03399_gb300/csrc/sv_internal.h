@@ -24,8 +24,11 @@ enum : int32_t {
     ST_PAULI_BR = 2,  // per-branch Pauli string from its 4 parameters (Section IV-A-3)
     ST_PROJ_BR = 3    // per-branch projection onto the measured outcome, optional reset
 };
-enum : int32_t { RED_NONE = 0, RED_FORMS = 1, RED_BINS = 2 };
-enum : int32_t { DEC_PAULI = 0, DEC_KRAUS = 1, DEC_MEASURE = 2 };
+enum : int32_t { RED_NONE = 0, RED_FORMS = 1, RED_BINS = 2, RED_DIAG = 3 };
+// DEC_KRAUS_J1 / _J2: two one-qubit Kraus ops on different qubits decided
+// from one joint reduction p_ij = ||K2_j K1_i psi||^2 (partials indexed
+// i * r2 + j): op 1 from p_i = sum_j p_ij, op 2 from p_ij / p_i
+enum : int32_t { DEC_PAULI = 0, DEC_KRAUS = 1, DEC_MEASURE = 2, DEC_KRAUS_J1 = 3, DEC_KRAUS_J2 = 4 };
 
 // error word codes
 enum : int32_t { ERR_NONE = 0, ERR_SLOT = 1, ERR_INDEX = 2, ERR_GROUPS = 3, ERR_TIMEOUT = 4 };
@@ -58,6 +61,7 @@ struct PassDesc {
     int32_t red_kind, red_k, red_R, red_off;
     int32_t red_pos[MAX_STAGE_Q];
     int32_t reg_wp;            // > 0: register path (k_pass_reg), group of 2^reg_wp amplitudes
+    int32_t reg_paired;        // register path: qubit 0 is group bit 0 (128-bit pairs)
     Stage st[MAX_STAGES];
 };
 
@@ -70,6 +74,8 @@ struct DecideDesc {
     int32_t fork;              // shot-branching on
     int32_t m;                 // measured qubits
     int32_t clbit[MAX_STAGE_Q];
+    int32_t r2;                // joint Kraus: terms of the second op (partials stride)
+    int32_t pend_prev;         // DEC_KRAUS_J2: pending column of the first op's choice
     int32_t* log_sel;          // per shot id, nullable
     double* log_thr;           // 2 per shot id, nullable
     double cum[MAX_TERMS];     // Pauli cumulative table
@@ -148,7 +154,7 @@ cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s);
 cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s);
 size_t pass_smem_bytes(int prec, const PassDesc& p, int threads);
 size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads);
-int pass_reg_blocks_per_sm(int prec, int wp, size_t smem);
+int pass_reg_blocks_per_sm(int prec, int wp, int paired, size_t smem);
 cudaError_t init_kernels();
 
 }  // namespace sv

@@ -639,9 +639,7 @@ __device__ __forceinline__ void reg_apply1(T* v, const T* M) {
 // 2-qubit matrix, matrix bit 0 on group bit J0, matrix bit 1 on group bit J1
 template <class T, int G, int J0, int J1>
 __device__ __forceinline__ void reg_apply2(T* v, const T* M) {
-    T m[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) m[e] = M[e];
+    const T* m = M;  // shared memory, read per use (keeps registers for the group)
 #pragma unroll
     for (int r = 0; r < G; ++r) {
         if (r & ((1 << J0) | (1 << J1))) continue;
@@ -660,6 +658,30 @@ __device__ __forceinline__ void reg_apply2(T* v, const T* M) {
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[i[c]] = o[c];
+    }
+}
+
+// diagonal (shape 1) or anti-diagonal (shape 2) one-qubit matrix
+template <class T, int G, int J>
+__device__ __forceinline__ void reg_apply1_sparse(T* v, const T* M, int shape) {
+    const T m0 = shape == 1 ? M[0] : M[1], m1 = shape == 1 ? M[3] : M[2];
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+        if (r & (1 << J)) continue;
+        const int r1 = r | (1 << J);
+        const T a = shape == 1 ? v[r] : v[r1], b = shape == 1 ? v[r1] : v[r];
+        v[r] = cmul(m0, a);
+        v[r1] = cmul(m1, b);
+    }
+}
+
+template <class T, int G>
+__device__ __forceinline__ void reg_apply1s_dyn(T* v, int j, const T* M, int shape) {
+    switch (j) {
+    case 0: reg_apply1_sparse<T, G, 0>(v, M, shape); break;
+    case 1: if constexpr (G > 2) reg_apply1_sparse<T, G, 1>(v, M, shape); break;
+    case 2: if constexpr (G > 4) reg_apply1_sparse<T, G, 2>(v, M, shape); break;
+    default: if constexpr (G > 8) reg_apply1_sparse<T, G, 3>(v, M, shape); break;
     }
 }
 
@@ -748,11 +770,63 @@ __device__ __forceinline__ void reg_forms1_dyn(const typename Cplx<R>::T* v, int
 
 constexpr int REG_MAX_RED = 4;
 
-template <class R, int WP>
+// diagonal forms (sum_r w_f[r] |v_r|^2 over the 2^k amplitudes of the
+// reduced qubits): every group first collects |v|^2 into the 2^k bins of the
+// reduced qubits (compile-time bin of each amplitude), then weights the
+// bins (float32) and adds the group totals to the float-float accumulators
+template <class R, int G, int J0, int J1>
+__device__ __forceinline__ void reg_diag_bins(const typename Cplx<R>::T* v, R* q) {
+#pragma unroll
+    for (int e = 0; e < G; ++e) {
+        const int idx = ((e >> J0) & 1) | (J1 >= 0 ? ((e >> (J1 < 0 ? 0 : J1)) & 1) << 1 : 0);
+        q[idx] += v[e].x * v[e].x + v[e].y * v[e].y;
+    }
+}
+
+template <class R, int G>
+__device__ __forceinline__ void reg_diag(const typename Cplx<R>::T* v, const PassDesc& p,
+                                         const typename Cplx<R>::T* W, Acc<R>* acc) {
+    R q[4] = {0, 0, 0, 0};
+    if (p.red_k == 1) {
+        switch (p.red_pos[0]) {
+        case 0: reg_diag_bins<R, G, 0, -1>(v, q); break;
+        case 1: if constexpr (G > 2) reg_diag_bins<R, G, 1, -1>(v, q); break;
+        case 2: if constexpr (G > 4) reg_diag_bins<R, G, 2, -1>(v, q); break;
+        default: if constexpr (G > 8) reg_diag_bins<R, G, 3, -1>(v, q); break;
+        }
+    } else {
+        switch (p.red_pos[0] * 4 + p.red_pos[1]) {
+        case 1: if constexpr (G > 2) reg_diag_bins<R, G, 0, 1>(v, q); break;
+        case 4: if constexpr (G > 2) reg_diag_bins<R, G, 1, 0>(v, q); break;
+        case 2: if constexpr (G > 4) reg_diag_bins<R, G, 0, 2>(v, q); break;
+        case 8: if constexpr (G > 4) reg_diag_bins<R, G, 2, 0>(v, q); break;
+        case 6: if constexpr (G > 4) reg_diag_bins<R, G, 1, 2>(v, q); break;
+        case 9: if constexpr (G > 4) reg_diag_bins<R, G, 2, 1>(v, q); break;
+        case 3: if constexpr (G > 8) reg_diag_bins<R, G, 0, 3>(v, q); break;
+        case 12: if constexpr (G > 8) reg_diag_bins<R, G, 3, 0>(v, q); break;
+        case 7: if constexpr (G > 8) reg_diag_bins<R, G, 1, 3>(v, q); break;
+        case 13: if constexpr (G > 8) reg_diag_bins<R, G, 3, 1>(v, q); break;
+        case 11: if constexpr (G > 8) reg_diag_bins<R, G, 2, 3>(v, q); break;
+        default: if constexpr (G > 8) reg_diag_bins<R, G, 3, 2>(v, q); break;
+        }
+    }
+    const int D = 1 << p.red_k;
+#pragma unroll
+    for (int f = 0; f < REG_MAX_RED; ++f) {
+        if (f >= p.red_R) break;
+        R loc = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (r < D) loc += W[f * D + r].x * q[r];
+        acc[f].add(loc);
+    }
+}
+
+template <class R, int WP, int PAIRED>
 __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_constant__ PassDesc p) {
     using T = typename Cplx<R>::T;
     constexpr int G = 1 << WP;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     // per-warp shared memory: matrices | stage choice | stage packed | stage scale
     const int mat_stride = (p.mat_elems + 1) & ~1;
@@ -826,6 +900,12 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
                         m.y = src[2 * e + 1] * sc;
                         mats[st.mat + e] = m;
                     }
+                    if (st.k == 1 && lane == 0) {
+                        // structure of a one-qubit matrix: 1 diagonal, 2 anti-diagonal
+                        const bool off0 = src[2] == 0 && src[3] == 0 && src[4] == 0 && src[5] == 0;
+                        const bool diag0 = src[0] == 0 && src[1] == 0 && src[6] == 0 && src[7] == 0;
+                        w_packed[s] = off0 ? 1 : (diag0 ? 2 : 0);
+                    }
                 } else if (!sk && st.kind == ST_PROJ_BR && lane == 0) {
                     T m;
                     m.x = (R)scale;
@@ -833,13 +913,14 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
                     mats[st.mat] = m;
                 }
             }
-            if (p.red_kind == RED_FORMS) {
+            if (p.red_kind == RED_FORMS || p.red_kind == RED_DIAG) {
+                const int E = p.red_kind == RED_FORMS ? 4 * p.red_R : p.red_R << p.red_k;
                 const R* src = pool + p.red_off;
-                for (int e = lane; e < p.red_R * 4; e += 32) {
+                for (int e = lane; e < E; e += 32) {
                     T m;
                     m.x = src[2 * e];
                     m.y = src[2 * e + 1];
-                    mats[p.mat_elems - p.red_R * 4 + e] = m;
+                    mats[p.mat_elems - E + e] = m;
                 }
             }
             __syncwarp();
@@ -859,7 +940,7 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
             }
             T* g = gstate + base;
             T v[G];
-            if constexpr (sizeof(T) == 8) {
+            if constexpr (sizeof(T) == 8 && PAIRED) {
 #pragma unroll
                 for (int e = 0; e < G; e += 2) {
                     const float4 x = *reinterpret_cast<const float4*>(g + off[e]);
@@ -876,8 +957,13 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
                 if ((skipmask >> s) & 1) continue;
                 const Stage& st = p.st[s];
                 if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
-                    if (st.k == 1) reg_apply1_dyn<T, G>(v, st.pos[0], mats + st.mat);
-                    else reg_apply2_dyn<T, G>(v, st.pos[0], st.pos[1], mats + st.mat);
+                    if (st.k == 1) {
+                        const int shape = w_packed[s];
+                        if (shape) reg_apply1s_dyn<T, G>(v, st.pos[0], mats + st.mat, shape);
+                        else reg_apply1_dyn<T, G>(v, st.pos[0], mats + st.mat);
+                    } else {
+                        reg_apply2_dyn<T, G>(v, st.pos[0], st.pos[1], mats + st.mat);
+                    }
                 } else if (st.kind == ST_PAULI_BR) {
                     const int packed = w_packed[s];
                     int zg = 0;
@@ -922,9 +1008,12 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
                             if ((sel >> j) & 1) reg_flip_dyn<T, G>(v, st.pos[j]);
                 }
             }
-            if (red) reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - p.red_R * 4, p.red_R, acc);
+            if (p.red_kind == RED_FORMS)
+                reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - p.red_R * 4, p.red_R, acc);
+            else if (p.red_kind == RED_DIAG)
+                reg_diag<R, G>(v, p, mats + p.mat_elems - (p.red_R << p.red_k), acc);
             if (p.store) {
-                if constexpr (sizeof(T) == 8) {
+                if constexpr (sizeof(T) == 8 && PAIRED) {
 #pragma unroll
                     for (int e = 0; e < G; e += 2)
                         *reinterpret_cast<float4*>(g + off[e]) = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
@@ -957,11 +1046,33 @@ constexpr int DEC_THREADS = 512;
 constexpr int DEC_SMALL = 64;
 
 // probabilities and cumulative table of branch b into p_out / cum_out
-__device__ __forceinline__ void decide_probs(const DevBatch& d, const DecideDesc& dd, int slot, int r,
+// (cum_out only for Pauli; the caller forms the running sum otherwise)
+__device__ __forceinline__ void decide_probs(const DevBatch& d, const DecideDesc& dd, int b, int slot, int r,
                                              double* p_out, double* cum_out) {
     if (dd.kind == DEC_PAULI) {
         p_out[r] = dd.cum[r] - (r ? dd.cum[r - 1] : 0.0);
         cum_out[r] = dd.cum[r];
+    } else if (dd.kind == DEC_KRAUS_J1) {
+        const double* pp = d.partials + (int64_t)slot * d.max_chunks * MAX_RED + r * dd.r2;
+        double s = 0.0;
+        for (int c = 0; c < dd.chunks; ++c)
+            for (int j = 0; j < dd.r2; ++j) s += pp[(int64_t)c * MAX_RED + j];
+        p_out[r] = s;
+    } else if (dd.kind == DEC_KRAUS_J2) {
+        // branches forked by the first op still find the joint partials in
+        // their parent's slot
+        const int cf = d.ctl[CTL_COPY_FIRST], ce = d.ctl[CTL_COPY_END];
+        const int src = (b >= cf && b < ce) ? d.br_slot[d.br_parent[b]] : slot;
+        const int i = d.br_sel[(int64_t)dd.pend_prev * d.cap_br + b];
+        const double* pp = d.partials + (int64_t)src * d.max_chunks * MAX_RED + i * dd.R;
+        double pi = 0.0, pr = 0.0;
+        for (int j = 0; j < dd.R; ++j) {
+            double s = 0.0;
+            for (int c = 0; c < dd.chunks; ++c) s += pp[(int64_t)c * MAX_RED + j];
+            pi += s;
+            if (j == r) pr = s;
+        }
+        p_out[r] = pr / pi;
     } else {
         const double* pp = d.partials + (int64_t)slot * d.max_chunks * MAX_RED + r;
         double s = 0.0;
@@ -1029,7 +1140,7 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
         const int slot = d.br_slot[b], start = d.br_start[b];
         __syncthreads();
         if (tid < R) {
-            decide_probs(d, dd, slot, tid, p_sh, cum_sh);
+            decide_probs(d, dd, b, slot, tid, p_sh, cum_sh);
             bincnt[tid] = 0;
             binrun[tid] = 0;
         }
@@ -1104,7 +1215,7 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
         if (cnt > DEC_SMALL) continue;
         const int slot = d.br_slot[b], start = d.br_start[b];
         for (int r = lane; r < R; r += 32) {
-            decide_probs(d, dd, slot, r, p, cum);
+            decide_probs(d, dd, b, slot, r, p, cum);
             bc[r] = 0;
             br[r] = 0;
         }
@@ -1477,20 +1588,36 @@ cudaError_t init_kernels() {
     return e;
 }
 
-int pass_reg_blocks_per_sm(int prec, int wp, size_t smem) {
-    int n = 0;
-    const void* f = nullptr;
-    switch (wp * 2 + prec) {
-    case 2: f = (const void*)k_pass_reg<float, 1>; break;
-    case 3: f = (const void*)k_pass_reg<double, 1>; break;
-    case 4: f = (const void*)k_pass_reg<float, 2>; break;
-    case 5: f = (const void*)k_pass_reg<double, 2>; break;
-    case 6: f = (const void*)k_pass_reg<float, 3>; break;
-    case 7: f = (const void*)k_pass_reg<double, 3>; break;
-    case 8: f = (const void*)k_pass_reg<float, 4>; break;
-    default: f = (const void*)k_pass_reg<double, 4>; break;
+template <class R, int WP, int PAIRED> const void* reg_fn() { return (const void*)k_pass_reg<R, WP, PAIRED>; }
+
+const void* pass_reg_fn(int prec, int wp, int paired) {
+    if (prec) {
+        switch (wp) {
+        case 1: return reg_fn<double, 1, 0>();
+        case 2: return reg_fn<double, 2, 0>();
+        case 3: return reg_fn<double, 3, 0>();
+        default: return reg_fn<double, 4, 0>();
+        }
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 256, smem) != cudaSuccess) {
+    if (paired) {
+        switch (wp) {
+        case 1: return reg_fn<float, 1, 1>();
+        case 2: return reg_fn<float, 2, 1>();
+        case 3: return reg_fn<float, 3, 1>();
+        default: return reg_fn<float, 4, 1>();
+        }
+    }
+    switch (wp) {
+    case 1: return reg_fn<float, 1, 0>();
+    case 2: return reg_fn<float, 2, 0>();
+    case 3: return reg_fn<float, 3, 0>();
+    default: return reg_fn<float, 4, 0>();
+    }
+}
+
+int pass_reg_blocks_per_sm(int prec, int wp, int paired, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pass_reg_fn(prec, wp, paired), 256, smem) != cudaSuccess) {
         cudaGetLastError();
         n = 1;
     }
@@ -1506,17 +1633,9 @@ size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads) {
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s) {
     if (p.reg_wp > 0) {
         const size_t smem = pass_reg_smem_bytes(prec, p, 256);
-        switch (p.reg_wp * 2 + prec) {
-        case 2: k_pass_reg<float, 1><<<grid, 256, smem, s>>>(d, p); break;
-        case 3: k_pass_reg<double, 1><<<grid, 256, smem, s>>>(d, p); break;
-        case 4: k_pass_reg<float, 2><<<grid, 256, smem, s>>>(d, p); break;
-        case 5: k_pass_reg<double, 2><<<grid, 256, smem, s>>>(d, p); break;
-        case 6: k_pass_reg<float, 3><<<grid, 256, smem, s>>>(d, p); break;
-        case 7: k_pass_reg<double, 3><<<grid, 256, smem, s>>>(d, p); break;
-        case 8: k_pass_reg<float, 4><<<grid, 256, smem, s>>>(d, p); break;
-        default: k_pass_reg<double, 4><<<grid, 256, smem, s>>>(d, p); break;
-        }
-        return cudaGetLastError();
+        const void* f = pass_reg_fn(prec, p.reg_wp, p.reg_paired && !prec);
+        void* args[] = {(void*)&d, (void*)&p};
+        return cudaLaunchKernel(f, dim3(grid), dim3(256), args, smem, s);
     }
     const size_t smem = pass_smem_bytes(prec, p, threads);
     if (prec) k_pass<double><<<grid, threads, smem, s>>>(d, p);

@@ -151,6 +151,7 @@ struct sv_batch_s {
     bool upload_each = false;
     double h2d_bytes = 0;
     int pass_path = 0;  // 0 auto, 1 shared-memory tiles only
+    bool joint = true;  // decide back-to-back one-qubit Kraus pairs from one pass
     std::map<int, int> reg_occ;
     int slot_limit = 0;
 };
@@ -187,11 +188,11 @@ int pass_grid(sv_batch b, const PassDesc& p) {
     if (p.reg_wp > 0) {
         const int prec = b->prec == SV_C128;
         const size_t smem = pass_reg_smem_bytes(prec, p, 256);
-        const int key = p.reg_wp * 2 + prec;
+        const int key = (p.reg_wp * 2 + prec) * 2 + p.reg_paired;
         auto it = b->reg_occ.find(key * 4096 + (int)(smem / 64));
         int per_sm;
         if (it == b->reg_occ.end()) {
-            per_sm = pass_reg_blocks_per_sm(prec, p.reg_wp, smem);
+            per_sm = pass_reg_blocks_per_sm(prec, p.reg_wp, p.reg_paired, smem);
             b->reg_occ[key * 4096 + (int)(smem / 64)] = per_sm;
         } else {
             per_sm = it->second;
@@ -298,6 +299,7 @@ int local_pos(const int* tile_q, int tb, int q) {
 // Flush queued stages as one pass; optionally end it with a reduction.
 struct RedSpec {
     int kind = RED_NONE, k = 0, R = 0, off = 0;
+    int diag_off = -1;  // RED_FORMS whose forms are all diagonal: weights here
     int q[MAX_STAGE_Q] = {0, 0, 0, 0};
 };
 
@@ -305,12 +307,13 @@ struct RedSpec {
 // dense stages <= 2 qubits, and no reduction or <= 4 one-qubit forms
 int reg_width(sv_batch b, const RedSpec& red, uint64_t act) {
     if (b->pass_path == 1) return 0;
-    const int wp = __builtin_popcountll(act | 1ull);
-    if (wp > 4) return 0;
+    const int wp = __builtin_popcountll(act);
+    if (wp > 4 || wp < 1) return 0;
     for (const PendStage& ps : b->pend)
         if ((ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) && ps.k > 2) return 0;
     if (red.kind == RED_BINS) return 0;
-    if (red.kind == RED_FORMS && (red.k != 1 || red.R > 4)) return 0;
+    if (red.kind == RED_FORMS && red.R > 4) return 0;
+    if (red.kind == RED_FORMS && red.k != 1 && red.diag_off < 0) return 0;
     return wp;
 }
 
@@ -325,11 +328,16 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
     uint64_t act = b->active;
     for (int j = 0; j < red.k; ++j) act |= 1ull << red.q[j];
     const int wp = reg_width(b, red, act);
-    if (wp > 0) p.tb = wp;
-    // tile (or register group) qubits: qubit 0 (complex64 moves amplitude
-    // pairs 2j, 2j+1 with one 128-bit access), every active qubit, then the
-    // lowest others
-    act |= 1ull;
+    if (wp > 0) {
+        // register group: exactly the pass's qubits; with qubit 0 among them
+        // complex64 amplitudes move as 128-bit pairs
+        p.tb = wp;
+        p.reg_paired = (int)(act & 1ull);
+    } else {
+        // tile: qubit 0 (complex64 moves amplitude pairs 2j, 2j+1 with one
+        // 128-bit access), every active qubit, then the lowest others
+        act |= 1ull;
+    }
     std::vector<int> tq;
     for (int q = 0; q < b->n; ++q)
         if ((act >> q) & 1) tq.push_back(q);
@@ -380,8 +388,13 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
     p.red_k = red.k;
     p.red_R = red.R;
     p.red_off = red.off;
+    if (wp > 0 && red.kind == RED_FORMS && red.diag_off >= 0) {
+        p.red_kind = RED_DIAG;
+        p.red_off = red.diag_off;
+    }
     for (int j = 0; j < red.k; ++j) p.red_pos[j] = local_pos(p.tile_q, p.tb, red.q[j]);
-    if (red.kind == RED_FORMS) mat += red.R << (2 * red.k);
+    if (p.red_kind == RED_FORMS) mat += red.R << (2 * red.k);
+    else if (p.red_kind == RED_DIAG) mat += red.R << red.k;
     p.mat_elems = mat;
     b->pend.clear();
     b->active = 0;
@@ -464,7 +477,7 @@ sv_status get_log(sv_batch b, uint32_t op, int32_t** sel, double** thr) {
 
 // decide (+ fork) for random op `op`; the chosen term is then queued as a stage
 sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cum, int pend, int m,
-                      const int* clbits) {
+                      const int* clbits, int r2 = 0, int pend_prev = -1) {
     Launch L;
     L.type = L_DECIDE;
     DecideDesc& d = L.dec;
@@ -476,6 +489,8 @@ sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cu
     d.chunks = b->chunks;
     d.fork = b->branch;
     d.m = m;
+    d.r2 = r2;
+    d.pend_prev = pend_prev;
     for (int j = 0; j < m; ++j) d.clbit[j] = clbits[j];
     if (cum)
         for (int t = 0; t < R; ++t) d.cum[t] = cum[t];
@@ -574,16 +589,10 @@ sv_status op_pauli(sv_batch b, uint32_t op, int k, const int* q, int n_terms, co
     return SV_OK;
 }
 
-sv_status op_kraus(sv_batch b, uint32_t op, int k, const int* q, int n_terms, const double* kraus) {
-    sv_status st = check_qubits(b, k, q);
-    if (st) return st;
-    if (k < 1 || k > 2) return fail(SV_EUNSUPPORTED, "Kraus noise acts on 1 or 2 qubits");
-    if (n_terms < 1 || n_terms > MAX_RED) return fail(SV_EUNSUPPORTED, "Kraus noise has 1 to 16 matrices");
-    if (!kraus) return fail(SV_EINVAL, "Kraus matrices are NULL");
+// F_i = K_i^dagger K_i of every term (row-major complex)
+std::vector<std::complex<double>> kraus_forms(const double* kraus, int k, int n_terms) {
     const int D = 1 << k, E = D * D;
-    // forms F_i = K_i^dagger K_i, and the completeness check sum F_i = I
-    std::vector<double> forms(2 * E * n_terms);
-    std::vector<std::complex<double>> tot(E);
+    std::vector<std::complex<double>> F((size_t)E * n_terms);
     for (int t = 0; t < n_terms; ++t) {
         const double* K = kraus + 2 * E * t;
         for (int i = 0; i < D; ++i)
@@ -592,15 +601,56 @@ sv_status op_kraus(sv_batch b, uint32_t op, int k, const int* q, int n_terms, co
                 for (int r = 0; r < D; ++r)
                     s += std::conj(std::complex<double>(K[2 * (r * D + i)], K[2 * (r * D + i) + 1])) *
                          std::complex<double>(K[2 * (r * D + j)], K[2 * (r * D + j) + 1]);
-                forms[2 * (E * t + i * D + j)] = s.real();
-                forms[2 * (E * t + i * D + j) + 1] = s.imag();
-                tot[i * D + j] += s;
+                F[(size_t)E * t + i * D + j] = s;
             }
     }
+    return F;
+}
+
+bool kraus_complete(const std::vector<std::complex<double>>& F, int k, int n_terms) {
+    const int D = 1 << k, E = D * D;
     for (int i = 0; i < D; ++i)
-        for (int j = 0; j < D; ++j)
-            if (std::abs(tot[i * D + j] - (i == j ? 1.0 : 0.0)) > 1e-10)
-                return fail(SV_EINVAL, "Kraus matrices are not complete (sum K^dagger K != I)");
+        for (int j = 0; j < D; ++j) {
+            std::complex<double> s = 0;
+            for (int t = 0; t < n_terms; ++t) s += F[(size_t)E * t + i * D + j];
+            if (std::abs(s - (i == j ? 1.0 : 0.0)) > 1e-10) return false;
+        }
+    return true;
+}
+
+// push forms (and, when all are diagonal, their diagonals) into the pool
+void push_forms(sv_batch b, const std::vector<std::complex<double>>& F, int k, int R, RedSpec& red) {
+    const int D = 1 << k, E = D * D;
+    red.off = (int)b->pool.size();
+    bool diag = true;
+    for (int f = 0; f < R; ++f)
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                const std::complex<double> v = F[(size_t)E * f + i * D + j];
+                b->pool.push_back(v.real());
+                b->pool.push_back(v.imag());
+                if (i != j && v != 0.0) diag = false;
+            }
+    red.diag_off = -1;
+    if (diag) {
+        red.diag_off = (int)b->pool.size();
+        for (int f = 0; f < R; ++f)
+            for (int i = 0; i < D; ++i) {
+                b->pool.push_back(F[(size_t)E * f + i * D + i].real());
+                b->pool.push_back(0.0);
+            }
+    }
+}
+
+sv_status op_kraus(sv_batch b, uint32_t op, int k, const int* q, int n_terms, const double* kraus) {
+    sv_status st = check_qubits(b, k, q);
+    if (st) return st;
+    if (k < 1 || k > 2) return fail(SV_EUNSUPPORTED, "Kraus noise acts on 1 or 2 qubits");
+    if (n_terms < 1 || n_terms > MAX_RED) return fail(SV_EUNSUPPORTED, "Kraus noise has 1 to 16 matrices");
+    if (!kraus) return fail(SV_EINVAL, "Kraus matrices are NULL");
+    const int D = 1 << k, E = D * D;
+    const std::vector<std::complex<double>> F = kraus_forms(kraus, k, n_terms);
+    if (!kraus_complete(F, k, n_terms)) return fail(SV_EINVAL, "Kraus matrices are not complete (sum K^dagger K != I)");
     if ((st = ensure_started(b))) return st;
     // the reduction must see every earlier op: queued stages + forms in one pass
     uint64_t act = b->active;
@@ -612,8 +662,7 @@ sv_status op_kraus(sv_batch b, uint32_t op, int k, const int* q, int n_terms, co
     red.k = k;
     red.R = n_terms;
     for (int j = 0; j < k; ++j) red.q[j] = q[j];
-    red.off = (int)b->pool.size();
-    for (double v : forms) b->pool.push_back(v);
+    push_forms(b, F, k, n_terms, red);
     const int mat_off = (int)b->pool.size();
     for (int i = 0; i < 2 * E * n_terms; ++i) b->pool.push_back(kraus[i]);
     if ((st = upload_pool(b))) return st;
@@ -629,6 +678,65 @@ sv_status op_kraus(sv_batch b, uint32_t op, int k, const int* q, int n_terms, co
     s.off = mat_off;
     s.stride = 2 * E;
     if ((st = make_room(b, q, k, E, true))) return st;
+    add_stage(b, s);
+    return SV_OK;
+}
+
+// Two one-qubit Kraus ops on different qubits, back to back: one pass
+// reduces the joint probabilities p_ij = ||K2_j K1_i psi||^2 (forms
+// F1_i (x) F2_j); op 1 is decided from p_i = sum_j p_ij = ||K1_i psi||^2 and
+// op 2, per branch, from p_ij / p_i = ||K2_j (K1_i psi / sqrt(p_i))||^2,
+// which is the sequential rule of Section III-B-2 computed in one pass.
+sv_status op_kraus_pair(sv_batch b, uint32_t op1, int qa, int n1, const double* k1, uint32_t op2, int qb, int n2,
+                        const double* k2) {
+    sv_status st;
+    int qs[2] = {qa, qb};
+    if ((st = check_qubits(b, 2, qs))) return st;
+    if (!k1 || !k2) return fail(SV_EINVAL, "Kraus matrices are NULL");
+    const std::vector<std::complex<double>> F1 = kraus_forms(k1, 1, n1), F2 = kraus_forms(k2, 1, n2);
+    if (!kraus_complete(F1, 1, n1) || !kraus_complete(F2, 1, n2))
+        return fail(SV_EINVAL, "Kraus matrices are not complete (sum K^dagger K != I)");
+    if ((st = ensure_started(b))) return st;
+    uint64_t act = b->active | (1ull << qa) | (1ull << qb);
+    if (!fits(b, act) || b->mat_used + n1 * n2 * 16 + 4 * (n1 + n2) > MAT_SMEM - 256)
+        if ((st = flush(b))) return st;
+    // joint forms on [qa, qb]: matrix index bit 0 <-> qa, bit 1 <-> qb
+    std::vector<std::complex<double>> F((size_t)16 * n1 * n2);
+    for (int i = 0; i < n1; ++i)
+        for (int j = 0; j < n2; ++j)
+            for (int r = 0; r < 4; ++r)
+                for (int c = 0; c < 4; ++c)
+                    F[(size_t)16 * (i * n2 + j) + r * 4 + c] = F1[4 * i + (r & 1) * 2 + (c & 1)] *
+                                                              F2[4 * j + (r >> 1) * 2 + (c >> 1)];
+    RedSpec red;
+    red.kind = RED_FORMS;
+    red.k = 2;
+    red.R = n1 * n2;
+    red.q[0] = qa;
+    red.q[1] = qb;
+    push_forms(b, F, 2, n1 * n2, red);
+    const int m1 = (int)b->pool.size();
+    for (int i = 0; i < 8 * n1; ++i) b->pool.push_back(k1[i]);
+    const int m2 = (int)b->pool.size();
+    for (int i = 0; i < 8 * n2; ++i) b->pool.push_back(k2[i]);
+    if ((st = upload_pool(b))) return st;
+    if ((st = emit_pass(b, red))) return st;
+    const int pend1 = b->n_pend++;
+    if ((st = emit_decide(b, op1, DEC_KRAUS_J1, n1, nullptr, pend1, 0, nullptr, n2, -1))) return st;
+    const int pend2 = b->n_pend++;
+    if ((st = emit_decide(b, op2, DEC_KRAUS_J2, n2, nullptr, pend2, 0, nullptr, n2, pend1))) return st;
+    PendStage s{};
+    s.kind = ST_DENSE_BR;
+    s.k = 1;
+    s.cond_clbit = -1;
+    s.q[0] = qa;
+    s.pend = pend1;
+    s.off = m1;
+    s.stride = 8;
+    add_stage(b, s);
+    s.q[0] = qb;
+    s.pend = pend2;
+    s.off = m2;
     add_stage(b, s);
     return SV_OK;
 }
@@ -1048,6 +1156,7 @@ sv_status sv_set_option(sv_batch b, sv_option opt, int64_t v) {
     case SV_OPT_GRID: b->grid_pass = (int)std::max<int64_t>(0, v); return SV_OK;
     case SV_OPT_PROFILE: b->profile = v != 0; return SV_OK;
     case SV_OPT_UPLOAD: b->upload_each = v != 0; return SV_OK;
+    case SV_OPT_JOINT_KRAUS: b->joint = v != 0; return SV_OK;
     case SV_OPT_PASS_PATH:
         if (v < 0 || v > 1) return fail(SV_EINVAL, "pass path must be 0 (auto) or 1 (shared-memory tiles)");
         b->pass_path = (int)v;
@@ -1169,7 +1278,18 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
         b->started = true;  // reset / init are issued below, per run
         b->rec = &launches;
         b->n_pend = 0;
-        for (int i = 0; i < c->n_ops && !st; ++i) st = circuit_op(b, c, i);
+        for (int i = 0; i < c->n_ops && !st; ++i) {
+            if (b->joint && i + 1 < c->n_ops && c->kind[i] == SV_OP_KRAUS && c->kind[i + 1] == SV_OP_KRAUS &&
+                c->nq[i] == 1 && c->nq[i + 1] == 1 && c->qubits[c->q_off[i]] != c->qubits[c->q_off[i + 1]] &&
+                c->n_terms[i] * c->n_terms[i + 1] <= MAX_RED) {
+                st = op_kraus_pair(b, (uint32_t)i, c->qubits[c->q_off[i]], c->n_terms[i], c->data + c->d_off[i],
+                                   (uint32_t)(i + 1), c->qubits[c->q_off[i + 1]], c->n_terms[i + 1],
+                                   c->data + c->d_off[i + 1]);
+                ++i;
+                continue;
+            }
+            st = circuit_op(b, c, i);
+        }
         if (!st) st = flush(b);
         b->rec = nullptr;
         if (st) return st;

@@ -59,6 +59,18 @@ def test_register_and_tile_paths_agree_on_config2_prefix(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_joint_and_separate_kraus_decisions_match_oracle(prec):
+    # back-to-back damping on the two qubits of every gate: decided from one
+    # joint reduction (default) or from two passes; both follow the oracle
+    c = W.random_su4(9, 4, 0.02, 0.2, seed=33)
+    a = run_gpu(c, 12, 300, sv.SV_BRANCH, prec, want_amps=[0, 150])
+    b = run_gpu(c, 12, 300, sv.SV_BRANCH, prec, opts={sv.SV_OPT_JOINT_KRAUS: 0}, want_amps=[0, 150])
+    assert a["stats"]["passes"] < b["stats"]["passes"]
+    compare_shots(c, 12, a, range(300), prec)
+    compare_shots(c, 12, b, range(300), prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_batch_and_branch_logs_identical(prec):
     c = W.random_su4(6, 5, 0.08, 0.1, seed=31)
     a = run_gpu(c, 3, 400, sv.SV_BATCH, prec)
