@@ -165,6 +165,7 @@ def main():
     ap.add_argument("--ref-shots", type=int, default=32)
     ap.add_argument("--shots", type=int, default=0, help="override the workload's shot count (profiling)")
     ap.add_argument("--timed-only", action="store_true", help="skip the end-to-end and roofline phases")
+    ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -194,7 +195,7 @@ def main():
     cs = sv.circuit_struct(arrays)
     stream = torch.cuda.current_stream()
     b = sv.Batch(circ.n_qubits, n_shots, max(1, circ.n_clbits), prec, mode, seed, stream=stream.cuda_stream)
-    use_graph = mode != sv.SV_PLAIN
+    use_graph = mode != sv.SV_PLAIN and not args.no_graph
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):

@@ -49,6 +49,25 @@ template <class T> __device__ __forceinline__ void cfma(T& acc, T a, T b) {
     acc.y += a.x * b.y + a.y * b.x;
 }
 
+// Packed float32x2 arithmetic (Blackwell fma.rn.f32x2): a complex
+// multiply-accumulate acc += m v is two packed FMAs,
+// acc += (m.re, m.re) * (v.re, v.im) and acc += (-m.im, m.im) * (v.im, v.re).
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Accumulators.  complex128 states sum in float64.  complex64 states sum in
 // float-float (an unevaluated pair hi + lo updated with Knuth's TwoSum), which
 // carries about 48 bits of precision using only float32 arithmetic; the
@@ -661,27 +680,93 @@ __device__ __forceinline__ void reg_apply2(T* v, const T* M) {
     }
 }
 
-// diagonal (shape 1) or anti-diagonal (shape 2) one-qubit matrix
-template <class T, int G, int J>
-__device__ __forceinline__ void reg_apply1_sparse(T* v, const T* M, int shape) {
-    const T m0 = shape == 1 ? M[0] : M[1], m1 = shape == 1 ? M[3] : M[2];
+// structured one-qubit matrices: shape 1 diagonal, 2 anti-diagonal, +4 when
+// the two nonzero entries are real (amplitude damping terms scaled by
+// 1/sqrt(p)): a real diagonal costs two multiplies per amplitude
+template <class T, int G, int J, int SHAPE>
+__device__ __forceinline__ void reg_apply1_shape(T* v, const T* M) {
+    const T m0 = (SHAPE & 3) == 1 ? M[0] : M[1], m1 = (SHAPE & 3) == 1 ? M[3] : M[2];
 #pragma unroll
     for (int r = 0; r < G; ++r) {
         if (r & (1 << J)) continue;
         const int r1 = r | (1 << J);
-        const T a = shape == 1 ? v[r] : v[r1], b = shape == 1 ? v[r1] : v[r];
-        v[r] = cmul(m0, a);
-        v[r1] = cmul(m1, b);
+        const T a = (SHAPE & 3) == 1 ? v[r] : v[r1], b = (SHAPE & 3) == 1 ? v[r1] : v[r];
+        if (SHAPE & 4) {
+            v[r].x = m0.x * a.x;
+            v[r].y = m0.x * a.y;
+            v[r1].x = m1.x * b.x;
+            v[r1].y = m1.x * b.y;
+        } else {
+            v[r] = cmul(m0, a);
+            v[r1] = cmul(m1, b);
+        }
+    }
+}
+
+template <class T, int G, int J>
+__device__ __forceinline__ void reg_apply1_shaped(T* v, const T* M, int shape) {
+    switch (shape) {
+    case 1: reg_apply1_shape<T, G, J, 1>(v, M); break;
+    case 2: reg_apply1_shape<T, G, J, 2>(v, M); break;
+    case 5: reg_apply1_shape<T, G, J, 5>(v, M); break;
+    default: reg_apply1_shape<T, G, J, 6>(v, M); break;
     }
 }
 
 template <class T, int G>
 __device__ __forceinline__ void reg_apply1s_dyn(T* v, int j, const T* M, int shape) {
     switch (j) {
-    case 0: reg_apply1_sparse<T, G, 0>(v, M, shape); break;
-    case 1: if constexpr (G > 2) reg_apply1_sparse<T, G, 1>(v, M, shape); break;
-    case 2: if constexpr (G > 4) reg_apply1_sparse<T, G, 2>(v, M, shape); break;
-    default: if constexpr (G > 8) reg_apply1_sparse<T, G, 3>(v, M, shape); break;
+    case 0: reg_apply1_shaped<T, G, 0>(v, M, shape); break;
+    case 1: if constexpr (G > 2) reg_apply1_shaped<T, G, 1>(v, M, shape); break;
+    case 2: if constexpr (G > 4) reg_apply1_shaped<T, G, 2>(v, M, shape); break;
+    default: if constexpr (G > 8) reg_apply1_shaped<T, G, 3>(v, M, shape); break;
+    }
+}
+
+// complex64 2-qubit matrix with packed FMAs; MX holds every entry expanded as
+// ((re, re), (-im, im))
+template <int G, int J0, int J1>
+__device__ __forceinline__ void reg_apply2_f32x2(float2* v, const ulonglong2* MX) {
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+        if (r & ((1 << J0) | (1 << J1))) continue;
+        const int i[4] = {r, r | (1 << J0), r | (1 << J1), r | (1 << J0) | (1 << J1)};
+        unsigned long long ap[4], as[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            ap[c] = pk2(v[i[c]].x, v[i[c]].y);
+            as[c] = pk2(v[i[c]].y, v[i[c]].x);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            unsigned long long acc = 0ull;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const ulonglong2 m = MX[q * 4 + c];
+                acc = fma2(m.x, ap[c], acc);
+                acc = fma2(m.y, as[c], acc);
+            }
+            v[i[q]] = upk2(acc);
+        }
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void reg_apply2x_dyn(float2* v, int j0, int j1, const ulonglong2* MX) {
+    const int code = j0 * 4 + j1;
+    switch (code) {
+    case 1: if constexpr (G > 2) reg_apply2_f32x2<G, 0, 1>(v, MX); break;
+    case 4: if constexpr (G > 2) reg_apply2_f32x2<G, 1, 0>(v, MX); break;
+    case 2: if constexpr (G > 4) reg_apply2_f32x2<G, 0, 2>(v, MX); break;
+    case 8: if constexpr (G > 4) reg_apply2_f32x2<G, 2, 0>(v, MX); break;
+    case 6: if constexpr (G > 4) reg_apply2_f32x2<G, 1, 2>(v, MX); break;
+    case 9: if constexpr (G > 4) reg_apply2_f32x2<G, 2, 1>(v, MX); break;
+    case 3: if constexpr (G > 8) reg_apply2_f32x2<G, 0, 3>(v, MX); break;
+    case 12: if constexpr (G > 8) reg_apply2_f32x2<G, 3, 0>(v, MX); break;
+    case 7: if constexpr (G > 8) reg_apply2_f32x2<G, 1, 3>(v, MX); break;
+    case 13: if constexpr (G > 8) reg_apply2_f32x2<G, 3, 1>(v, MX); break;
+    case 11: if constexpr (G > 8) reg_apply2_f32x2<G, 2, 3>(v, MX); break;
+    default: if constexpr (G > 8) reg_apply2_f32x2<G, 3, 2>(v, MX); break;
     }
 }
 
@@ -834,6 +919,11 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
     int* w_sel = reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) + (size_t)nwarps * mat_stride) +
                  warp * 2 * MAX_STAGES;
     int* w_packed = w_sel + MAX_STAGES;
+    // complex64 only: expanded copies of the stages' matrices for packed FMAs
+    ulonglong2* matx = reinterpret_cast<ulonglong2*>(reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) +
+                                                                            (size_t)nwarps * mat_stride) +
+                                                     nwarps * 2 * MAX_STAGES) +
+                       (size_t)warp * mat_stride;
 
     const int n_br = d.ctl[CTL_NBR];
     if (blockIdx.x == 0 && threadIdx.x == 0 && d.pass_log) {
@@ -841,15 +931,10 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
         if (i < d.pass_log_cap) d.pass_log[i] = n_br;
     }
     // group offsets: element e of a group sits at base + off[e]
-    int off[G];
+    // element e of a group sits at base + sum of stride[j] over its set bits
+    int stride[WP];
 #pragma unroll
-    for (int e = 0; e < G; ++e) {
-        int o = 0;
-#pragma unroll
-        for (int j = 0; j < WP; ++j)
-            if ((e >> j) & 1) o |= 1 << p.tile_q[j];
-        off[e] = o;
-    }
+    for (int j = 0; j < WP; ++j) stride[j] = 1 << p.tile_q[j];
     const int64_t units = (int64_t)n_br * p.chunks;
     const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, tw = (int64_t)gridDim.x * nwarps;
     const int64_t u0 = units * gw / tw, u1 = units * (gw + 1) / tw;
@@ -899,12 +984,17 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
                         m.x = src[2 * e] * sc;
                         m.y = src[2 * e + 1] * sc;
                         mats[st.mat + e] = m;
+                        if constexpr (sizeof(T) == 8)
+                            matx[st.mat + e] = make_ulonglong2(pk2((float)m.x, (float)m.x), pk2(-(float)m.y, (float)m.y));
                     }
                     if (st.k == 1 && lane == 0) {
-                        // structure of a one-qubit matrix: 1 diagonal, 2 anti-diagonal
+                        // structure of a one-qubit matrix: 1 diagonal, 2 anti-diagonal, +4 real
                         const bool off0 = src[2] == 0 && src[3] == 0 && src[4] == 0 && src[5] == 0;
                         const bool diag0 = src[0] == 0 && src[1] == 0 && src[6] == 0 && src[7] == 0;
-                        w_packed[s] = off0 ? 1 : (diag0 ? 2 : 0);
+                        int shape = off0 ? 1 : (diag0 ? 2 : 0);
+                        if (shape == 1 && src[1] == 0 && src[7] == 0) shape |= 4;
+                        if (shape == 2 && src[3] == 0 && src[5] == 0) shape |= 4;
+                        w_packed[s] = shape;
                     }
                 } else if (!sk && st.kind == ST_PROJ_BR && lane == 0) {
                     T m;
@@ -932,18 +1022,27 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
         T* gstate = states + (int64_t)slot * d.dim;
         for (int64_t gi = lane; gi < gpu; gi += 32) {
             // base: the group index with zeros inserted at the group qubits
-            int64_t base = (int64_t)c * gpu + gi;
+            // base: the group index with zeros inserted at the group qubits
+            // (32-bit: a state has at most 2^30 amplitudes)
+            uint32_t base = (uint32_t)(c * gpu + gi);
 #pragma unroll
             for (int j = 0; j < WP; ++j) {
-                const int q = p.tile_q[j];
-                base = ((base >> q) << (q + 1)) | (base & ((1ll << q) - 1));
+                const uint32_t lowm = (uint32_t)stride[j] - 1u;
+                base = ((base & ~lowm) << 1) | (base & lowm);
             }
             T* g = gstate + base;
+            auto off = [&](int e) {
+                int o = 0;
+#pragma unroll
+                for (int j = 0; j < WP; ++j)
+                    if ((e >> j) & 1) o += stride[j];
+                return o;
+            };
             T v[G];
             if constexpr (sizeof(T) == 8 && PAIRED) {
 #pragma unroll
                 for (int e = 0; e < G; e += 2) {
-                    const float4 x = *reinterpret_cast<const float4*>(g + off[e]);
+                    const float4 x = *reinterpret_cast<const float4*>(g + off(e));
                     v[e].x = x.x;
                     v[e].y = x.y;
                     v[e + 1].x = x.z;
@@ -951,7 +1050,7 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < G; ++e) v[e] = g[off[e]];
+                for (int e = 0; e < G; ++e) v[e] = g[off(e)];
             }
             for (int s = 0; s < p.n_stages; ++s) {
                 if ((skipmask >> s) & 1) continue;
@@ -962,7 +1061,10 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
                         if (shape) reg_apply1s_dyn<T, G>(v, st.pos[0], mats + st.mat, shape);
                         else reg_apply1_dyn<T, G>(v, st.pos[0], mats + st.mat);
                     } else {
-                        reg_apply2_dyn<T, G>(v, st.pos[0], st.pos[1], mats + st.mat);
+                        if constexpr (sizeof(T) == 8)
+                            reg_apply2x_dyn<G>(reinterpret_cast<float2*>(v), st.pos[0], st.pos[1], matx + st.mat);
+                        else
+                            reg_apply2_dyn<T, G>(v, st.pos[0], st.pos[1], mats + st.mat);
                     }
                 } else if (st.kind == ST_PAULI_BR) {
                     const int packed = w_packed[s];
@@ -1016,10 +1118,10 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
                 if constexpr (sizeof(T) == 8 && PAIRED) {
 #pragma unroll
                     for (int e = 0; e < G; e += 2)
-                        *reinterpret_cast<float4*>(g + off[e]) = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
+                        *reinterpret_cast<float4*>(g + off(e)) = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
                 } else {
 #pragma unroll
-                    for (int e = 0; e < G; ++e) g[off[e]] = v[e];
+                    for (int e = 0; e < G; ++e) g[off(e)] = v[e];
                 }
             }
         }
@@ -1627,7 +1729,8 @@ int pass_reg_blocks_per_sm(int prec, int wp, int paired, size_t smem) {
 size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads) {
     const size_t c = prec ? 16 : 8;
     const size_t nw = threads / 32;
-    return nw * ((size_t)((p.mat_elems + 1) & ~1) * c + 2 * MAX_STAGES * 4);
+    const size_t m = (size_t)((p.mat_elems + 1) & ~1);
+    return nw * (m * c + 2 * MAX_STAGES * 4) + (prec ? 0 : nw * m * 16);
 }
 
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s) {
