@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsv.so")
 SOURCES = ["sv_kernels.cu", "sv_runtime.cu", "sv_noalloc.cu"]
-HEADERS = ["sv_internal.h", os.path.join("..", "..", "include", "sv.h")]
+HEADERS = ["sv_internal.h", "sv_sample.cuh", os.path.join("..", "..", "include", "sv.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

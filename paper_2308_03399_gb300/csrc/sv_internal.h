@@ -75,6 +75,7 @@ struct DecideDesc {
     int32_t m;                 // measured qubits
     int32_t clbit[MAX_STAGE_Q];
     int32_t r2;                // joint Kraus: terms of the second op (partials stride)
+    int32_t npend;             // pending-choice columns in use (copied to forks)
     int32_t pend_prev;         // DEC_KRAUS_J2: pending column of the first op's choice
     int32_t* log_sel;          // per shot id, nullable
     double* log_thr;           // 2 per shot id, nullable
@@ -114,13 +115,13 @@ struct DevBatch {
     double* grp_scale;
     uint64_t* grp_clbits;
     int32_t* free_slots;
-    int32_t* fork_list;        // branches that fork at the current random op
     uint32_t* wait_shots;
     double* partials;          // [n_slots][max_chunks][MAX_RED]
     int32_t max_chunks;
     const void* pool;          // real-typed constants (matrices, forms)
     const int32_t* ipool;      // integer constants (Pauli parameters)
     uint64_t* keys;            // per shot id
+    int32_t* pos_branch;       // branch owning each perm position (final sampling)
     int64_t* fork_log;         // 5 per event, nullable
     int32_t fork_log_cap;
     int32_t* pass_log;         // live branches seen by each pass (profiling), nullable
@@ -139,7 +140,8 @@ enum : int32_t {
     CTL_NFORK = 7,      // fork events logged
     CTL_NPASS = 8,      // passes logged
     CTL_NCOPIED = 9,    // branches created by forks (each one state copy)
-    CTL_NFL = 10,       // forking branches listed by the last decide
+    CTL_NALLOC = 10,    // new-branch ids handed out by the current decide
+    CTL_DONE = 11,      // finished CTAs of k_copy (last one folds the counts)
     CTL_WORDS = 16
 };
 
@@ -149,7 +151,6 @@ cudaError_t launch_reset(const DevBatch& d, int mode_branch, int n_shots_run, in
                          cudaStream_t s);
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s);
 cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int grid, cudaStream_t s);
-cudaError_t launch_alloc(const DevBatch& d, uint32_t op, int pend, cudaStream_t s);
 cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s);
 cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s);
 size_t pass_smem_bytes(int prec, const PassDesc& p, int threads);

@@ -12,12 +12,11 @@
 //                   Pauli string, Kraus matrix or measurement projection) in
 //                   shared memory, then reducing the probabilities the next
 //                   random op needs.  Persistent over (branch, chunk) items.
-//   k_decide        per branch: sum the reduced probabilities in a fixed
+//   k_decide_*      per branch: sum the reduced probabilities in a fixed
 //                   order (float64), draw every shot's Philox number, choose
-//                   its outcome, and partition the branch's shots by outcome.
-//   k_alloc         one CTA: give every new outcome group a branch id and a
-//                   free slot, in branch order, or park its shots on the
-//                   waiting list when no slot is left.
+//                   its outcome, partition the branch's shots by outcome, and
+//                   give every new outcome group a branch id and a free slot
+//                   (or park its shots on the waiting list when none is left).
 //   k_copy          copy parent states into the new branches' slots.
 //   k_final_*       sampling of all qubits from each branch (sampling measure).
 //
@@ -29,6 +28,7 @@
 #include <cstdint>
 
 #include "sv_internal.h"
+#include "sv_sample.cuh"
 
 namespace sv {
 
@@ -1142,45 +1142,56 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
 // partials), one Philox draw per shot, the shot's choice, and a stable
 // partition of the branch's shots by choice.  Branches with more than
 // DEC_SMALL shots take a whole CTA (k_decide_big); the others one warp
-// (k_decide_small).  Forking branches are appended to a list for k_alloc.
+// (k_decide_small).
 // ---------------------------------------------------------------------------
 constexpr int DEC_THREADS = 512;
 constexpr int DEC_SMALL = 64;
 
-// probabilities and cumulative table of branch b into p_out / cum_out
-// (cum_out only for Pauli; the caller forms the running sum otherwise)
-__device__ __forceinline__ void decide_probs(const DevBatch& d, const DecideDesc& dd, int b, int slot, int r,
-                                             double* p_out, double* cum_out) {
+// probabilities of branch b into p_out (and, for Pauli, the table into
+// cum_out); one whole warp: lanes read chunks lane, lane+32, ... and the
+// per-lane sums are combined by a fixed shuffle tree (deterministic)
+__device__ __forceinline__ double warp_sum(double x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ void warp_probs(const DevBatch& d, const DecideDesc& dd, int b, int slot, double* p_out, double* cum_out) {
+    const int lane = threadIdx.x & 31;
+    const int R = dd.R;
     if (dd.kind == DEC_PAULI) {
-        p_out[r] = dd.cum[r] - (r ? dd.cum[r - 1] : 0.0);
-        cum_out[r] = dd.cum[r];
-    } else if (dd.kind == DEC_KRAUS_J1) {
-        const double* pp = d.partials + (int64_t)slot * d.max_chunks * MAX_RED + r * dd.r2;
-        double s = 0.0;
-        for (int c = 0; c < dd.chunks; ++c)
-            for (int j = 0; j < dd.r2; ++j) s += pp[(int64_t)c * MAX_RED + j];
-        p_out[r] = s;
+        for (int r = lane; r < R; r += 32) {
+            p_out[r] = dd.cum[r] - (r ? dd.cum[r - 1] : 0.0);
+            cum_out[r] = dd.cum[r];
+        }
+        __syncwarp();
+        return;
+    }
+    int src = slot, base_r = 0, stride_r = 1, inner = 1;
+    if (dd.kind == DEC_KRAUS_J1) {
+        stride_r = dd.r2;  // p_i = sum over chunks and j of partial[i * r2 + j]
+        inner = dd.r2;
     } else if (dd.kind == DEC_KRAUS_J2) {
         // branches forked by the first op still find the joint partials in
         // their parent's slot
         const int cf = d.ctl[CTL_COPY_FIRST], ce = d.ctl[CTL_COPY_END];
-        const int src = (b >= cf && b < ce) ? d.br_slot[d.br_parent[b]] : slot;
-        const int i = d.br_sel[(int64_t)dd.pend_prev * d.cap_br + b];
-        const double* pp = d.partials + (int64_t)src * d.max_chunks * MAX_RED + i * dd.R;
-        double pi = 0.0, pr = 0.0;
-        for (int j = 0; j < dd.R; ++j) {
-            double s = 0.0;
-            for (int c = 0; c < dd.chunks; ++c) s += pp[(int64_t)c * MAX_RED + j];
-            pi += s;
-            if (j == r) pr = s;
-        }
-        p_out[r] = pr / pi;
-    } else {
-        const double* pp = d.partials + (int64_t)slot * d.max_chunks * MAX_RED + r;
-        double s = 0.0;
-        for (int c = 0; c < dd.chunks; ++c) s += pp[(int64_t)c * MAX_RED];
-        p_out[r] = s;
+        if (b >= cf && b < ce) src = d.br_slot[d.br_parent[b]];
+        base_r = d.br_sel[(int64_t)dd.pend_prev * d.cap_br + b] * R;  // p_ij = partial[i * R + j]
     }
+    const double* pp = d.partials + (int64_t)src * d.max_chunks * MAX_RED;
+    for (int r = 0; r < R; ++r) {
+        double t = 0.0;
+        for (int c = lane; c < dd.chunks; c += 32)
+            for (int j = 0; j < inner; ++j) t += pp[(int64_t)c * MAX_RED + base_r + r * stride_r + j];
+        t = warp_sum(t);
+        if (lane == 0) p_out[r] = t;
+    }
+    __syncwarp();
+    if (dd.kind == DEC_KRAUS_J2 && lane == 0) {
+        double pi = 0.0;
+        for (int r = 0; r < R; ++r) pi += p_out[r];
+        for (int r = 0; r < R; ++r) p_out[r] = p_out[r] / pi;
+    }
+    __syncwarp();
 }
 
 // group records of branch b (one thread): outcome, 1/sqrt(p) in float64,
@@ -1210,9 +1221,53 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
     d.br_sel[(int64_t)dd.pend * d.cap_br + b] = d.grp_sel[g0];
     d.br_scale[(int64_t)dd.pend * d.cap_br + b] = d.grp_scale[g0];
     d.br_clbits[b] = d.grp_clbits[g0];
-    if (g > 1) {
-        if (!dd.fork) set_err(d, ERR_GROUPS, b);
-        else d.fork_list[atomicAdd(&d.ctl[CTL_NFL], 1)] = b;
+    if (g > 1 && !dd.fork) set_err(d, ERR_GROUPS, b);
+    if (g <= 1 || !dd.fork) return;
+    // Fork (Section IV-B-2): the smallest outcome keeps this branch; every
+    // other group takes the next branch id and the next free slot, or parks
+    // its shots on the waiting list when no slot is left.  Ids and slots come
+    // from atomic counters, so which branch gets which id depends on timing,
+    // but no result does: a branch's arithmetic never depends on its id or
+    // slot.  k_copy folds the counters into the branch count.
+    const int n_br0 = d.ctl[CTL_NBR], n_free = d.ctl[CTL_NFREE];
+    if (d.fork_log) {
+        const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
+        if (e < d.fork_log_cap) {
+            int64_t* ev = d.fork_log + 5 * (int64_t)e;
+            ev[0] = dd.op; ev[1] = b; ev[2] = b; ev[3] = d.grp_sel[g0]; ev[4] = d.grp_cnt[g0];
+        }
+    }
+    d.br_count[b] = d.grp_cnt[g0];
+    for (int gi = 1; gi < g; ++gi) {
+        const int64_t gx = g0 + gi;
+        const int j = atomicAdd(&d.ctl[CTL_NALLOC], 1);
+        int child = -1;
+        if (j < n_free) {
+            child = n_br0 + j;
+            d.br_slot[child] = d.free_slots[n_free - 1 - j];
+            d.br_start[child] = d.grp_start[gx];
+            d.br_count[child] = d.grp_cnt[gx];
+            d.br_clbits[child] = d.grp_clbits[gx];
+            d.br_parent[child] = b;
+            d.grp_n[child] = 1;
+            for (int q = 0; q < dd.npend; ++q) {
+                d.br_sel[(int64_t)q * d.cap_br + child] = d.br_sel[(int64_t)q * d.cap_br + b];
+                d.br_scale[(int64_t)q * d.cap_br + child] = d.br_scale[(int64_t)q * d.cap_br + b];
+            }
+            d.br_sel[(int64_t)dd.pend * d.cap_br + child] = d.grp_sel[gx];
+            d.br_scale[(int64_t)dd.pend * d.cap_br + child] = d.grp_scale[gx];
+        } else {
+            const int cnt = d.grp_cnt[gx], st = d.grp_start[gx];
+            const int w = atomicAdd(&d.ctl[CTL_NWAIT], cnt);
+            for (int i = 0; i < cnt; ++i) d.wait_shots[w + i] = d.perm[st + i];
+        }
+        if (d.fork_log) {
+            const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
+            if (e < d.fork_log_cap) {
+                int64_t* ev = d.fork_log + 5 * (int64_t)e;
+                ev[0] = dd.op; ev[1] = b; ev[2] = child; ev[3] = d.grp_sel[gx]; ev[4] = d.grp_cnt[gx];
+            }
+        }
     }
 }
 
@@ -1241,8 +1296,8 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
         if (cnt <= DEC_SMALL) continue;
         const int slot = d.br_slot[b], start = d.br_start[b];
         __syncthreads();
+        if (warp == 0) warp_probs(d, dd, b, slot, p_sh, cum_sh);
         if (tid < R) {
-            decide_probs(d, dd, b, slot, tid, p_sh, cum_sh);
             bincnt[tid] = 0;
             binrun[tid] = 0;
         }
@@ -1252,10 +1307,15 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
             for (int r = 0; r < R; ++r) cum_sh[r] = (acc += p_sh[r]);
         }
         __syncthreads();
-        for (int i = tid; i < cnt; i += nth) {
-            const int sel = draw_choice(d, dd, d.perm[start + i], cum_sh);
-            d.shot_sel[start + i] = sel;
-            atomicAdd(&bincnt[sel], 1);
+        for (int base = 0; base < cnt; base += nth) {  // warp-aggregated bin counts
+            const int i = base + tid;
+            int sel = -1;
+            if (i < cnt) {
+                sel = draw_choice(d, dd, d.perm[start + i], cum_sh);
+                d.shot_sel[start + i] = sel;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, sel);
+            if (sel >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&bincnt[sel], __popc(peers));
         }
         __syncthreads();
         if (tid == 0) {
@@ -1267,34 +1327,35 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
                     ++ng;
                 }
             ng_sh = ng;
-            decide_groups(d, dd, b, start, bincnt, binbase, p_sh);
         }
         __syncthreads();
-        if (ng_sh <= 1 || !dd.fork) continue;
-        for (int base = 0; base < cnt; base += nth) {
-            const int i = base + tid;
-            const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
-            for (int e = tid; e < (nth >> 5) * MAX_TERMS; e += nth) (&wcnt[0][0])[e] = 0;
-            __syncthreads();
-            const unsigned peers = __match_any_sync(0xffffffffu, sel);
-            const int rank = __popc(peers & ((1u << lane) - 1u));
-            if (sel >= 0 && rank == 0) wcnt[warp][sel] = __popc(peers);
-            __syncthreads();
-            if (sel >= 0) {
-                int before = 0;
-                for (int w = 0; w < warp; ++w) before += wcnt[w][sel];
-                d.perm_tmp[start + binbase[sel] + binrun[sel] + before + rank] = d.perm[start + i];
+        if (ng_sh > 1 && dd.fork) {
+            for (int base = 0; base < cnt; base += nth) {
+                const int i = base + tid;
+                const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
+                for (int e = tid; e < (nth >> 5) * MAX_TERMS; e += nth) (&wcnt[0][0])[e] = 0;
+                __syncthreads();
+                const unsigned peers = __match_any_sync(0xffffffffu, sel);
+                const int rank = __popc(peers & ((1u << lane) - 1u));
+                if (sel >= 0 && rank == 0) wcnt[warp][sel] = __popc(peers);
+                __syncthreads();
+                if (sel >= 0) {
+                    int before = 0;
+                    for (int w = 0; w < warp; ++w) before += wcnt[w][sel];
+                    d.perm_tmp[start + binbase[sel] + binrun[sel] + before + rank] = d.perm[start + i];
+                }
+                __syncthreads();
+                if (tid < R) {
+                    int tot = 0;
+                    for (int w = 0; w < (nth >> 5); ++w) tot += wcnt[w][tid];
+                    binrun[tid] += tot;
+                }
+                __syncthreads();
             }
-            __syncthreads();
-            if (tid < R) {
-                int tot = 0;
-                for (int w = 0; w < (nth >> 5); ++w) tot += wcnt[w][tid];
-                binrun[tid] += tot;
-            }
+            for (int i = tid; i < cnt; i += nth) d.perm[start + i] = d.perm_tmp[start + i];
             __syncthreads();
         }
-        for (int i = tid; i < cnt; i += nth) d.perm[start + i] = d.perm_tmp[start + i];
-        if (tid == 0) d.br_count[b] = d.grp_cnt[(int64_t)b * MAX_TERMS];
+        if (tid == 0) decide_groups(d, dd, b, start, bincnt, binbase, p_sh);
     }
 }
 
@@ -1316,8 +1377,8 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
         const int cnt = d.br_count[b];
         if (cnt > DEC_SMALL) continue;
         const int slot = d.br_slot[b], start = d.br_start[b];
+        warp_probs(d, dd, b, slot, p, cum);
         for (int r = lane; r < R; r += 32) {
-            decide_probs(d, dd, b, slot, r, p, cum);
             bc[r] = 0;
             br[r] = 0;
         }
@@ -1342,169 +1403,39 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
                     acc += bc[r];
                     ++ng;
                 }
-            decide_groups(d, dd, b, start, bc, bb, p);
         }
         ng = __shfl_sync(0xffffffffu, ng, 0);
         __syncwarp();
-        if (ng <= 1 || !dd.fork) continue;
-        for (int base = 0; base < cnt; base += 32) {
-            const int i = base + lane;
-            const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
-            const unsigned peers = __match_any_sync(0xffffffffu, sel);
-            const int rank = __popc(peers & ((1u << lane) - 1u));
-            if (sel >= 0) d.perm_tmp[start + bb[sel] + br[sel] + rank] = d.perm[start + i];
-            __syncwarp();
-            if (sel >= 0 && rank == 0) br[sel] += __popc(peers);
+        if (ng > 1 && dd.fork) {
+            for (int base = 0; base < cnt; base += 32) {
+                const int i = base + lane;
+                const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, sel);
+                const int rank = __popc(peers & ((1u << lane) - 1u));
+                if (sel >= 0) d.perm_tmp[start + bb[sel] + br[sel] + rank] = d.perm[start + i];
+                __syncwarp();
+                if (sel >= 0 && rank == 0) br[sel] += __popc(peers);
+                __syncwarp();
+            }
+            for (int i = lane; i < cnt; i += 32) d.perm[start + i] = d.perm_tmp[start + i];
             __syncwarp();
         }
-        for (int i = lane; i < cnt; i += 32) d.perm[start + i] = d.perm_tmp[start + i];
-        if (lane == 0) d.br_count[b] = d.grp_cnt[(int64_t)b * MAX_TERMS];
+        if (lane == 0) decide_groups(d, dd, b, start, bc, bb, p);
         __syncwarp();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_alloc: one CTA of 1024 threads.  The forking branches (listed by the
-// decide kernels) are sorted by id, so new branch ids and slots are handed
-// out in branch order whatever order the list was written in.
-// ---------------------------------------------------------------------------
-constexpr int ALLOC_SORT_MAX = 8192;
-
-__device__ int block_excl_scan(int v, int* sh, int* total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    __syncthreads();
-    if (lane == 31) sh[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        int w = lane < nw ? sh[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < nw) sh[lane] = w;
-    }
-    __syncthreads();
-    const int excl = x - v + (warp ? sh[warp - 1] : 0);
-    *total = sh[(blockDim.x >> 5) - 1];
-    __syncthreads();
-    return excl;
-}
-
-__global__ void __launch_bounds__(1024) k_alloc(DevBatch d, uint32_t op, int pend) {
-    __shared__ int sh[32];
-    __shared__ int list[ALLOC_SORT_MAX];
-    const int n_br0 = d.ctl[CTL_NBR];
-    const int n_free = d.ctl[CTL_NFREE];
-    const int n_wait0 = d.ctl[CTL_NWAIT];
-    const int n_list = d.ctl[CTL_NFL];
-    const bool use_list = n_list <= ALLOC_SORT_MAX;
-    int n_items = n_br0;
-    if (use_list) {
-        int np2 = 1;
-        while (np2 < n_list) np2 <<= 1;
-        for (int i = threadIdx.x; i < np2; i += blockDim.x) list[i] = i < n_list ? d.fork_list[i] : 0x7fffffff;
-        __syncthreads();
-        for (int k = 2; k <= np2; k <<= 1)  // bitonic sort, ascending
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-                    const int l = i ^ j;
-                    if (l > i) {
-                        const int a = list[i], c = list[l];
-                        const bool up = (i & k) == 0;
-                        if ((a > c) == up) {
-                            list[i] = c;
-                            list[l] = a;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        n_items = n_list;
-    }
-    int carry = 0, wcarry = 0;
-    for (int base = 0; base < n_items; base += blockDim.x) {
-        const int idx = base + threadIdx.x;
-        const int b = idx < n_items ? (use_list ? list[idx] : idx) : -1;
-        const int gn = b >= 0 ? d.grp_n[b] : 1;
-        const int ng = gn > 1 ? gn - 1 : 0;
-        int tot;
-        const int excl = carry + block_excl_scan(ng, sh, &tot);
-        int wshots = 0;
-        for (int g = 1; g < gn; ++g)
-            if (excl + g - 1 >= n_free) wshots += d.grp_cnt[(int64_t)b * MAX_TERMS + g];
-        int wtot;
-        const int wexcl = wcarry + block_excl_scan(wshots, sh, &wtot);
-        if (b >= 0 && gn > 1) {
-            const int64_t g0 = (int64_t)b * MAX_TERMS;
-            if (d.fork_log) {
-                const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
-                if (e < d.fork_log_cap) {
-                    int64_t* ev = d.fork_log + 5 * (int64_t)e;
-                    ev[0] = op; ev[1] = b; ev[2] = b; ev[3] = d.grp_sel[g0]; ev[4] = d.grp_cnt[g0];
-                }
-            }
-            int woff = wexcl;
-            for (int g = 1; g < gn; ++g) {
-                const int j = excl + g - 1;
-                const int64_t gi = g0 + g;
-                int child = -1;
-                if (j < n_free) {
-                    child = n_br0 + j;
-                    d.br_slot[child] = d.free_slots[n_free - 1 - j];
-                    d.br_start[child] = d.grp_start[gi];
-                    d.br_count[child] = d.grp_cnt[gi];
-                    d.br_clbits[child] = d.grp_clbits[gi];
-                    d.br_parent[child] = b;
-                    d.grp_n[child] = 1;
-                    for (int q = 0; q < MAX_PEND; ++q) {
-                        d.br_sel[(int64_t)q * d.cap_br + child] = d.br_sel[(int64_t)q * d.cap_br + b];
-                        d.br_scale[(int64_t)q * d.cap_br + child] = d.br_scale[(int64_t)q * d.cap_br + b];
-                    }
-                    d.br_sel[(int64_t)pend * d.cap_br + child] = d.grp_sel[gi];
-                    d.br_scale[(int64_t)pend * d.cap_br + child] = d.grp_scale[gi];
-                } else {
-                    const int cnt = d.grp_cnt[gi], st = d.grp_start[gi];
-                    for (int i = 0; i < cnt; ++i) d.wait_shots[n_wait0 + woff + i] = d.perm[st + i];
-                    woff += cnt;
-                }
-                if (d.fork_log) {
-                    const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
-                    if (e < d.fork_log_cap) {
-                        int64_t* ev = d.fork_log + 5 * (int64_t)e;
-                        ev[0] = op; ev[1] = b; ev[2] = child; ev[3] = d.grp_sel[gi]; ev[4] = d.grp_cnt[gi];
-                    }
-                }
-            }
-        }
-        carry += tot;
-        wcarry += wtot;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int admitted = carry < n_free ? carry : n_free;
-        d.ctl[CTL_NBR] = n_br0 + admitted;
-        d.ctl[CTL_NFREE] = n_free - admitted;
-        d.ctl[CTL_NWAIT] = n_wait0 + wcarry;
-        d.ctl[CTL_COPY_FIRST] = n_br0;
-        d.ctl[CTL_COPY_END] = n_br0 + admitted;
-        d.ctl[CTL_NCOPIED] += admitted;
-        d.ctl[CTL_NFL] = 0;
     }
 }
 
 // ---------------------------------------------------------------------------
 // k_copy: parent state -> new branch slot (128-bit accesses)
 // ---------------------------------------------------------------------------
+// The forks of the last decide took ids [n_br, n_br + admitted) and their
+// slots; copy each parent state into its children's slots, then (last CTA
+// to finish) fold the new branches into the counts.
 __global__ void __launch_bounds__(256) k_copy(DevBatch d, int64_t state_vec16) {
-    const int first = d.ctl[CTL_COPY_FIRST], end = d.ctl[CTL_COPY_END];
-    const int nb = end - first;
-    if (nb <= 0) return;
+    __shared__ int last;
+    const int first = d.ctl[CTL_NBR];
+    const int nalloc = d.ctl[CTL_NALLOC], n_free = d.ctl[CTL_NFREE];
+    const int nb = nalloc < n_free ? nalloc : n_free;
     const int64_t per_item = 4096;  // 16-byte words per work item (64 KB)
     const int64_t items_per_state = (state_vec16 + per_item - 1) / per_item;
     const int64_t items = (int64_t)nb * items_per_state;
@@ -1519,6 +1450,22 @@ __global__ void __launch_bounds__(256) k_copy(DevBatch d, int64_t state_vec16) {
         const int64_t lo = c * per_item;
         const int64_t hi = (lo + per_item < state_vec16) ? lo + per_item : state_vec16;
         for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&d.ctl[CTL_DONE], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        d.ctl[CTL_COPY_FIRST] = first;
+        d.ctl[CTL_COPY_END] = first + nb;
+        d.ctl[CTL_NBR] = first + nb;
+        d.ctl[CTL_NFREE] = n_free - nb;
+        d.ctl[CTL_NCOPIED] += nb;
+        d.ctl[CTL_NALLOC] = 0;
+        d.ctl[CTL_DONE] = 0;
+        __threadfence();
     }
 }
 
@@ -1537,95 +1484,51 @@ __global__ void __launch_bounds__(256) k_final_partials(DevBatch d, FinalDesc f)
         const int b = (int)(it / f.chunks), c = (int)(it % f.chunks);
         const int slot = d.br_slot[b];
         const T* g = reinterpret_cast<const T*>(d.states) + (int64_t)slot * d.dim + c * L;
-        Acc<R> a;
-        a.zero();
-        for (int64_t j = threadIdx.x; j < L; j += blockDim.x) {
-            const T v = g[j];
-            a.add(v.x * v.x + v.y * v.y);
-        }
-        const double s = block_sum(a.get(), red_sh);
+        const double s = svs::chunk_sum<R>(g, L, red_sh);
         if (threadIdx.x == 0) d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED] = s;
     }
 }
 
+// per branch (one warp): running sum of the chunk sums (into partials[..][1])
+// and the branch of every perm position it owns
+__global__ void __launch_bounds__(256) k_final_cum(DevBatch d, FinalDesc f) {
+    const int n_br = d.ctl[CTL_NBR];
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int b = gw; b < n_br; b += nw) {
+        const int slot = d.br_slot[b], start = d.br_start[b], cnt = d.br_count[b];
+        double* base = d.partials + (int64_t)slot * d.max_chunks * MAX_RED;
+        svs::chunk_cum(base, base + 1, f.chunks, MAX_RED);
+        for (int i = lane; i < cnt; i += 32) d.pos_branch[start + i] = b;
+    }
+}
+
+// one warp per shot, over all live shots whatever their branch
 template <class R>
 __global__ void __launch_bounds__(256) k_final_sample(DevBatch d, FinalDesc f) {
     using T = typename Cplx<R>::T;
-    __shared__ double cum[MAX_CHUNKS];
     const int n_br = d.ctl[CTL_NBR];
-    const int64_t L = d.dim / f.chunks;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    for (int b = blockIdx.x; b < n_br; b += gridDim.x) {
-        const int slot = d.br_slot[b], start = d.br_start[b], cnt = d.br_count[b];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            const double* pp = d.partials + (int64_t)slot * d.max_chunks * MAX_RED;
-            for (int c = 0; c < f.chunks; ++c) {
-                s += pp[(int64_t)c * MAX_RED];
-                cum[c] = s;
-            }
-        }
-        __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int pos = gw; pos < d.cap_br; pos += nw) {
+        const int b = d.pos_branch[pos];
+        if (b < 0 || b >= n_br) continue;
+        const int start = d.br_start[b], cnt = d.br_count[b];
+        if (pos < start || pos >= start + cnt) continue;  // stale entry (waiting shot)
+        const int slot = d.br_slot[b];
+        const uint32_t s = d.perm[pos];
+        const double u = philox_uniform(d.seed, s, f.op);
         const T* g = reinterpret_cast<const T*>(d.states) + (int64_t)slot * d.dim;
-        // one warp per shot: the chunk by binary search over chunk totals, then
-        // 32 amplitudes at a time with a warp prefix sum (float64)
-        for (int i = warp; i < cnt; i += nwarps) {
-            const uint32_t s = d.perm[start + i];
-            const double u = philox_uniform(d.seed, s, f.op);
-            int clo = 0, chi = f.chunks;
-            while (clo < chi) {
-                const int mid = (clo + chi) >> 1;
-                if (u < cum[mid]) chi = mid;
-                else clo = mid + 1;
-            }
-            int64_t key = -1;
-            double lo = 0.0, hi = 0.0;
-            if (clo < f.chunks) {
-                double acc = clo ? cum[clo - 1] : 0.0;
-                const int64_t j0 = (int64_t)clo * L;
-                for (int64_t blk = 0; blk < L && key < 0; blk += 32) {
-                    double pj = 0.0;
-                    if (blk + lane < L) {
-                        const T v = g[j0 + blk + lane];
-                        pj = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-                    }
-                    double incl = pj;
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const double y = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    const double val = acc + incl;
-                    const unsigned hit = __ballot_sync(0xffffffffu, (blk + lane < L) && u < val);
-                    if (hit) {
-                        const int first = __ffs(hit) - 1;
-                        key = j0 + blk + first;
-                        hi = __shfl_sync(0xffffffffu, val, first);
-                        lo = hi - __shfl_sync(0xffffffffu, pj, first);
-                    }
-                    acc += __shfl_sync(0xffffffffu, incl, 31);
-                }
-            }
-            if (key < 0 && lane == 0) {  // u at or past the rounded total: last nonzero entry
-                for (int64_t j = d.dim - 1; j >= 0; --j) {
-                    const T v = g[j];
-                    const double pj = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-                    if (pj > 0) {
-                        key = j;
-                        hi = cum[f.chunks - 1];
-                        lo = hi - pj;
-                        break;
-                    }
-                }
-                if (key < 0) key = d.dim - 1;
-            }
-            if (lane == 0) {
-                d.keys[s] = (uint64_t)key;
-                if (f.log_sel) f.log_sel[s] = (int32_t)key;
-                if (f.log_thr) {
-                    f.log_thr[2 * (int64_t)s] = lo;
-                    f.log_thr[2 * (int64_t)s + 1] = hi;
-                }
+        double lo, hi;
+        const int64_t key = svs::sample_warp<R>(g, d.dim, f.chunks,
+                                                d.partials + (int64_t)slot * d.max_chunks * MAX_RED + 1, MAX_RED, u,
+                                                &lo, &hi);
+        if (lane == 0) {
+            d.keys[s] = (uint64_t)key;
+            if (f.log_sel) f.log_sel[s] = (int32_t)key;
+            if (f.log_thr) {
+                f.log_thr[2 * (int64_t)s] = lo;
+                f.log_thr[2 * (int64_t)s + 1] = hi;
             }
         }
     }
@@ -1667,12 +1570,13 @@ __global__ void __launch_bounds__(256) k_reset(DevBatch d, int branch_mode, int 
     const int n_free = d.n_slots - nb;
     for (int64_t j = t0; j < n_free; j += stride) d.free_slots[j] = d.n_slots - 1 - (int)j;
     if (t0 == 0) {
-        d.ctl[CTL_NFL] = 0;
         d.ctl[CTL_NBR] = nb;
         d.ctl[CTL_NFREE] = n_free;
         d.ctl[CTL_NWAIT] = 0;
         d.ctl[CTL_COPY_FIRST] = 0;
         d.ctl[CTL_COPY_END] = 0;
+        d.ctl[CTL_NALLOC] = 0;
+        d.ctl[CTL_DONE] = 0;
     }
 }
 
@@ -1754,10 +1658,7 @@ cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int grid, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_alloc(const DevBatch& d, uint32_t op, int pend, cudaStream_t s) {
-    k_alloc<<<1, 1024, 0, s>>>(d, op, pend);
-    return cudaGetLastError();
-}
+
 
 cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s) {
     const int64_t vec16 = d.dim * (prec ? 16 : 8) / 16;
@@ -1768,9 +1669,11 @@ cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s) {
 cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s) {
     if (prec) {
         k_final_partials<double><<<grid, 256, 0, s>>>(d, f);
+        k_final_cum<<<grid, 256, 0, s>>>(d, f);
         k_final_sample<double><<<grid, 256, 0, s>>>(d, f);
     } else {
         k_final_partials<float><<<grid, 256, 0, s>>>(d, f);
+        k_final_cum<<<grid, 256, 0, s>>>(d, f);
         k_final_sample<float><<<grid, 256, 0, s>>>(d, f);
     }
     return cudaGetLastError();

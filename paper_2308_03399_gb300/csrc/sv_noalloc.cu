@@ -8,9 +8,10 @@
 // process exits.  Nothing here calls cudaMalloc, cudaFree or an allocating
 // library routine.
 //
-// The kernels repeat the arithmetic of k_final_partials / k_final_sample in
-// sv_kernels.cu (same chunking, same per-thread order, same fixed-order
-// combination), so a state gives the same key through either entry point.
+// The kernels use the same building blocks as the batch path's final
+// sampling (sv_sample.cuh: same chunking, same per-thread order, same
+// fixed-order combination), so a state gives the same key through either
+// entry point.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -18,6 +19,7 @@
 #include <string>
 
 #include "../../include/sv.h"
+#include "sv_sample.cuh"
 
 namespace sv {
 void set_last_error(const std::string& msg);  // sv_runtime.cu
@@ -27,36 +29,12 @@ namespace {
 
 constexpr int NA_MAX_DEVICES = 64;
 constexpr size_t NA_SCRATCH_DOUBLES = 131072;  // 1 MiB
-constexpr int NA_MAX_CHUNKS = 1024;
+constexpr int NA_MAX_CHUNKS = 1024;  // chunk count limit (as in the batch path)
 
 static __device__ __align__(256) double na_scratch[NA_SCRATCH_DOUBLES];
 
 double* na_scratch_ptr[NA_MAX_DEVICES] = {};
 std::mutex na_mutex;
-
-template <class R> struct NaCplx;
-template <> struct NaCplx<float> { using T = float2; };
-template <> struct NaCplx<double> { using T = double2; };
-
-template <class R> struct NaAcc;
-template <> struct NaAcc<double> {
-    double s;
-    __device__ __forceinline__ void zero() { s = 0.0; }
-    __device__ __forceinline__ void add(double x) { s += x; }
-    __device__ __forceinline__ double get() const { return s; }
-};
-template <> struct NaAcc<float> {  // float-float pair, Knuth TwoSum
-    float hi, lo;
-    __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
-    __device__ __forceinline__ void add(float x) {
-        float s = __fadd_rn(hi, x);
-        float bp = __fsub_rn(s, hi);
-        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
-        hi = s;
-        lo = __fadd_rn(lo, e);
-    }
-    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
-};
 
 // Philox4x32-10 (Salmon et al., SC'11), key = seed, counter = (shot, op, 0)
 __device__ __forceinline__ double na_uniform(uint64_t seed, uint64_t shot, uint32_t op) {
@@ -77,100 +55,39 @@ __device__ __forceinline__ double na_uniform(uint64_t seed, uint64_t shot, uint3
     return (double)(((((uint64_t)c0) << 32) | (uint64_t)c1) >> 11) * 0x1.0p-53;
 }
 
-__device__ __forceinline__ double na_block_sum(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    return s;
-}
-
 // per (state, chunk): sum of |psi_j|^2 over the chunk's contiguous range
 template <class R>
-__global__ void __launch_bounds__(256) na_partials(const typename NaCplx<R>::T* states, int64_t dim, int chunks,
+__global__ void __launch_bounds__(256) na_partials(const typename svs::Cx<R>::T* states, int64_t dim, int chunks,
                                                   int n_states, double* scratch) {
-    using T = typename NaCplx<R>::T;
     __shared__ double red_sh[32];
     const int64_t L = dim / chunks;
     const int64_t items = (int64_t)n_states * chunks;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int st = (int)(it / chunks), c = (int)(it % chunks);
-        const T* g = states + (int64_t)st * dim + c * L;
-        NaAcc<R> a;
-        a.zero();
-        for (int64_t j = threadIdx.x; j < L; j += blockDim.x) {
-            const T v = g[j];
-            a.add(v.x * v.x + v.y * v.y);
-        }
-        const double s = na_block_sum(a.get(), red_sh);
+        const double s = svs::chunk_sum<R>(states + (int64_t)st * dim + c * L, L, red_sh);
         if (threadIdx.x == 0) scratch[(int64_t)st * chunks + c] = s;
     }
 }
 
-// per state: chunk by binary search over chunk totals, then a warp prefix
-// sum over 32 amplitudes at a time; the first j with u < C_j is the key
+// per state (one warp): running sum of its chunk sums, in place
+__global__ void __launch_bounds__(256) na_cum(int chunks, int n_states, double* scratch) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int st = gw; st < n_states; st += nw)
+        svs::chunk_cum(scratch + (int64_t)st * chunks, scratch + (int64_t)st * chunks, chunks, 1);
+}
+
+// per state (one warp): its key
 template <class R>
-__global__ void __launch_bounds__(256) na_sample(const typename NaCplx<R>::T* states, int64_t dim, int chunks,
+__global__ void __launch_bounds__(256) na_sample(const typename svs::Cx<R>::T* states, int64_t dim, int chunks,
                                                 int n_states, const uint32_t* shots, uint64_t seed, uint32_t op,
                                                 uint64_t* keys, const double* scratch) {
-    using T = typename NaCplx<R>::T;
-    __shared__ double cum[NA_MAX_CHUNKS];
-    const int64_t L = dim / chunks;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int st = blockIdx.x; st < n_states; st += gridDim.x) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int c = 0; c < chunks; ++c) {
-                s += scratch[(int64_t)st * chunks + c];
-                cum[c] = s;
-            }
-        }
-        __syncthreads();
-        if (warp != 0) continue;
-        const T* g = states + (int64_t)st * dim;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int st = gw; st < n_states; st += nw) {
         const double u = na_uniform(seed, shots[st], op);
-        int clo = 0, chi = chunks;
-        while (clo < chi) {
-            const int mid = (clo + chi) >> 1;
-            if (u < cum[mid]) chi = mid;
-            else clo = mid + 1;
-        }
-        int64_t key = -1;
-        if (clo < chunks) {
-            double acc = clo ? cum[clo - 1] : 0.0;
-            const int64_t j0 = (int64_t)clo * L;
-            for (int64_t blk = 0; blk < L && key < 0; blk += 32) {
-                double pj = 0.0;
-                if (blk + lane < L) {
-                    const T v = g[j0 + blk + lane];
-                    pj = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-                }
-                double incl = pj;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const double y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const unsigned hit = __ballot_sync(0xffffffffu, (blk + lane < L) && u < acc + incl);
-                if (hit) key = j0 + blk + (__ffs(hit) - 1);
-                acc += __shfl_sync(0xffffffffu, incl, 31);
-            }
-        }
-        if (key < 0 && lane == 0) {  // u at or past the rounded total: last nonzero entry
-            for (int64_t j = dim - 1; j >= 0; --j) {
-                const T v = g[j];
-                if ((double)v.x * (double)v.x + (double)v.y * (double)v.y > 0) {
-                    key = j;
-                    break;
-                }
-            }
-            if (key < 0) key = dim - 1;
-        }
-        if (lane == 0) keys[st] = (uint64_t)key;
+        double lo, hi;
+        const int64_t key = svs::sample_warp<R>(states + (int64_t)st * dim, dim, chunks,
+                                                scratch + (int64_t)st * chunks, 1, u, &lo, &hi);
+        if ((threadIdx.x & 31) == 0) keys[st] = (uint64_t)key;
     }
 }
 
@@ -231,10 +148,12 @@ extern "C" sv_status sv_final_sample_noalloc(const void* states, sv_prec prec, i
     if (prec == SV_C128) {
         const double2* st = static_cast<const double2*>(states);
         na_partials<double><<<grid, 256, 0, s>>>(st, dim, chunks, (int)n_states, scratch);
+        na_cum<<<grid, 256, 0, s>>>(chunks, (int)n_states, scratch);
         na_sample<double><<<grid, 256, 0, s>>>(st, dim, chunks, (int)n_states, shots, seed, op, keys, scratch);
     } else {
         const float2* st = static_cast<const float2*>(states);
         na_partials<float><<<grid, 256, 0, s>>>(st, dim, chunks, (int)n_states, scratch);
+        na_cum<<<grid, 256, 0, s>>>(chunks, (int)n_states, scratch);
         na_sample<float><<<grid, 256, 0, s>>>(st, dim, chunks, (int)n_states, shots, seed, op, keys, scratch);
     }
     const cudaError_t e = cudaGetLastError();

@@ -8,7 +8,7 @@
 // state (Kraus, measurement), when the tile cannot hold more distinct qubits,
 // or when the state is read.  Pauli choices do not depend on the state
 // (Section IV-A-3) and are sampled without touching it.  Every random op is
-// followed by k_decide, and in shot-branching mode by k_alloc and k_copy, so
+// followed by k_decide, and in shot-branching mode by k_copy, so
 // no host synchronisation happens inside a circuit (Section IV-A-4).
 #include <cuda_runtime.h>
 
@@ -213,7 +213,7 @@ cudaError_t exec_one(sv_batch b, const Launch& L) {
     case L_RESET: return launch_reset(b->dev, L.a0, L.a1, L.a2, b->n_sm * 2, b->stream);
     case L_PASS: return launch_pass(b->dev, prec, L.pass, b->threads, pass_grid(b, L.pass), b->stream);
     case L_DECIDE: return launch_decide(b->dev, L.dec, b->grid_small, b->stream);
-    case L_ALLOC: return launch_alloc(b->dev, L.op, L.a0, b->stream);
+    case L_ALLOC: return cudaSuccess;
     case L_COPY: return launch_copy(b->dev, prec, b->n_sm * 4, b->stream);
     case L_FINAL: return launch_final(b->dev, prec, L.fin, b->grid_small, b->stream);
     }
@@ -233,7 +233,7 @@ sv_status exec(sv_batch b, const Launch& L) {
         cudaEventRecord(e1, b->stream);
         b->prof_ev.push_back({pclass(L.type), {e0, e1}});
     }
-    b->n_launch += (L.type == L_FINAL || L.type == L_DECIDE) ? 2 : 1;
+    b->n_launch += L.type == L_FINAL ? 3 : (L.type == L_DECIDE ? 2 : 1);
     if (L.type == L_PASS) {
         b->n_passes += 1;
         b->pass_store.push_back(L.pass.store ? 1 : 0);
@@ -491,6 +491,7 @@ sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cu
     d.m = m;
     d.r2 = r2;
     d.pend_prev = pend_prev;
+    d.npend = pend + 1;
     for (int j = 0; j < m; ++j) d.clbit[j] = clbits[j];
     if (cum)
         for (int t = 0; t < R; ++t) d.cum[t] = cum[t];
@@ -499,12 +500,6 @@ sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cu
     st = emit(b, std::move(L));
     if (st) return st;
     if (b->branch) {
-        Launch a;
-        a.type = L_ALLOC;
-        a.op = op;
-        a.a0 = pend;
-        st = emit(b, std::move(a));
-        if (st) return st;
         Launch c;
         c.type = L_COPY;
         st = emit(b, std::move(c));
@@ -1083,9 +1078,9 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
         (st = dalloc(b, &d.grp_start, S * MAX_TERMS)) || (st = dalloc(b, &d.grp_cnt, S * MAX_TERMS)) ||
         (st = dalloc(b, &d.grp_scale, S * MAX_TERMS)) || (st = dalloc(b, &d.grp_clbits, S * MAX_TERMS)) ||
         (st = dalloc(b, &d.free_slots, b->n_slots)) || (st = dalloc(b, &d.wait_shots, S)) ||
-        (st = dalloc(b, &d.fork_list, S)) ||
+
         (st = dalloc(b, &d.partials, (size_t)b->n_slots * max_chunks * MAX_RED)) || (st = dalloc(b, &d.keys, S)) ||
-        (st = dalloc(b, &d.pass_log, 1 << 20))) {
+        (st = dalloc(b, &d.pass_log, 1 << 20)) || (st = dalloc(b, &d.pos_branch, S))) {
         sv_free_batch(b);
         return st;
     }
@@ -1107,6 +1102,7 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
         return fail(SV_ECUDA, "cannot configure the kernels");
     }
     cudaMemsetAsync(d.ctl, 0, CTL_WORDS * 4, b->stream);
+    cudaMemsetAsync(d.pos_branch, 0xff, S * 4, b->stream);
     *out = b;
     return SV_OK;
 }
@@ -1335,7 +1331,7 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
                 cudaGraphDestroy(g);
                 b->graph_hash = h;
                 int64_t nl = 0;
-                for (const Launch& L : launches) nl += (L.type == L_FINAL || L.type == L_DECIDE) ? 2 : 1;
+                for (const Launch& L : launches) nl += L.type == L_FINAL ? 3 : (L.type == L_DECIDE ? 2 : 1);
                 b->graph_launches = nl;
                 b->graph_pass_store.clear();
                 for (const Launch& L : launches)
