@@ -1285,7 +1285,6 @@ __device__ __forceinline__ int draw_choice(const DevBatch& d, const DecideDesc& 
 __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __grid_constant__ DecideDesc dd) {
     __shared__ double p_sh[MAX_TERMS], cum_sh[MAX_TERMS];
     __shared__ int bincnt[MAX_TERMS], binbase[MAX_TERMS], binrun[MAX_TERMS];
-    __shared__ int wcnt[DEC_THREADS / 32][MAX_TERMS];
     __shared__ int ng_sh;
     const int n_br = d.ctl[CTL_NBR];
     const int R = dd.R;
@@ -1330,28 +1329,21 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
         }
         __syncthreads();
         if (ng_sh > 1 && dd.fork) {
+            // partition by outcome in one sweep: positions within a group come
+            // from warp-aggregated shared-memory counters, so the order of shots
+            // inside a group is not fixed (no result depends on it)
             for (int base = 0; base < cnt; base += nth) {
                 const int i = base + tid;
                 const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
-                for (int e = tid; e < (nth >> 5) * MAX_TERMS; e += nth) (&wcnt[0][0])[e] = 0;
-                __syncthreads();
                 const unsigned peers = __match_any_sync(0xffffffffu, sel);
                 const int rank = __popc(peers & ((1u << lane) - 1u));
-                if (sel >= 0 && rank == 0) wcnt[warp][sel] = __popc(peers);
-                __syncthreads();
-                if (sel >= 0) {
-                    int before = 0;
-                    for (int w = 0; w < warp; ++w) before += wcnt[w][sel];
-                    d.perm_tmp[start + binbase[sel] + binrun[sel] + before + rank] = d.perm[start + i];
-                }
-                __syncthreads();
-                if (tid < R) {
-                    int tot = 0;
-                    for (int w = 0; w < (nth >> 5); ++w) tot += wcnt[w][tid];
-                    binrun[tid] += tot;
-                }
-                __syncthreads();
+                const int leader = __ffs(peers) - 1;
+                int pos = 0;
+                if (sel >= 0 && rank == 0) pos = atomicAdd(&binrun[sel], __popc(peers));
+                pos = __shfl_sync(0xffffffffu, pos, leader);
+                if (sel >= 0) d.perm_tmp[start + binbase[sel] + pos + rank] = d.perm[start + i];
             }
+            __syncthreads();
             for (int i = tid; i < cnt; i += nth) d.perm[start + i] = d.perm_tmp[start + i];
             __syncthreads();
         }
@@ -1652,8 +1644,9 @@ cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int thre
 
 cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int grid, cudaStream_t s) {
     // small branches first: a branch the big kernel partitions may end up
-    // with DEC_SMALL shots or fewer and must not be decided twice
-    k_decide_small<<<grid, DECS_WARPS * 32, 0, s>>>(d, dd);
+    // with DEC_SMALL shots or fewer and must not be decided twice.  The small
+    // kernel is latency-bound: one warp per branch, in one wave
+    k_decide_small<<<8 * grid, DECS_WARPS * 32, 0, s>>>(d, dd);
     k_decide_big<<<grid, DEC_THREADS, 0, s>>>(d, dd);
     return cudaGetLastError();
 }
