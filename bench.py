@@ -105,6 +105,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def pass_traffic(args):
+    """DRAM bytes per k_pass launch from the committed ncu record, or None when
+    the kernels have changed since it was taken or the workload differs."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_pass_traffic_cfg2_su4_16.txt")
+    if not os.path.exists(path) or args.shots:
+        return None
+    rec = dict(ln.split(None, 1) for ln in open(path).read().strip().splitlines())
+    src = os.path.join(ROOT, "paper_2308_03399_gb300", "csrc", "sv_kernels.cu")
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    if rec.get("source_sha1") != sha or rec.get("workload") != f"{args.workload}:{args.mode}:{args.prec}":
+        return None
+    return float(rec["dram_bytes_per_step"]) / float(rec["launches"])
+
+
 def cpu_baseline(circ, seed, budget_s=15.0):
     """The oracle as it stands, on the host's cores, on a bounded sample of
     the workload's shots (shots are independent, so shots/s scales)."""
@@ -116,7 +131,7 @@ def cpu_baseline(circ, seed, budget_s=15.0):
     O.run_shots(oc, seed, 0, n, threads, want_outcomes=False)
     dt = time.perf_counter() - t0
     # grow the sample to about budget_s of work
-    n2 = int(max(n, min(20 * n, n * budget_s / max(dt, 1e-3))))
+    n2 = int(max(n, min(200 * n, n * budget_s / max(dt, 1e-3))))
     if n2 > n:
         t0 = time.perf_counter()
         O.run_shots(oc, seed, 0, n2, threads, want_outcomes=False)
@@ -236,7 +251,10 @@ def main():
     if args.timed_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "shots/s", "ms_per_step": total_ms / args.steps,
-                              "shots": n_shots, "workload": circ.name, "clocks": clk}), flush=True)
+                              "shots": n_shots, "workload": circ.name, "mode": args.mode, "precision": args.prec,
+                              "pass_bytes_per_step": st["pass_bytes"] / args.steps,
+                              "passes_per_step": st["passes"] / args.steps,
+                              "launches_per_step": launches_per_step, "clocks": clk}), flush=True)
         b.close()
         return
 
@@ -271,10 +289,7 @@ def main():
     pass_ms, n_pass = prof["pass"]
     hbm_peak, peak_kind = peaks()
     achieved = stp["pass_bytes"] / (pass_ms / 1e3) / 1e9 if pass_ms > 0 else 0.0
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "pass_traffic.json")
-    if os.path.exists(tfile):
-        traffic = json.load(open(tfile)).get(f"{args.workload}:{args.mode}:{args.prec}")
+    traffic = pass_traffic(args)
 
     line = {
         "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
@@ -289,6 +304,7 @@ def main():
                 "d2h_bytes_per_step": int(keys.nbytes)},
         "roofline": {"bound": "hbm", "kernel": "k_pass", "achieved": achieved, "peak": hbm_peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": stp["pass_bytes"] / max(n_pass, 1),
                      "algorithmic_bytes_per_step": stp["pass_bytes"] / prof_steps,
                      "pass_ms_per_step": pass_ms / prof_steps, "pass_launches_per_step": n_pass / prof_steps,
                      "share_of_step": pass_ms / max(prof["total"][0], 1e-9)},
