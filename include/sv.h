@@ -240,6 +240,31 @@ sv_status sv_final_sample_noalloc(const void *states, sv_prec prec, int n_qubits
                                   const uint32_t *shots, uint64_t seed, uint32_t op, uint64_t *keys,
                                   void *cuda_stream);
 
+/* Learned cost model ------------------------------------------------------
+ * A small MLP, n_in -> n_hidden -> n_hidden -> 1 with ReLU, that predicts the
+ * log run time of a circuit under a candidate configuration (batch or
+ * branch mode, fusion width, pass path, ...), trained on the simulator's own
+ * timing logs.  Forward, backward (loss = mean over samples of
+ * 0.5 (y - t)^2) and Adam run in the library's CUDA kernels; parameters are
+ * one float32 array W1[H x n_in] b1[H] W2[H x H] b2[H] w3[H] b3[1].  x is
+ * host, row-major n x n_in; t and y are host, n long.  The model owns its
+ * device memory and stream; every call synchronises.  (The paper has no
+ * learned part; it ends by noting that the technique has to be chosen per
+ * application, Section VI.)                                                   */
+typedef struct sv_mlp_s *sv_mlp;
+sv_status sv_mlp_create(int n_in, int n_hidden, sv_mlp *out);   /* n_in 1..64, n_hidden 1..128 */
+sv_status sv_mlp_free(sv_mlp m);
+uint64_t sv_mlp_num_params(sv_mlp m);
+sv_status sv_mlp_set_params(sv_mlp m, const float *params, uint64_t n);  /* also resets Adam state */
+sv_status sv_mlp_get_params(sv_mlp m, float *params, uint64_t n);
+sv_status sv_mlp_forward(sv_mlp m, const float *x, int n, float *y);
+/* summed gradient of the loss over the n samples (grad: host, num_params) */
+sv_status sv_mlp_gradient(sv_mlp m, const float *x, const float *t, int n, float *loss, float *grad);
+/* epochs of shuffled minibatch Adam (shuffle keyed by seed); final_loss =
+ * the loss over all n samples afterwards                                      */
+sv_status sv_mlp_train(sv_mlp m, const float *x, const float *t, int n, int epochs, int batch, float lr,
+                       uint64_t seed, float *final_loss);
+
 /* Wait for the batch's stream, at most timeout_ns (0 = no limit). */
 sv_status sv_sync(sv_batch b, uint64_t timeout_ns);
 

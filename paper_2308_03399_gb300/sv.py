@@ -71,11 +71,21 @@ def lib():
                 "sv_stats": [P, P],
                 "sv_profile": [P, P, P],
                 "sv_sync": [P, U64],
+                "sv_final_sample_noalloc": [P, I, I, U32, P, U64, U32, P, P],
+                "sv_mlp_create": [I, I, P],
+                "sv_mlp_free": [P],
+                "sv_mlp_set_params": [P, P, U64],
+                "sv_mlp_get_params": [P, P, U64],
+                "sv_mlp_forward": [P, P, I, P],
+                "sv_mlp_gradient": [P, P, P, I, P, P],
+                "sv_mlp_train": [P, P, P, I, I, I, C.c_float, U64, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
                 f.argtypes = args
                 f.restype = C.c_int
+            L.sv_mlp_num_params.argtypes = [P]
+            L.sv_mlp_num_params.restype = U64
             _lib = L
     return _lib
 
@@ -215,9 +225,63 @@ class Batch:
         _check(lib().sv_sync(self.h, timeout_ns))
 
 
+class MLP:
+    """The learned cost model (sv_mlp_*): forward, gradient and Adam training
+    run in the library's CUDA kernels."""
+
+    def __init__(self, n_in, n_hidden=64):
+        self.n_in, self.n_hidden = n_in, n_hidden
+        h = C.c_void_p()
+        _check(lib().sv_mlp_create(n_in, n_hidden, C.byref(h)))
+        self.h = h
+        self.n_params = int(lib().sv_mlp_num_params(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sv_mlp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        _check(lib().sv_mlp_set_params(self.h, _p(p), p.size))
+
+    def get_params(self):
+        p = np.zeros(self.n_params, np.float32)
+        _check(lib().sv_mlp_get_params(self.h, _p(p), p.size))
+        return p
+
+    def forward(self, x):
+        x = np.ascontiguousarray(x, np.float32)
+        y = np.zeros(x.shape[0], np.float32)
+        _check(lib().sv_mlp_forward(self.h, _p(x), x.shape[0], _p(y)))
+        return y
+
+    def gradient(self, x, t):
+        x = np.ascontiguousarray(x, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_float()
+        _check(lib().sv_mlp_gradient(self.h, _p(x), _p(t), x.shape[0], C.byref(loss), _p(g)))
+        return float(loss.value), g
+
+    def train(self, x, t, epochs=200, batch=64, lr=1e-3, seed=0):
+        x = np.ascontiguousarray(x, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        loss = C.c_float()
+        _check(lib().sv_mlp_train(self.h, _p(x), _p(t), x.shape[0], epochs, batch, lr, seed, C.byref(loss)))
+        return float(loss.value)
+
+
 def exported_symbols():
     """Names of the entry points the header declares (checked by the tests)."""
     return ["sv_alloc_batch", "sv_free_batch", "sv_set_option", "sv_apply_gate_batch", "sv_sample_noise",
             "sv_measure_batch", "sv_branch", "sv_counts", "sv_get_keys", "sv_waiting", "sv_run_circuit",
             "sv_get_amplitudes", "sv_get_outcomes", "sv_get_fork_events", "sv_stats", "sv_profile", "sv_sync",
-            "sv_last_error"]
+            "sv_last_error", "sv_final_sample_noalloc", "sv_mlp_create", "sv_mlp_free", "sv_mlp_num_params",
+            "sv_mlp_set_params", "sv_mlp_get_params", "sv_mlp_forward", "sv_mlp_gradient", "sv_mlp_train"]
