@@ -120,6 +120,40 @@ def pass_traffic(args):
     return float(rec["dram_bytes_per_step"]) / float(rec["launches"])
 
 
+def plain_vs_batched(torch, flush_buf):
+    """Config 1 (10-qubit brickwork, 1000 shots): the plain per-shot float64
+    form (one state, one launch per op, host-side choices -- the paper's
+    conventional "GPU: Base") against the batched forms, shots/s each,
+    device time with CUDA events."""
+    from paper_2308_03399_gb300 import sv
+    circ, shots, seed = workload("cfg1")
+    cs = sv.circuit_struct(circ.to_arrays())
+    stream = torch.cuda.current_stream()
+    out = {"workload": circ.name, "shots": shots}
+    for key, mode, prec, warm, steps in (("plain_fp64", sv.SV_PLAIN, sv.SV_C128, 1, 1),
+                                         ("batched_fp64", sv.SV_BATCH, sv.SV_C128, 3, 3),
+                                         ("batched_fp32", sv.SV_BATCH, sv.SV_C64, 3, 3)):
+        b = sv.Batch(circ.n_qubits, shots, 1, prec, mode, seed, stream=stream.cuda_stream)
+        graph = mode != sv.SV_PLAIN
+        for _ in range(warm):
+            b.run_circuit(cs, use_graph=graph)
+        ms = 0.0
+        for _ in range(steps):
+            flush_buf.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run_circuit(cs, use_graph=graph)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        b.close()
+        out[key + "_shots_per_s"] = shots * steps / (ms / 1e3)
+    out["ratio_fp32_over_plain"] = out["batched_fp32_shots_per_s"] / out["plain_fp64_shots_per_s"]
+    out["ratio_fp64_over_plain"] = out["batched_fp64_shots_per_s"] / out["plain_fp64_shots_per_s"]
+    return out
+
+
 def cpu_baseline(circ, seed, budget_s=15.0):
     """The oracle as it stands, on the host's cores, on a bounded sample of
     the workload's shots (shots are independent, so shots/s scales)."""
@@ -181,6 +215,8 @@ def main():
     ap.add_argument("--shots", type=int, default=0, help="override the workload's shot count (profiling)")
     ap.add_argument("--timed-only", action="store_true", help="skip the end-to-end and roofline phases")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one (profiling)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the config-1 plain-vs-batched comparison")
+    ap.add_argument("--max-active", type=int, default=0, help="fusion width (qubits per pass), 0 = library default")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -211,6 +247,8 @@ def main():
     stream = torch.cuda.current_stream()
     b = sv.Batch(circ.n_qubits, n_shots, max(1, circ.n_clbits), prec, mode, seed, stream=stream.cuda_stream)
     use_graph = mode != sv.SV_PLAIN and not args.no_graph
+    if args.max_active:
+        b.set_option(sv.SV_OPT_MAX_ACTIVE, args.max_active)
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):
@@ -252,6 +290,7 @@ def main():
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "shots/s", "ms_per_step": total_ms / args.steps,
                               "shots": n_shots, "workload": circ.name, "mode": args.mode, "precision": args.prec,
+                              "max_active": args.max_active,
                               "pass_bytes_per_step": st["pass_bytes"] / args.steps,
                               "passes_per_step": st["passes"] / args.steps,
                               "launches_per_step": launches_per_step, "clocks": clk}), flush=True)
@@ -314,6 +353,8 @@ def main():
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(circ, seed)
+    if rank == 0 and not args.no_plain and world == 1:
+        line["plain_vs_batched"] = plain_vs_batched(torch, flush_buf)
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

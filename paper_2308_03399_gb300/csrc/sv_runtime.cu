@@ -110,7 +110,7 @@ struct sv_batch_s {
     int n_slots = 0;
     int tb = 11, chunks = 1, chunks_final = 1;
     int threads = 256, grid_pass = 0, grid_small = 0, n_sm = 0;
-    int max_active = 8, max_stages = MAX_STAGES;
+    int max_active = 8, max_stages = MAX_STAGES;  // max_active is set in sv_alloc_batch
     bool branch = false;
     // device memory
     std::vector<void*> allocs;
@@ -1017,6 +1017,11 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
     cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
     b->grid_small = 2 * b->n_sm;
     b->tb = std::min(n_qubits, prec == SV_C128 ? 10 : 11);
+    // Fusion width: when the whole state is one tile, fuse up to 8 qubits per
+    // pass; otherwise at most 4, so passes run on the register path (wider
+    // passes over a bigger state leave the tile few contiguous low qubits
+    // and its bulk copies turn short)
+    b->max_active = n_qubits <= b->tb ? 8 : 4;
     const int64_t tiles = 1ll << (n_qubits - b->tb);
     b->chunks = (int)std::min<int64_t>(tiles, MAX_CHUNKS);
     b->chunks_final = (int)std::min<int64_t>(std::max<int64_t>(b->dim / 2048, 1), MAX_CHUNKS);
@@ -1143,7 +1148,9 @@ sv_status sv_set_option(sv_batch b, sv_option opt, int64_t v) {
         b->tb = std::min<int>(b->n, v ? (int)v : (b->prec == SV_C128 ? 10 : 11));
         b->chunks = (int)std::min<int64_t>(1ll << (b->n - b->tb), b->dev.max_chunks);
         return SV_OK;
-    case SV_OPT_MAX_ACTIVE: b->max_active = v ? (int)std::max<int64_t>(4, v) : 8; return SV_OK;
+    case SV_OPT_MAX_ACTIVE:
+        b->max_active = v ? (int)std::max<int64_t>(2, v) : (b->n <= b->tb ? 8 : 4);
+        return SV_OK;
     case SV_OPT_MAX_STAGES: b->max_stages = v ? (int)std::min<int64_t>(std::max<int64_t>(v, 1), MAX_STAGES) : MAX_STAGES; return SV_OK;
     case SV_OPT_THREADS:
         if (v && v != 128 && v != 256) return fail(SV_EINVAL, "threads must be 128 or 256");
