@@ -201,6 +201,95 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_config4(args):
+    """Config 4: 64 brickwork circuits of 8-24 qubits, 10^5 shots split
+    unevenly, all run from one captured CUDA graph (sv_run_circuits).  Each
+    circuit's configuration (batch or branch mode, fusion width, pass path)
+    is picked by the learned cost model; with --autotune the same run with
+    the exhaustive autotuner's picks (and the time the search itself took)
+    is reported beside it."""
+    import torch
+    from paper_2308_03399_gb300 import sv
+    from paper_2308_03399_gb300 import tuner as T
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    circs, shots = __import__("paper_2308_03399_gb300.workloads", fromlist=["config4"]).config4()
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    free = torch.cuda.mem_get_info()[0]
+    pool = int(free * 0.8)
+    need = [s * (8 << c.n_qubits) for c, s in zip(circs, shots)]
+    model = T.CostModel.load()
+    cands = T.candidates()
+
+    def picks_by(fn):
+        out = []
+        for c, s, nd in zip(circs, shots, need):
+            ok = [cfg for cfg in cands if cfg["mode"] == "branch" or nd <= pool // 8]
+            out.append(fn(c, s, ok))
+        return out
+
+    def run(picks, label):
+        # memory: batch-mode circuits get exactly one state per shot, the
+        # branching ones share the rest in proportion to their full need
+        batch_need = sum(nd for nd, p in zip(need, picks) if p["mode"] == "batch")
+        rest = max(pool - batch_need, 0)
+        br_need = sum(nd for nd, p in zip(need, picks) if p["mode"] == "branch") or 1
+        bs, structs = [], []
+        for c, s, nd, p, i in zip(circs, shots, need, picks, range(len(circs))):
+            mode = sv.SV_BATCH if p["mode"] == "batch" else sv.SV_BRANCH
+            # per slot: the state plus its reduction partials (<= 1024 chunks x 16 x 8 B)
+            st_bytes = (8 << c.n_qubits) + 128 * max(min(max(1 << max(c.n_qubits - 11, 0), 1), 1024), 1)
+            budget = s * st_bytes + (1 << 20) if mode == sv.SV_BATCH else \
+                max(min(s * st_bytes, rest * nd // br_need), 2 * st_bytes)
+            b = sv.Batch(c.n_qubits, s, 1, sv.SV_C64, mode, 4000 + i, mem_budget=budget, stream=stream.cuda_stream)
+            b.set_option(sv.SV_OPT_MAX_ACTIVE, p["max_active"])
+            b.set_option(sv.SV_OPT_PASS_PATH, p["path"])
+            b.set_option(sv.SV_OPT_JOINT_KRAUS, p["joint"])
+            bs.append(b)
+            structs.append(sv.circuit_struct(c.to_arrays()))
+        for _ in range(args.warmup):
+            sv.run_circuits(bs, structs, use_graph=True)
+        for b in bs:
+            b.stats()
+        ms = []
+        for _ in range(args.steps):
+            flush_buf.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv.run_circuits(bs, structs, use_graph=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        launches = sum(b.stats()["launches"] for b in bs)
+        for b in bs:
+            b.close()
+        return {"label": label, "ms_per_step": float(np.mean(ms)), "shots_per_s": sum(shots) / (np.mean(ms) / 1e3),
+                "gpu_launches_per_step": launches / args.steps,
+                "batch_mode_circuits": sum(p["mode"] == "batch" for p in picks)}
+
+    t0 = time.perf_counter()
+    mlp_picks = picks_by(lambda c, s, ok: model.pick(c, s, ok))
+    t_pick = time.perf_counter() - t0
+    res = run(mlp_picks, "cost model")
+    line = {"metric": METRIC, "value": res["shots_per_s"], "unit": "shots/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "cfg4_64_brickwork_8_24q", "circuits": len(circs), "shots": sum(shots),
+                       "graph": "one CUDA graph for all 64 circuits", "l2": "flushed between steps (512 MB)"},
+            "gpu_launches": int(res["gpu_launches_per_step"] * args.steps), "cost_model_pick_s": t_pick,
+            "cost_model": res}
+    if args.autotune:
+        t0 = time.perf_counter()
+        small = [c for c in cands if c["joint"] == 1 and c["path"] == 0 and c["max_active"] in (3, 8)]
+        tuned = picks_by(lambda c, s, ok: T.autotune(c, s, cands=[x for x in small if x in ok], reps=1)[0])
+        line["autotune_search_s"] = time.perf_counter() - t0
+        line["autotuned"] = run(tuned, "autotuner")
+        line["fixed_branch"] = run([dict(T.DEFAULT) for _ in circs], "fixed: branch, default fusion")
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,6 +306,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one (profiling)")
     ap.add_argument("--no-plain", action="store_true", help="skip the config-1 plain-vs-batched comparison")
     ap.add_argument("--max-active", type=int, default=0, help="fusion width (qubits per pass), 0 = library default")
+    ap.add_argument("--autotune", action="store_true", help="config 4: also run the autotuner's picks")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -225,11 +315,15 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "cfg4":
+        return run_config4(args)
 
     import torch
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a GPU (the library has no CPU path)")
     torch.cuda.set_device(local)
+    # one dedicated stream for the library, the L2 flush and the events
+    torch.cuda.set_stream(torch.cuda.Stream())
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -188,6 +188,16 @@ sv_status sv_waiting(sv_batch b, uint64_t *n_waiting);
  * graph once per circuit and replays it.                                    */
 sv_status sv_run_circuit(sv_batch b, const sv_circuit *c, int use_graph);
 
+/* Several circuits, one per batch (n of them, batches sharing one stream;
+ * batch and branch modes may mix), run back to back: with use_graph != 0 the
+ * launch sequences of all of them, each with its reset, are captured into
+ * ONE CUDA graph (cached for the same batches and circuits) and replayed
+ * (the paper's multi-circuit batching, Section VI).  Shot-branching
+ * batches whose forks parked shots on the waiting list then restart them
+ * outside the graph until none wait.  Per-shot keys via sv_get_keys.
+ * Batches and circuits must stay alive while the graph is cached.           */
+sv_status sv_run_circuits(sv_batch *batches, const sv_circuit *const *circuits, int n, int use_graph);
+
 /* Test / introspection ---------------------------------------------------- */
 
 /* State of the branch that holds `shot`, as 2*len float64 (re, im); len

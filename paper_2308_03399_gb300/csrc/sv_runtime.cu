@@ -151,6 +151,15 @@ struct sv_batch_s {
     bool upload_each = false;
     double h2d_bytes = 0;
     int pass_path = 0;  // 0 auto, 1 shared-memory tiles only
+    // sv_run_circuits: one graph over several batches (kept by the first)
+    uint64_t multi_hash = 0;
+    cudaGraphExec_t multi_exec = nullptr;
+    std::vector<std::vector<Launch>> multi_lists;
+    std::vector<uint64_t> multi_gens;
+    // the constant pool holds one recorded circuit at a time; every recording
+    // (and every growth of the pool) starts a new generation, and a cached
+    // graph replays only while the generations it captured are current
+    uint64_t pool_gen = 0, graph_gen = 0;
     bool joint = true;  // decide back-to-back one-qubit Kraus pairs from one pass
     std::map<int, int> reg_occ;
     int slot_limit = 0;
@@ -250,10 +259,45 @@ sv_status emit(sv_batch b, Launch&& L) {
 }
 
 // ---- pool ------------------------------------------------------------------
+// grow the device pool and its pinned staging copy (everything is uploaded
+// again afterwards)
+sv_status grow_pool(sv_batch b) {
+    CU(cudaStreamSynchronize(b->stream));
+    size_t pc = b->pool_cap, ic = b->ipool_cap;
+    while (pc < b->pool.size()) pc *= 2;
+    while (ic < b->ipool.size()) ic *= 2;
+    void *dp = nullptr, *hp = nullptr, *di = nullptr, *hi = nullptr;
+    if (cudaMalloc(&dp, pc * 8) != cudaSuccess || cudaMallocHost(&hp, pc * 8) != cudaSuccess ||
+        cudaMalloc(&di, ic * 4) != cudaSuccess || cudaMallocHost(&hi, ic * 4) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dp);
+        cudaFreeHost(hp);
+        cudaFree(di);
+        return fail(SV_ENOMEM, "cannot grow the constant pool");
+    }
+    cudaFree(b->d_pool);
+    cudaFreeHost(b->h_pool);
+    cudaFree(b->d_ipool);
+    cudaFreeHost(b->h_ipool);
+    b->d_pool = dp;
+    b->h_pool = hp;
+    b->d_ipool = (int32_t*)di;
+    b->h_ipool = (int32_t*)hi;
+    b->pool_cap = pc;
+    b->ipool_cap = ic;
+    b->pool_gen += 1;
+    b->dev.pool = dp;
+    b->dev.ipool = (const int32_t*)di;
+    b->pool_up = b->ipool_up = 0;
+    return SV_OK;
+}
+
 sv_status upload_pool(sv_batch b) {
     const size_t rsz = b->prec == SV_C128 ? 8 : 4;
-    if (b->pool.size() > b->pool_cap || b->ipool.size() > b->ipool_cap)
-        return fail(SV_ENOMEM, "constant pool full (circuit too large for one batch)");
+    if (b->pool.size() > b->pool_cap || b->ipool.size() > b->ipool_cap) {
+        sv_status st = grow_pool(b);
+        if (st) return st;
+    }
     if (b->pool.size() > b->pool_up) {
         for (size_t i = b->pool_up; i < b->pool.size(); ++i) {
             if (rsz == 8) reinterpret_cast<double*>(b->h_pool)[i] = b->pool[i];
@@ -980,6 +1024,57 @@ sv_status run_plain(sv_batch b, const sv_circuit* c) {
     return SV_OK;
 }
 
+// the launch sequence of a whole circuit (without the reset / init of the
+// root), with its constants uploaded
+sv_status record_circuit(sv_batch b, const sv_circuit* c, std::vector<Launch>& launches) {
+    sv_status st = reset_pool(b);
+    if (st) return st;
+    b->pool_gen += 1;
+    b->started = true;  // reset / init are issued by the caller, per run
+    b->rec = &launches;
+    b->n_pend = 0;
+    for (int i = 0; i < c->n_ops && !st; ++i) {
+        if (b->joint && i + 1 < c->n_ops && c->kind[i] == SV_OP_KRAUS && c->kind[i + 1] == SV_OP_KRAUS &&
+            c->nq[i] == 1 && c->nq[i + 1] == 1 && c->qubits[c->q_off[i]] != c->qubits[c->q_off[i + 1]] &&
+            c->n_terms[i] * c->n_terms[i + 1] <= MAX_RED) {
+            st = op_kraus_pair(b, (uint32_t)i, c->qubits[c->q_off[i]], c->n_terms[i], c->data + c->d_off[i],
+                               (uint32_t)(i + 1), c->qubits[c->q_off[i + 1]], c->n_terms[i + 1],
+                               c->data + c->d_off[i + 1]);
+            ++i;
+            continue;
+        }
+        st = circuit_op(b, c, i);
+    }
+    if (!st) st = flush(b);
+    b->rec = nullptr;
+    if (st) return st;
+    return upload_pool(b);
+}
+
+// restart the waiting list of a shot-branching batch until it is empty
+// (Section IV-B-2), launching one by one
+sv_status drain_waiting(sv_batch b, const std::vector<Launch>& launches) {
+    for (;;) {
+        int32_t ctl[CTL_WORDS];
+        sv_status st = read_ctl(b, ctl);
+        if (st) return st;
+        if (ctl[CTL_ERR] || ctl[CTL_NWAIT] == 0) return SV_OK;
+        Launch r;
+        r.type = L_RESET;
+        r.a0 = 1;
+        r.a1 = ctl[CTL_NWAIT];
+        r.a2 = 1;
+        if ((st = exec(b, r))) return st;
+        Launch in;
+        in.type = L_INIT;
+        in.a0 = 1;
+        if ((st = exec(b, in))) return st;
+        for (const Launch& L : launches)
+            if ((st = exec(b, L))) return st;
+        b->restarts += 1;
+    }
+}
+
 }  // namespace
 
 // =============================================================================
@@ -1089,8 +1184,8 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
         sv_free_batch(b);
         return st;
     }
-    b->pool_cap = 1 << 22;
-    b->ipool_cap = 1 << 20;
+    b->pool_cap = 1 << 16;
+    b->ipool_cap = 1 << 14;
     if (cudaMalloc(&b->d_pool, b->pool_cap * 8) != cudaSuccess ||
         cudaMalloc((void**)&b->d_ipool, b->ipool_cap * 4) != cudaSuccess ||
         cudaMallocHost(&b->h_pool, b->pool_cap * 8) != cudaSuccess ||
@@ -1116,6 +1211,7 @@ sv_status sv_free_batch(sv_batch b) {
     if (!b) return SV_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->multi_exec) cudaGraphExecDestroy(b->multi_exec);
     for (auto& e : b->prof_ev) {
         cudaEventDestroy(e.second.first);
         cudaEventDestroy(e.second.second);
@@ -1274,30 +1370,9 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
     }
     // launch list of the op sequence (after the reset / init of the root)
     const uint64_t h = circuit_hash(b, c);
-    const bool cached = use_graph && b->graph_exec && b->graph_hash == h;
+    const bool cached = use_graph && b->graph_exec && b->graph_hash == h && b->graph_gen == b->pool_gen;
     std::vector<Launch> launches;
-    if (!cached) {
-        if ((st = reset_pool(b))) return st;
-        b->started = true;  // reset / init are issued below, per run
-        b->rec = &launches;
-        b->n_pend = 0;
-        for (int i = 0; i < c->n_ops && !st; ++i) {
-            if (b->joint && i + 1 < c->n_ops && c->kind[i] == SV_OP_KRAUS && c->kind[i + 1] == SV_OP_KRAUS &&
-                c->nq[i] == 1 && c->nq[i + 1] == 1 && c->qubits[c->q_off[i]] != c->qubits[c->q_off[i + 1]] &&
-                c->n_terms[i] * c->n_terms[i + 1] <= MAX_RED) {
-                st = op_kraus_pair(b, (uint32_t)i, c->qubits[c->q_off[i]], c->n_terms[i], c->data + c->d_off[i],
-                                   (uint32_t)(i + 1), c->qubits[c->q_off[i + 1]], c->n_terms[i + 1],
-                                   c->data + c->d_off[i + 1]);
-                ++i;
-                continue;
-            }
-            st = circuit_op(b, c, i);
-        }
-        if (!st) st = flush(b);
-        b->rec = nullptr;
-        if (st) return st;
-        if ((st = upload_pool(b))) return st;
-    }
+    if (!cached && (st = record_circuit(b, c, launches))) return st;
     if (cached && b->upload_each) {
         // the circuit's constants cross the bus again (end-to-end timing)
         b->pool_up = 0;
@@ -1337,6 +1412,7 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
                 CU(cudaGraphInstantiate(&b->graph_exec, g, 0));
                 cudaGraphDestroy(g);
                 b->graph_hash = h;
+                b->graph_gen = b->pool_gen;
                 int64_t nl = 0;
                 for (const Launch& L : launches) nl += L.type == L_FINAL ? 3 : (L.type == L_DECIDE ? 2 : 1);
                 b->graph_launches = nl;
@@ -1365,6 +1441,98 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
     }
     b->started = false;
     return check_device_error(b);
+}
+
+sv_status sv_run_circuits(sv_batch* bs, const sv_circuit* const* cs, int n, int use_graph) {
+    if (!bs || !cs || n < 1) return fail(SV_EINVAL, "sv_run_circuits: NULL or empty arguments");
+    sv_status st;
+    for (int i = 0; i < n; ++i) {
+        if (!bs[i] || !cs[i]) return fail(SV_EINVAL, "sv_run_circuits: NULL batch or circuit");
+        if (bs[i]->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "sv_run_circuits: plain mode runs one circuit");
+        if (bs[i]->stream != bs[0]->stream) return fail(SV_EINVAL, "sv_run_circuits: batches must share one stream");
+        if (cs[i]->n_qubits != bs[i]->n) return fail(SV_EINVAL, "sv_run_circuits: circuit / batch qubit counts differ");
+        if (!bs[i]->pend.empty()) return fail(SV_EINVAL, "sv_run_circuits: per-op calls are in progress");
+        for (int j = 0; j < i; ++j)
+            if (bs[j] == bs[i]) return fail(SV_EINVAL, "sv_run_circuits: a batch appears twice");
+    }
+    sv_batch b0 = bs[0];
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < n; ++i) {
+        const uint64_t hi = circuit_hash(bs[i], cs[i]);
+        h = fnv(h, &hi, 8);
+        h = fnv(h, &bs[i], sizeof(void*));
+    }
+    bool cached = use_graph && b0->multi_exec && b0->multi_hash == h && (int)b0->multi_gens.size() == n;
+    for (int i = 0; cached && i < n; ++i) cached = b0->multi_gens[i] == bs[i]->pool_gen;
+    if (!cached) {
+        b0->multi_lists.assign(n, {});
+        for (int i = 0; i < n; ++i) {
+            std::vector<Launch>& L = b0->multi_lists[i];
+            Launch r;
+            r.type = L_RESET;
+            r.a0 = bs[i]->branch;
+            r.a1 = (int)bs[i]->n_shots;
+            r.a2 = 0;
+            L.push_back(r);
+            Launch in;
+            in.type = L_INIT;
+            in.a0 = bs[i]->branch ? 1 : (int)bs[i]->n_shots;
+            L.push_back(in);
+            std::vector<Launch> ops;
+            if ((st = record_circuit(bs[i], cs[i], ops))) return st;
+            L.insert(L.end(), ops.begin(), ops.end());
+        }
+    }
+    if (use_graph) {
+        if (!cached) {
+            if (b0->multi_exec) {
+                cudaGraphExecDestroy(b0->multi_exec);
+                b0->multi_exec = nullptr;
+            }
+            cudaGraph_t g;
+            CU(cudaStreamBeginCapture(b0->stream, cudaStreamCaptureModeThreadLocal));
+            for (int i = 0; i < n; ++i)
+                for (const Launch& L : b0->multi_lists[i]) {
+                    cudaError_t e = exec_one(bs[i], L);
+                    if (e != cudaSuccess) {
+                        cudaStreamEndCapture(b0->stream, &g);
+                        return fail(SV_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+                    }
+                }
+            CU(cudaStreamEndCapture(b0->stream, &g));
+            CU(cudaGraphInstantiate(&b0->multi_exec, g, 0));
+            cudaGraphDestroy(g);
+            b0->multi_hash = h;
+            b0->multi_gens.resize(n);
+            for (int i = 0; i < n; ++i) b0->multi_gens[i] = bs[i]->pool_gen;
+        }
+        CU(cudaGraphLaunch(b0->multi_exec, b0->stream));
+        for (int i = 0; i < n; ++i)
+            for (const Launch& L : b0->multi_lists[i]) {
+                bs[i]->n_launch += L.type == L_FINAL ? 3 : (L.type == L_DECIDE ? 2 : 1);
+                if (L.type == L_PASS) {
+                    bs[i]->n_passes += 1;
+                    bs[i]->pass_store.push_back(L.pass.store ? 1 : 0);
+                }
+            }
+    } else {
+        for (int i = 0; i < n; ++i)
+            for (const Launch& L : b0->multi_lists[i])
+                if ((st = exec(bs[i], L))) return st;
+    }
+    // shot-branching batches whose forks found no slot: restart their
+    // waiting lists one by one (the graph covered the first round)
+    for (int i = 0; i < n; ++i) {
+        if (!bs[i]->branch) continue;
+        std::vector<Launch> ops(b0->multi_lists[i].begin() + 2, b0->multi_lists[i].end());
+        if ((st = drain_waiting(bs[i], ops))) return st;
+        bs[i]->started = false;
+    }
+    for (int i = 0; i < n; ++i) {
+        bs[i]->started = false;
+        if ((st = check_device_error(bs[i]))) return st;
+    }
+    return SV_OK;
 }
 
 sv_status sv_get_amplitudes(sv_batch b, uint64_t shot, double* out, uint64_t len) {

@@ -65,6 +65,7 @@ def lib():
                 "sv_get_keys": [P, P],
                 "sv_waiting": [P, P],
                 "sv_run_circuit": [P, P, I],
+                "sv_run_circuits": [P, P, I, I],
                 "sv_get_amplitudes": [P, U64, P, U64],
                 "sv_get_outcomes": [P, U32, P, P],
                 "sv_get_fork_events": [P, P, U64, P],
@@ -278,10 +279,18 @@ class MLP:
         return float(loss.value)
 
 
+def run_circuits(batches, circ_structs, use_graph=True):
+    """sv_run_circuits: several (batch, circuit) pairs in one CUDA graph."""
+    n = len(batches)
+    hs = (C.c_void_p * n)(*[b.h.value for b in batches])
+    cs = (C.c_void_p * n)(*[C.cast(C.pointer(c), C.c_void_p).value for c in circ_structs])
+    _check(lib().sv_run_circuits(hs, cs, n, int(use_graph)))
+
+
 def exported_symbols():
     """Names of the entry points the header declares (checked by the tests)."""
     return ["sv_alloc_batch", "sv_free_batch", "sv_set_option", "sv_apply_gate_batch", "sv_sample_noise",
             "sv_measure_batch", "sv_branch", "sv_counts", "sv_get_keys", "sv_waiting", "sv_run_circuit",
             "sv_get_amplitudes", "sv_get_outcomes", "sv_get_fork_events", "sv_stats", "sv_profile", "sv_sync",
-            "sv_last_error", "sv_final_sample_noalloc", "sv_mlp_create", "sv_mlp_free", "sv_mlp_num_params",
+            "sv_last_error", "sv_run_circuits", "sv_final_sample_noalloc", "sv_mlp_create", "sv_mlp_free", "sv_mlp_num_params",
             "sv_mlp_set_params", "sv_mlp_get_params", "sv_mlp_forward", "sv_mlp_gradient", "sv_mlp_train"]

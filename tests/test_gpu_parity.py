@@ -202,3 +202,38 @@ def test_config3_sampled_shots():
     n_shots = 256
     gpu = run_gpu(c, 3, n_shots, sv.SV_BRANCH, sv.SV_C64, want_amps=[0])
     compare_shots(c, 3, gpu, [0, 101, 255], sv.SV_C64)
+
+
+def test_run_circuits_one_graph_matches_separate_runs():
+    # three circuits, mixed modes and precisions' shot counts, one graph
+    cs = [W.brickwork(7, 4, 0.02, 0.05, seed=101), W.random_su4(8, 3, 0.05, 0.1, seed=102),
+          W.midcircuit_measure(6, 2, 0.03, [1, 4], seed=103)]
+    modes = [sv.SV_BATCH, sv.SV_BRANCH, sv.SV_BRANCH]
+    shots = [50, 120, 80]
+    ref = [run_gpu(c, 20 + i, s, m, sv.SV_C64, log=False)["keys"] for i, (c, m, s) in enumerate(zip(cs, modes, shots))]
+    import torch
+    stream = torch.cuda.Stream().cuda_stream  # one shared, non-default stream
+    structs = [sv.circuit_struct(c.to_arrays()) for c in cs]
+    bs = [sv.Batch(c.n_qubits, s, max(1, c.n_clbits), sv.SV_C64, m, 20 + i, mem_budget=1 << 30, stream=stream)
+          for i, (c, m, s) in enumerate(zip(cs, modes, shots))]
+    bs[2].set_option(sv.SV_OPT_SLOT_LIMIT, 4)  # force a waiting list in one of them
+    for _ in range(2):  # the second call replays the cached graph
+        sv.run_circuits(bs, structs, use_graph=True)
+        for b, r in zip(bs, ref):
+            assert np.array_equal(b.get_keys(), r)
+    for b in bs:
+        b.close()
+
+
+def test_alternating_circuits_on_one_batch_replay_correct_graphs():
+    # two circuits share one batch: each recording replaces the batch's
+    # constants, so a cached graph must not replay the other circuit's data
+    a = W.random_su4(6, 3, 0.05, 0.1, seed=111)
+    b = W.random_su4(6, 3, 0.05, 0.1, seed=112)
+    ka = run_gpu(a, 5, 64, sv.SV_BRANCH, sv.SV_C64, log=False)["keys"]
+    kb = run_gpu(b, 5, 64, sv.SV_BRANCH, sv.SV_C64, log=False)["keys"]
+    sa, sb = sv.circuit_struct(a.to_arrays()), sv.circuit_struct(b.to_arrays())
+    with sv.Batch(6, 64, 1, sv.SV_C64, sv.SV_BRANCH, 5) as bt:
+        for c, k in ((sa, ka), (sb, kb), (sa, ka), (sa, ka), (sb, kb)):
+            bt.run_circuit(c, use_graph=True)
+            assert np.array_equal(bt.get_keys(), k)
