@@ -1022,14 +1022,17 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
         T* gstate = states + (int64_t)slot * d.dim;
         for (int64_t gi = lane; gi < gpu; gi += 32) {
             // base: the group index with zeros inserted at the group qubits
-            // base: the group index with zeros inserted at the group qubits
             // (32-bit: a state has at most 2^30 amplitudes)
-            uint32_t base = (uint32_t)(c * gpu + gi);
+            auto group_base = [&](int64_t gidx) {
+                uint32_t bb = (uint32_t)gidx;
 #pragma unroll
-            for (int j = 0; j < WP; ++j) {
-                const uint32_t lowm = (uint32_t)stride[j] - 1u;
-                base = ((base & ~lowm) << 1) | (base & lowm);
-            }
+                for (int j = 0; j < WP; ++j) {
+                    const uint32_t lowm = (uint32_t)stride[j] - 1u;
+                    bb = ((bb & ~lowm) << 1) | (bb & lowm);
+                }
+                return bb;
+            };
+            const uint32_t base = group_base(c * gpu + gi);
             T* g = gstate + base;
             auto off = [&](int e) {
                 int o = 0;
@@ -1038,6 +1041,14 @@ __global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_const
                     if ((e >> j) & 1) o += stride[j];
                 return o;
             };
+            // the lane's next group goes to L2 ahead of its loads (no
+            // registers held): the pass is latency-bound at 16 warps per SM
+            if (gi + 32 < gpu) {
+                const T* gn = gstate + group_base(c * gpu + gi + 32);
+#pragma unroll
+                for (int e = 0; e < G; e += (sizeof(T) == 8 && PAIRED) ? 2 : 1)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(gn + off(e)));
+            }
             T v[G];
             if constexpr (sizeof(T) == 8 && PAIRED) {
 #pragma unroll
