@@ -333,7 +333,6 @@ def main():
     circ, n_shots, seed = workload(args.workload)
     if args.shots:
         n_shots = args.shots
-    seed = seed + 1000 * rank  # replicas: every rank its own independent shots
     mode = {"branch": sv.SV_BRANCH, "batch": sv.SV_BATCH, "plain": sv.SV_PLAIN}[args.mode]
     prec = {"c64": sv.SV_C64, "c128": sv.SV_C128}[args.prec]
     arrays = circ.to_arrays()
@@ -341,6 +340,8 @@ def main():
     stream = torch.cuda.current_stream()
     b = sv.Batch(circ.n_qubits, n_shots, max(1, circ.n_clbits), prec, mode, seed, stream=stream.cuda_stream)
     use_graph = mode != sv.SV_PLAIN and not args.no_graph
+    # replicas: rank r simulates global shots [r * n_shots, (r + 1) * n_shots) of one seed
+    b.set_option(sv.SV_OPT_SHOT_BASE, rank * n_shots)
     if args.max_active:
         b.set_option(sv.SV_OPT_MAX_ACTIVE, args.max_active)
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -431,7 +432,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": circ.name, "n_qubits": circ.n_qubits, "depth_ops": circ.n_ops, "shots": n_shots,
                    "mode": args.mode, "precision": args.prec, "seed": seed, "l2": "flushed between steps (512 MB)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                   "parallelism": f"replicas x{world} (disjoint shot ranges)" if world > 1 else "1 GPU"},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "e2e": {"value": e2e_value, "unit": "shots/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(keys.nbytes)},

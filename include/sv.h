@@ -115,9 +115,15 @@ typedef enum {
                                device on every call, even when its graph is cached   */
     SV_OPT_PASS_PATH = 9,   /* 0: passes of <= 4 qubits run in registers, others in
                                shared-memory tiles; 1: shared-memory tiles only      */
-    SV_OPT_JOINT_KRAUS = 10 /* 1 (default): sv_run_circuit decides two back-to-back
+    SV_OPT_JOINT_KRAUS = 10, /* 1 (default): sv_run_circuit decides two back-to-back
                                one-qubit Kraus ops on different qubits from one pass
                                (joint probabilities ||K2_j K1_i psi||^2)             */
+    SV_OPT_SHOT_BASE = 11   /* global id of the batch's shot 0 (default 0): shot s
+                               draws its random numbers as shot shot_base + s, so
+                               disjoint shot ranges of one seed, run by separate
+                               processes or devices, merge into the histogram of
+                               one run over the union (shots are independent,
+                               Section IV-C).  Keys stay indexed by local shot. */
 } sv_option;
 
 /* Allocate a batch of n_shots shots of an n_qubits register.

@@ -97,6 +97,7 @@ struct DevBatch {
     int32_t n_slots;
     int32_t cap_br;            // branch ids per run (= shots)
     uint64_t seed;
+    uint64_t shot_base;        // global id of shot 0 (Philox counter offset)
     int32_t* ctl;              // control words, see CTL_*
     int32_t* br_slot;
     int32_t* br_start;

@@ -1283,7 +1283,7 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
 }
 
 __device__ __forceinline__ int draw_choice(const DevBatch& d, const DecideDesc& dd, uint32_t shot, const double* cum) {
-    const double u = philox_uniform(d.seed, shot, dd.op);
+    const double u = philox_uniform(d.seed, d.shot_base + shot, dd.op);
     const int sel = select_cum(u, cum, dd.R);
     if (dd.log_sel) dd.log_sel[shot] = sel;
     if (dd.log_thr) {
@@ -1520,7 +1520,7 @@ __global__ void __launch_bounds__(256) k_final_sample(DevBatch d, FinalDesc f) {
         if (pos < start || pos >= start + cnt) continue;  // stale entry (waiting shot)
         const int slot = d.br_slot[b];
         const uint32_t s = d.perm[pos];
-        const double u = philox_uniform(d.seed, s, f.op);
+        const double u = philox_uniform(d.seed, d.shot_base + s, f.op);
         const T* g = reinterpret_cast<const T*>(d.states) + (int64_t)slot * d.dim;
         double lo, hi;
         const int64_t key = svs::sample_warp<R>(g, d.dim, f.chunks,

@@ -899,8 +899,6 @@ uint64_t circuit_hash(sv_batch b, const sv_circuit* c) {
 // plain per-shot form: one state, one launch per op, host-side choices
 sv_status run_plain(sv_batch b, const sv_circuit* c) {
     sv_status st;
-    const int prec = 1;
-    (void)prec;
     std::vector<uint64_t> keys(b->n_shots);
     for (uint64_t shot = 0; shot < b->n_shots; ++shot) {
         Launch r;
@@ -927,7 +925,7 @@ sv_status run_plain(sv_batch b, const sv_circuit* c) {
                 if ((st = upload_pool(b))) return st;
                 if ((st = flush(b))) return st;
             } else if (kind == SV_OP_PAULI) {
-                const double u = host_uniform(b->seed, shot, (uint32_t)i);
+                const double u = host_uniform(b->seed, b->dev.shot_base + shot, (uint32_t)i);
                 const int t = host_select(u, d, c->n_terms[i]);
                 const char* str = (const char*)c->paulis + c->s_off[i] + t * k;
                 if (pauli_packed(str, k) & 0xff) {
@@ -985,7 +983,7 @@ sv_status run_plain(sv_batch b, const sv_circuit* c) {
                 std::vector<double> cum(R);
                 double acc = 0;
                 for (int t = 0; t < R; ++t) cum[t] = (acc += p[t]);
-                const double u = host_uniform(b->seed, shot, (uint32_t)i);
+                const double u = host_uniform(b->seed, b->dev.shot_base + shot, (uint32_t)i);
                 const int t = host_select(u, cum.data(), R);
                 const double scale = 1.0 / std::sqrt(p[t]);
                 if (kind == SV_OP_KRAUS) {
@@ -1259,6 +1257,12 @@ sv_status sv_set_option(sv_batch b, sv_option opt, int64_t v) {
     case SV_OPT_PASS_PATH:
         if (v < 0 || v > 1) return fail(SV_EINVAL, "pass path must be 0 (auto) or 1 (shared-memory tiles)");
         b->pass_path = (int)v;
+        return SV_OK;
+    case SV_OPT_SHOT_BASE:
+        if (v < 0) return fail(SV_EINVAL, "shot base must be >= 0");
+        if (!b->pend.empty()) return fail(SV_EINVAL, "per-op calls are in progress on this batch");
+        b->dev.shot_base = (uint64_t)v;
+        b->pool_gen += 1;  // kernels take the batch by value: cached graphs are stale
         return SV_OK;
     case SV_OPT_SLOT_LIMIT:
         if (v < 0) return fail(SV_EINVAL, "slot limit must be >= 0");

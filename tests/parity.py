@@ -42,8 +42,9 @@ def run_gpu(circ, seed, n_shots, mode, prec, use_graph=True, opts=None, want_amp
     return res
 
 
-def compare_shots(circ, seed, gpu, shots, prec, check_amps=True):
-    """Compare the GPU's logs of `shots` with the oracle.  Returns counts of
+def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0):
+    """Compare the GPU's logs of `shots` with the oracle.  Local shot s of the
+    GPU batch is the oracle's global shot base + s.  Returns counts of
     checked draws and flagged draws; raises AssertionError on an unexplained
     mismatch."""
     tol = TOL[prec]
@@ -53,7 +54,7 @@ def compare_shots(circ, seed, gpu, shots, prec, check_amps=True):
     n_draws = n_flag = 0
     for s in shots:
         overrides = {}
-        ref = O.run_shot(oc, seed, int(s))
+        ref = O.run_shot(oc, seed, base + int(s))
         for op in rops:
             g = int(gpu["sel"][op][s])
             c = int(ref["outcome"][op])
@@ -72,12 +73,12 @@ def compare_shots(circ, seed, gpu, shots, prec, check_amps=True):
                         f"(thr {ref['c_lo'][op]:.17g},{ref['c_hi'][op]:.17g}) u={u:.17g}")
             n_flag += 1
             overrides[op] = g
-            ref = O.run_shot(oc, seed, int(s), overrides=overrides)
+            ref = O.run_shot(oc, seed, base + int(s), overrides=overrides)
         fin = [op for op in rops if kinds[op] == W.FINAL]
         if fin:
             assert int(gpu["keys"][s]) == int(gpu["sel"][fin[0]][s])
         if check_amps and s in gpu.get("amps", {}):
-            st = O.run_shot(oc, seed, int(s), overrides=overrides, want_state=True)["state"]
+            st = O.run_shot(oc, seed, base + int(s), overrides=overrides, want_state=True)["state"]
             err = np.abs(gpu["amps"][s] - st).max()
             assert err <= tol["amp"], f"shot {s}: amplitude error {err:.3g} > {tol['amp']}"
     return n_draws, n_flag

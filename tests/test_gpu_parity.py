@@ -237,3 +237,38 @@ def test_alternating_circuits_on_one_batch_replay_correct_graphs():
         for c, k in ((sa, ka), (sb, kb), (sa, ka), (sa, ka), (sb, kb)):
             bt.run_circuit(c, use_graph=True)
             assert np.array_equal(bt.get_keys(), k)
+
+
+@pytest.mark.parametrize("base", [1000, (1 << 33) + 5])
+@pytest.mark.parametrize("mode", MODES)
+def test_shot_base_draws_global_shots(mode, base):
+    c = SMALL["midmeasure"]()
+    gpu = run_gpu(c, 9, 120, mode, sv.SV_C128, opts={sv.SV_OPT_SHOT_BASE: base}, want_amps=(0, 77))
+    compare_shots(c, 9, gpu, range(120), sv.SV_C128, base=base)
+
+
+def test_shot_base_plain_form():
+    c = W.random_su4(4, 3, 0.1, 0.1, seed=83)
+    gpu = run_gpu(c, 6, 30, sv.SV_PLAIN, sv.SV_C128, log=False, opts={sv.SV_OPT_SHOT_BASE: 500})
+    keys, _, _ = O.run_shots(c, 6, 500, 30, want_outcomes=False)
+    assert np.array_equal(gpu["keys"], keys)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_shot_ranges_concatenate_to_one_run(prec):
+    from paper_2308_03399_gb300 import replicas
+    c = W.random_su4(7, 4, 0.05, 0.1, seed=93)
+    whole = run_gpu(c, 3, 301, sv.SV_BRANCH, prec, log=False)["keys"]
+    parts = []
+    for r in range(3):
+        base, count = replicas.shard(301, 3, r)
+        parts.append(replicas.gpu_runner(prec=prec)(c, 3, base, count))
+    assert np.array_equal(np.concatenate(parts), whole)
+    # a cached graph must not keep the old base
+    cs = sv.circuit_struct(c.to_arrays())
+    with sv.Batch(7, 100, 1, prec, sv.SV_BRANCH, 3) as b:
+        b.run_circuit(cs)
+        assert np.array_equal(b.get_keys(), whole[:100])
+        b.set_option(sv.SV_OPT_SHOT_BASE, 201)
+        b.run_circuit(cs)
+        assert np.array_equal(b.get_keys(), whole[201:301])
