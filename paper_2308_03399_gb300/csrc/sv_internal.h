@@ -151,12 +151,13 @@ cudaError_t launch_init(const DevBatch& d, int prec, int n_init_slots, int grid,
 cudaError_t launch_reset(const DevBatch& d, int mode_branch, int n_shots_run, int from_wait, int grid,
                          cudaStream_t s);
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s);
-cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int grid, cudaStream_t s);
+cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int n_sm, cudaStream_t s);
 cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s);
 cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s);
 size_t pass_smem_bytes(int prec, const PassDesc& p, int threads);
 size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads);
 int pass_reg_blocks_per_sm(int prec, int wp, int paired, size_t smem);
+int pass_reg_threads(int prec);  // CTA size of the register path
 cudaError_t init_kernels();
 
 }  // namespace sv

@@ -907,8 +907,19 @@ __device__ __forceinline__ void reg_diag(const typename Cplx<R>::T* v, const Pas
     }
 }
 
+// CTA shape of the register path: complex64 at 128 threads and up to 96
+// registers (five CTAs, 20 warps per SM; the pass is latency-bound, so
+// resident warps matter more than a few spilled words); complex128 at 256
+// threads, where the same cap would spill kilobytes
+template <class R> struct RegCta;
+template <> struct RegCta<float> { static constexpr int threads = 128, min_blocks = 5; };
+template <> struct RegCta<double> { static constexpr int threads = 256, min_blocks = 1; };
+
+int pass_reg_threads(int prec) { return prec ? RegCta<double>::threads : RegCta<float>::threads; }
+
 template <class R, int WP, int PAIRED>
-__global__ void __launch_bounds__(256) k_pass_reg(DevBatch d, const __grid_constant__ PassDesc p) {
+__global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
+    k_pass_reg(DevBatch d, const __grid_constant__ PassDesc p) {
     using T = typename Cplx<R>::T;
     constexpr int G = 1 << WP;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1177,30 +1188,49 @@ __device__ void warp_probs(const DevBatch& d, const DecideDesc& dd, int b, int s
         __syncwarp();
         return;
     }
-    int src = slot, base_r = 0, stride_r = 1, inner = 1;
+    // The terms needed are the contiguous entries [base_r, base_r + R*inner)
+    // of every chunk's record: p_r = sum over chunks and j < inner of
+    // entry base_r + r*inner + j.  Each lane adds its chunks' entries in
+    // registers (all loads of a chunk issued together), the lanes' sums are
+    // combined by the fixed shuffle tree, and lane 0 adds the inner terms.
+    int src = slot, base_r = 0, inner = 1;
     if (dd.kind == DEC_KRAUS_J1) {
-        stride_r = dd.r2;  // p_i = sum over chunks and j of partial[i * r2 + j]
-        inner = dd.r2;
+        inner = dd.r2;  // p_i = sum over j of the joint p_ij = entry i * r2 + j
     } else if (dd.kind == DEC_KRAUS_J2) {
         // branches forked by the first op still find the joint partials in
         // their parent's slot
         const int cf = d.ctl[CTL_COPY_FIRST], ce = d.ctl[CTL_COPY_END];
         if (b >= cf && b < ce) src = d.br_slot[d.br_parent[b]];
-        base_r = d.br_sel[(int64_t)dd.pend_prev * d.cap_br + b] * R;  // p_ij = partial[i * R + j]
+        base_r = d.br_sel[(int64_t)dd.pend_prev * d.cap_br + b] * R;  // p_ij = entry i * R + j
     }
-    const double* pp = d.partials + (int64_t)src * d.max_chunks * MAX_RED;
-    for (int r = 0; r < R; ++r) {
-        double t = 0.0;
-        for (int c = lane; c < dd.chunks; c += 32)
-            for (int j = 0; j < inner; ++j) t += pp[(int64_t)c * MAX_RED + base_r + r * stride_r + j];
-        t = warp_sum(t);
-        if (lane == 0) p_out[r] = t;
+    const int nk = R * inner;
+    const double* pp = d.partials + (int64_t)src * d.max_chunks * MAX_RED + base_r;
+    double u[MAX_RED];
+#pragma unroll
+    for (int k = 0; k < MAX_RED; ++k) u[k] = 0.0;
+    for (int c = lane; c < dd.chunks; c += 32) {
+        const double* q = pp + (int64_t)c * MAX_RED;
+#pragma unroll
+        for (int k = 0; k < MAX_RED; ++k)
+            if (k < nk) u[k] += q[k];
     }
+#pragma unroll
+    for (int k = 0; k < MAX_RED; ++k)
+        if (k < nk) {
+            const double t = warp_sum(u[k]);
+            if (lane == 0) cum_out[k] = t;  // scratch until the caller forms the table
+        }
     __syncwarp();
-    if (dd.kind == DEC_KRAUS_J2 && lane == 0) {
+    if (lane == 0) {
         double pi = 0.0;
-        for (int r = 0; r < R; ++r) pi += p_out[r];
-        for (int r = 0; r < R; ++r) p_out[r] = p_out[r] / pi;
+        for (int r = 0; r < R; ++r) {
+            double t = 0.0;
+            for (int j = 0; j < inner; ++j) t += cum_out[r * inner + j];
+            p_out[r] = t;
+            pi += t;
+        }
+        if (dd.kind == DEC_KRAUS_J2)
+            for (int r = 0; r < R; ++r) p_out[r] = p_out[r] / pi;
     }
     __syncwarp();
 }
@@ -1293,80 +1323,140 @@ __device__ __forceinline__ int draw_choice(const DevBatch& d, const DecideDesc& 
     return sel;
 }
 
+// Branches of up to DEC_THREADS * DEC_SPT shots keep their shot ids and
+// choices in registers: one load of the branch's perm range, the draws, the
+// bin counts, and the partition written straight back into perm (every read
+// of the range has completed before the first write).  Larger branches
+// stream through perm_tmp.
+constexpr int DEC_SPT = 20;
+
 __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __grid_constant__ DecideDesc dd) {
     __shared__ double p_sh[MAX_TERMS], cum_sh[MAX_TERMS];
     __shared__ int bincnt[MAX_TERMS], binbase[MAX_TERMS], binrun[MAX_TERMS];
-    __shared__ int ng_sh;
+    __shared__ int ng_sh, nlist_sh;
+    __shared__ int list_sh[DEC_THREADS];
     const int n_br = d.ctl[CTL_NBR];
     const int R = dd.R;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
-    for (int b = blockIdx.x; b < n_br; b += gridDim.x) {
-        const int cnt = d.br_count[b];
-        if (cnt <= DEC_SMALL) continue;
-        const int slot = d.br_slot[b], start = d.br_start[b];
+    // this CTA's branches are blockIdx.x + j * gridDim.x; its threads look at
+    // nth of them at once and list the ones above DEC_SMALL shots
+    for (int64_t b0 = blockIdx.x; b0 < n_br; b0 += (int64_t)gridDim.x * nth) {
         __syncthreads();
-        if (warp == 0) warp_probs(d, dd, b, slot, p_sh, cum_sh);
-        if (tid < R) {
-            bincnt[tid] = 0;
-            binrun[tid] = 0;
+        if (tid == 0) nlist_sh = 0;
+        __syncthreads();
+        {
+            const int64_t bt = b0 + (int64_t)tid * gridDim.x;
+            if (bt < n_br && d.br_count[bt] > DEC_SMALL) list_sh[atomicAdd(&nlist_sh, 1)] = (int)bt;
         }
         __syncthreads();
-        if (tid == 0 && dd.kind != DEC_PAULI) {
-            double acc = 0.0;
-            for (int r = 0; r < R; ++r) cum_sh[r] = (acc += p_sh[r]);
-        }
-        __syncthreads();
-        for (int base = 0; base < cnt; base += nth) {  // warp-aggregated bin counts
-            const int i = base + tid;
-            int sel = -1;
-            if (i < cnt) {
-                sel = draw_choice(d, dd, d.perm[start + i], cum_sh);
-                d.shot_sel[start + i] = sel;
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, sel);
-            if (sel >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&bincnt[sel], __popc(peers));
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int ng = 0, acc = 0;
-            for (int r = 0; r < R; ++r)
-                if (bincnt[r] > 0) {
-                    binbase[r] = acc;
-                    acc += bincnt[r];
-                    ++ng;
+        const int nlist = nlist_sh;
+        for (int li = 0; li < nlist; ++li) {
+            const int b = list_sh[li];
+            const int cnt = d.br_count[b];
+            const int slot = d.br_slot[b], start = d.br_start[b];
+            const bool regs = cnt <= DEC_SPT * nth;
+            uint32_t sh[DEC_SPT];
+            int sl[DEC_SPT];
+            if (regs) {
+#pragma unroll
+                for (int k = 0; k < DEC_SPT; ++k) {
+                    const int i = tid + k * nth;
+                    sh[k] = i < cnt ? d.perm[start + i] : 0u;
                 }
-            ng_sh = ng;
-        }
-        __syncthreads();
-        if (ng_sh > 1 && dd.fork) {
-            // partition by outcome in one sweep: positions within a group come
-            // from warp-aggregated shared-memory counters, so the order of shots
-            // inside a group is not fixed (no result depends on it)
-            for (int base = 0; base < cnt; base += nth) {
-                const int i = base + tid;
-                const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
-                const unsigned peers = __match_any_sync(0xffffffffu, sel);
-                const int rank = __popc(peers & ((1u << lane) - 1u));
-                const int leader = __ffs(peers) - 1;
-                int pos = 0;
-                if (sel >= 0 && rank == 0) pos = atomicAdd(&binrun[sel], __popc(peers));
-                pos = __shfl_sync(0xffffffffu, pos, leader);
-                if (sel >= 0) d.perm_tmp[start + binbase[sel] + pos + rank] = d.perm[start + i];
             }
             __syncthreads();
-            for (int i = tid; i < cnt; i += nth) d.perm[start + i] = d.perm_tmp[start + i];
+            if (warp == 0) warp_probs(d, dd, b, slot, p_sh, cum_sh);
+            if (tid < R) {
+                bincnt[tid] = 0;
+                binrun[tid] = 0;
+            }
             __syncthreads();
+            if (tid == 0 && dd.kind != DEC_PAULI) {
+                double acc = 0.0;
+                for (int r = 0; r < R; ++r) cum_sh[r] = (acc += p_sh[r]);
+            }
+            __syncthreads();
+            if (regs) {
+#pragma unroll
+                for (int k = 0; k < DEC_SPT; ++k) {
+                    if (k * nth >= cnt) break;  // uniform over the block
+                    const int i = tid + k * nth;
+                    sl[k] = i < cnt ? draw_choice(d, dd, sh[k], cum_sh) : -1;
+                    const unsigned peers = __match_any_sync(0xffffffffu, sl[k]);
+                    if (sl[k] >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&bincnt[sl[k]], __popc(peers));
+                }
+            } else {
+                for (int base = 0; base < cnt; base += nth) {  // warp-aggregated bin counts
+                    const int i = base + tid;
+                    int sel = -1;
+                    if (i < cnt) {
+                        sel = draw_choice(d, dd, d.perm[start + i], cum_sh);
+                        d.shot_sel[start + i] = sel;
+                    }
+                    const unsigned peers = __match_any_sync(0xffffffffu, sel);
+                    if (sel >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&bincnt[sel], __popc(peers));
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int ng = 0, acc = 0;
+                for (int r = 0; r < R; ++r)
+                    if (bincnt[r] > 0) {
+                        binbase[r] = acc;
+                        acc += bincnt[r];
+                        ++ng;
+                    }
+                ng_sh = ng;
+            }
+            __syncthreads();
+            if (ng_sh > 1 && dd.fork) {
+                // partition by outcome in one sweep: positions within a group come
+                // from warp-aggregated shared-memory counters, so the order of shots
+                // inside a group is not fixed (no result depends on it)
+                if (regs) {
+#pragma unroll
+                    for (int k = 0; k < DEC_SPT; ++k) {
+                        if (k * nth >= cnt) break;
+                        const int sel = sl[k];
+                        const unsigned peers = __match_any_sync(0xffffffffu, sel);
+                        const int rank = __popc(peers & ((1u << lane) - 1u));
+                        const int leader = __ffs(peers) - 1;
+                        int pos = 0;
+                        if (sel >= 0 && rank == 0) pos = atomicAdd(&binrun[sel], __popc(peers));
+                        pos = __shfl_sync(0xffffffffu, pos, leader);
+                        if (sel >= 0) d.perm[start + binbase[sel] + pos + rank] = sh[k];
+                    }
+                } else {
+                    for (int base = 0; base < cnt; base += nth) {
+                        const int i = base + tid;
+                        const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
+                        const unsigned peers = __match_any_sync(0xffffffffu, sel);
+                        const int rank = __popc(peers & ((1u << lane) - 1u));
+                        const int leader = __ffs(peers) - 1;
+                        int pos = 0;
+                        if (sel >= 0 && rank == 0) pos = atomicAdd(&binrun[sel], __popc(peers));
+                        pos = __shfl_sync(0xffffffffu, pos, leader);
+                        if (sel >= 0) d.perm_tmp[start + binbase[sel] + pos + rank] = d.perm[start + i];
+                    }
+                    __syncthreads();
+                    for (int i = tid; i < cnt; i += nth) d.perm[start + i] = d.perm_tmp[start + i];
+                }
+                __syncthreads();
+            }
+            if (tid == 0) decide_groups(d, dd, b, start, bincnt, binbase, p_sh);
         }
-        if (tid == 0) decide_groups(d, dd, b, start, bincnt, binbase, p_sh);
     }
 }
 
 constexpr int DECS_WARPS = 8;
 
+// one warp per branch of at most DEC_SMALL (= 64) shots: two shots per lane,
+// held in registers from the first load to the in-place partition
 __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, const __grid_constant__ DecideDesc dd) {
     __shared__ double p_sh[DECS_WARPS][MAX_TERMS], cum_sh[DECS_WARPS][MAX_TERMS];
     __shared__ int bincnt[DECS_WARPS][MAX_TERMS], binbase[DECS_WARPS][MAX_TERMS], binrun[DECS_WARPS][MAX_TERMS];
+    static_assert(DEC_SMALL == 64, "two shots per lane");
     const int n_br = d.ctl[CTL_NBR];
     const int R = dd.R;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1380,6 +1470,9 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
         const int cnt = d.br_count[b];
         if (cnt > DEC_SMALL) continue;
         const int slot = d.br_slot[b], start = d.br_start[b];
+        uint32_t sh[2];
+        sh[0] = lane < cnt ? d.perm[start + lane] : 0u;
+        sh[1] = lane + 32 < cnt ? d.perm[start + lane + 32] : 0u;
         warp_probs(d, dd, b, slot, p, cum);
         for (int r = lane; r < R; r += 32) {
             bc[r] = 0;
@@ -1391,10 +1484,11 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
             for (int r = 0; r < R; ++r) cum[r] = (acc += p[r]);
         }
         __syncwarp();
-        for (int i = lane; i < cnt; i += 32) {
-            const int sel = draw_choice(d, dd, d.perm[start + i], cum);
-            d.shot_sel[start + i] = sel;
-            atomicAdd(&bc[sel], 1);
+        int sl[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            sl[k] = lane + 32 * k < cnt ? draw_choice(d, dd, sh[k], cum) : -1;
+            if (sl[k] >= 0) atomicAdd(&bc[sl[k]], 1);
         }
         __syncwarp();
         int ng = 0;
@@ -1410,18 +1504,16 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
         ng = __shfl_sync(0xffffffffu, ng, 0);
         __syncwarp();
         if (ng > 1 && dd.fork) {
-            for (int base = 0; base < cnt; base += 32) {
-                const int i = base + lane;
-                const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int sel = sl[k];
                 const unsigned peers = __match_any_sync(0xffffffffu, sel);
                 const int rank = __popc(peers & ((1u << lane) - 1u));
-                if (sel >= 0) d.perm_tmp[start + bb[sel] + br[sel] + rank] = d.perm[start + i];
+                if (sel >= 0) d.perm[start + bb[sel] + br[sel] + rank] = sh[k];
                 __syncwarp();
                 if (sel >= 0 && rank == 0) br[sel] += __popc(peers);
                 __syncwarp();
             }
-            for (int i = lane; i < cnt; i += 32) d.perm[start + i] = d.perm_tmp[start + i];
-            __syncwarp();
         }
         if (lane == 0) decide_groups(d, dd, b, start, bc, bb, p);
         __syncwarp();
@@ -1434,12 +1526,16 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
 // The forks of the last decide took ids [n_br, n_br + admitted) and their
 // slots; copy each parent state into its children's slots, then (last CTA
 // to finish) fold the new branches into the counts.
+constexpr int COPY_VPT = 4;
+
 __global__ void __launch_bounds__(256) k_copy(DevBatch d, int64_t state_vec16) {
     __shared__ int last;
     const int first = d.ctl[CTL_NBR];
     const int nalloc = d.ctl[CTL_NALLOC], n_free = d.ctl[CTL_NFREE];
     const int nb = nalloc < n_free ? nalloc : n_free;
-    const int64_t per_item = 4096;  // 16-byte words per work item (64 KB)
+    // work item = COPY_VPT * 256 16-byte words (16 KB); a thread issues all
+    // its loads before its stores
+    const int64_t per_item = COPY_VPT * 256;
     const int64_t items_per_state = (state_vec16 + per_item - 1) / per_item;
     const int64_t items = (int64_t)nb * items_per_state;
     const uint4* src_all = reinterpret_cast<const uint4*>(d.states);
@@ -1450,9 +1546,14 @@ __global__ void __launch_bounds__(256) k_copy(DevBatch d, int64_t state_vec16) {
         const int src_slot = d.br_slot[d.br_parent[id]], dst_slot = d.br_slot[id];
         const uint4* src = src_all + (int64_t)src_slot * state_vec16;
         uint4* dst = dst_all + (int64_t)dst_slot * state_vec16;
-        const int64_t lo = c * per_item;
-        const int64_t hi = (lo + per_item < state_vec16) ? lo + per_item : state_vec16;
-        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) dst[i] = src[i];
+        const int64_t lo = c * per_item + threadIdx.x;
+        uint4 v[COPY_VPT];
+#pragma unroll
+        for (int k = 0; k < COPY_VPT; ++k)
+            if (lo + 256 * k < state_vec16) v[k] = src[lo + 256 * k];
+#pragma unroll
+        for (int k = 0; k < COPY_VPT; ++k)
+            if (lo + 256 * k < state_vec16) dst[lo + 256 * k] = v[k];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1626,7 +1727,8 @@ const void* pass_reg_fn(int prec, int wp, int paired) {
 
 int pass_reg_blocks_per_sm(int prec, int wp, int paired, size_t smem) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pass_reg_fn(prec, wp, paired), 256, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pass_reg_fn(prec, wp, paired), pass_reg_threads(prec),
+                                                      smem) != cudaSuccess) {
         cudaGetLastError();
         n = 1;
     }
@@ -1642,10 +1744,11 @@ size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads) {
 
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s) {
     if (p.reg_wp > 0) {
-        const size_t smem = pass_reg_smem_bytes(prec, p, 256);
+        const int threads = pass_reg_threads(prec);
+        const size_t smem = pass_reg_smem_bytes(prec, p, threads);
         const void* f = pass_reg_fn(prec, p.reg_wp, p.reg_paired && !prec);
         void* args[] = {(void*)&d, (void*)&p};
-        return cudaLaunchKernel(f, dim3(grid), dim3(256), args, smem, s);
+        return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
     }
     const size_t smem = pass_smem_bytes(prec, p, threads);
     if (prec) k_pass<double><<<grid, threads, smem, s>>>(d, p);
@@ -1653,12 +1756,24 @@ cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int thre
     return cudaGetLastError();
 }
 
-cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int grid, cudaStream_t s) {
+static int resident_blocks(const void* fn, int threads) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int n_sm, cudaStream_t s) {
     // small branches first: a branch the big kernel partitions may end up
-    // with DEC_SMALL shots or fewer and must not be decided twice.  The small
-    // kernel is latency-bound: one warp per branch, in one wave
-    k_decide_small<<<8 * grid, DECS_WARPS * 32, 0, s>>>(d, dd);
-    k_decide_big<<<grid, DEC_THREADS, 0, s>>>(d, dd);
+    // with DEC_SMALL shots or fewer and must not be decided twice.  Both
+    // kernels are latency-bound and grid-stride over the branches, so each
+    // launches exactly one resident wave
+    static const int small_per_sm = resident_blocks((const void*)k_decide_small, DECS_WARPS * 32);
+    static const int big_per_sm = resident_blocks((const void*)k_decide_big, DEC_THREADS);
+    k_decide_small<<<small_per_sm * n_sm, DECS_WARPS * 32, 0, s>>>(d, dd);
+    k_decide_big<<<big_per_sm * n_sm, DEC_THREADS, 0, s>>>(d, dd);
     return cudaGetLastError();
 }
 
@@ -1672,11 +1787,11 @@ cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s) {
 
 cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s) {
     if (prec) {
-        k_final_partials<double><<<grid, 256, 0, s>>>(d, f);
+        k_final_partials<double><<<4 * grid, 256, 0, s>>>(d, f);  // HBM-bound: 8 CTAs per SM
         k_final_cum<<<grid, 256, 0, s>>>(d, f);
         k_final_sample<double><<<grid, 256, 0, s>>>(d, f);
     } else {
-        k_final_partials<float><<<grid, 256, 0, s>>>(d, f);
+        k_final_partials<float><<<4 * grid, 256, 0, s>>>(d, f);  // HBM-bound: 8 CTAs per SM
         k_final_cum<<<grid, 256, 0, s>>>(d, f);
         k_final_sample<float><<<grid, 256, 0, s>>>(d, f);
     }

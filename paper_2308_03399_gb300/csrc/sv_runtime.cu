@@ -196,7 +196,7 @@ int pass_grid(sv_batch b, const PassDesc& p) {
     if (b->grid_pass > 0) return b->grid_pass;
     if (p.reg_wp > 0) {
         const int prec = b->prec == SV_C128;
-        const size_t smem = pass_reg_smem_bytes(prec, p, 256);
+        const size_t smem = pass_reg_smem_bytes(prec, p, pass_reg_threads(prec));
         const int key = (p.reg_wp * 2 + prec) * 2 + p.reg_paired;
         auto it = b->reg_occ.find(key * 4096 + (int)(smem / 64));
         int per_sm;
@@ -221,7 +221,7 @@ cudaError_t exec_one(sv_batch b, const Launch& L) {
     case L_INIT: return launch_init(b->dev, prec, L.a0, b->n_sm * 4, b->stream);
     case L_RESET: return launch_reset(b->dev, L.a0, L.a1, L.a2, b->n_sm * 2, b->stream);
     case L_PASS: return launch_pass(b->dev, prec, L.pass, b->threads, pass_grid(b, L.pass), b->stream);
-    case L_DECIDE: return launch_decide(b->dev, L.dec, b->grid_small, b->stream);
+    case L_DECIDE: return launch_decide(b->dev, L.dec, b->n_sm, b->stream);
     case L_ALLOC: return cudaSuccess;
     case L_COPY: return launch_copy(b->dev, prec, b->n_sm * 4, b->stream);
     case L_FINAL: return launch_final(b->dev, prec, L.fin, b->grid_small, b->stream);

@@ -42,9 +42,17 @@ template <> struct Sum<float> {  // float-float pair, Knuth TwoSum
 template <class R>
 __device__ __forceinline__ double chunk_sum(const typename Cx<R>::T* g, int64_t L, double* sh32) {
     Sum<R> a;
-    for (int64_t j = threadIdx.x; j < L; j += blockDim.x) {
-        const typename Cx<R>::T v = g[j];
-        a.add(v.x * v.x + v.y * v.y);
+    // a thread adds j = tid, tid + blockDim, ... in increasing order; the
+    // loads of eight consecutive terms are issued before their adds
+    const int64_t bd = blockDim.x;
+    for (int64_t j0 = threadIdx.x; j0 < L; j0 += 8 * bd) {
+        typename Cx<R>::T v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (j0 + k * bd < L) v[k] = g[j0 + k * bd];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (j0 + k * bd < L) a.add(v[k].x * v[k].x + v[k].y * v[k].y);
     }
     double x = a.get();
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
