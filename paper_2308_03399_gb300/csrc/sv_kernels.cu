@@ -301,6 +301,32 @@ __device__ __forceinline__ void acc_add(double* a, double x) { *a += x; }
 __device__ __forceinline__ double acc_get(float2 a) { return (double)a.x + (double)a.y; }
 __device__ __forceinline__ double acc_get(double a) { return a; }
 
+// Fixed-order combination of the 32 lanes' accumulators (result in lane 0).
+// Float-float pairs are added as pairs (Knuth's TwoSum of the high parts,
+// the low parts folded into the error, then Dekker's Fast2Sum to
+// renormalise), so complex64 reductions stay on the FP32 pipe until the
+// one conversion of the total.
+__device__ __forceinline__ double warp_combine(float2 a) {
+    float hi = a.x, lo = a.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_down_sync(0xffffffffu, hi, o);
+        const float bl = __shfl_down_sync(0xffffffffu, lo, o);
+        const float s = __fadd_rn(hi, bh);
+        const float bp = __fsub_rn(s, hi);
+        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(bh, bp));
+        e = __fadd_rn(e, __fadd_rn(lo, bl));
+        hi = __fadd_rn(s, e);
+        lo = __fsub_rn(e, __fsub_rn(hi, s));
+    }
+    return (double)hi + (double)lo;
+}
+__device__ __forceinline__ double warp_combine(double a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    return a;
+}
+
 // shared-memory layout of k_pass: ring buffers | matrices | accumulators |
 // run offsets | mbarriers
 __host__ __device__ inline size_t pass_bytes_before_bars(const PassDesc& p, int threads, size_t amp) {
@@ -342,27 +368,30 @@ __device__ __noinline__ void reduce_forms(const typename Cplx<R>::T* tile, int t
 
 // measurement probabilities of the 2^K outcomes of the measured qubits
 // (Section IV-A-5): bin r collects |psi_j|^2 of indices whose measured bits
-// spell r
+// spell r.  Warp w owns bins w, w + nwarps, ...; lane l adds the bin's
+// amplitudes of groups l, l + 32, ... in index order into its accumulator
+// acc[r * 32 + l], so a chunk's bin is one fixed-order warp combination.
 template <class R, int K>
 __device__ __noinline__ void reduce_bins(const typename Cplx<R>::T* tile, int tb, const int32_t* pos,
                                          typename AccSlot<R>::T* acc) {
     using T = typename Cplx<R>::T;
     constexpr int D = 1 << K;
-    const GroupIdx<K> gi(pos);
+    int sp[K];
+    sorted_pos<K>(pos, sp);
     const int groups = 1 << (tb - K);
-    typename AccSlot<R>::T a[D];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = warp; r < D; r += nw) {
+        int off = 0;
 #pragma unroll
-    for (int r = 0; r < D; ++r) a[r] = acc[r * blockDim.x + threadIdx.x];
-    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-        const int base = insert_zeros<K>(g, gi.sp);
-#pragma unroll
-        for (int r = 0; r < D; ++r) {
-            const T v = tile[base | gi.off[r]];
-            acc_add(&a[r], v.x * v.x + v.y * v.y);
+        for (int j = 0; j < K; ++j)
+            if ((r >> j) & 1) off |= 1 << pos[j];
+        typename AccSlot<R>::T a = acc[r * 32 + lane];
+        for (int g = lane; g < groups; g += 32) {
+            const T v = tile[insert_zeros<K>(g, sp) | off];
+            acc_add(&a, v.x * v.x + v.y * v.y);
         }
+        acc[r * 32 + lane] = a;
     }
-#pragma unroll
-    for (int r = 0; r < D; ++r) acc[r * blockDim.x + threadIdx.x] = a[r];
 }
 
 template <class R>
@@ -586,8 +615,12 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
             __syncthreads();
             cur_b = b;
         }
-        if (red && i % tpc == 0)
-            for (int r = 0; r < p.red_R; ++r) acc[r * blockDim.x + threadIdx.x] = A{};
+        if (red && i % tpc == 0) {
+            if (p.red_kind == RED_BINS)
+                for (int r = warp; r < p.red_R; r += (int)(blockDim.x >> 5)) acc[r * 32 + lane] = A{};
+            else
+                for (int r = 0; r < p.red_R; ++r) acc[r * blockDim.x + threadIdx.x] = A{};
+        }
         if (!mbar_wait(d, &bars[s], (uint32_t)((k / PASS_NBUF) & 1))) ok = false;
         T* tile = bufs + (size_t)s * tsize;
         for (int st_i = 0; st_i < p.n_stages; ++st_i) {
@@ -609,18 +642,27 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
             bulk_commit();
         }
         if (red && i % tpc == tpc - 1) {
-            // fixed-order combination: lanes by shuffles, warps in order
             const int slot = d.br_slot[b];
-            for (int r = 0; r < p.red_R; ++r) {
-                double v = acc_get(acc[r * blockDim.x + threadIdx.x]);
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                if (lane == 0) wsum[warp][r] = v;
-            }
-            __syncthreads();
-            if (threadIdx.x < p.red_R && slot >= 0 && slot < d.n_slots) {
-                double v = 0.0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += wsum[w][threadIdx.x];
-                d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED + threadIdx.x] = v;
+            const bool slot_ok = slot >= 0 && slot < d.n_slots;
+            double* part = d.partials + ((int64_t)(slot_ok ? slot : 0) * d.max_chunks + c) * MAX_RED;
+            if (p.red_kind == RED_BINS) {
+                // each bin lives in one warp: one fixed-order warp combination
+                for (int r = warp; r < p.red_R; r += (int)(blockDim.x >> 5)) {
+                    const double v = warp_combine(acc[r * 32 + lane]);
+                    if (lane == 0 && slot_ok) part[r] = v;
+                }
+            } else {
+                // fixed-order combination: lanes by shuffles, warps in order
+                for (int r = 0; r < p.red_R; ++r) {
+                    const double v = warp_combine(acc[r * blockDim.x + threadIdx.x]);
+                    if (lane == 0) wsum[warp][r] = v;
+                }
+                __syncthreads();
+                if (threadIdx.x < p.red_R && slot_ok) {
+                    double v = 0.0;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += wsum[w][threadIdx.x];
+                    part[threadIdx.x] = v;
+                }
             }
         }
     }
@@ -789,6 +831,18 @@ __device__ __forceinline__ void reg_flip_dyn(T* v, int j) {
     case 2: if constexpr (G > 4) reg_flip<T, G, 2>(v); break;
     default: if constexpr (G > 8) reg_flip<T, G, 3>(v); break;
     }
+}
+
+// v[e] <- v[e ^ x] for a group-bit mask x
+template <class T, int G>
+__device__ __forceinline__ void reg_xor_mask(T* v, int x) {
+    if (x & 1) reg_flip<T, G, 0>(v);
+    if constexpr (G > 2)
+        if (x & 2) reg_flip<T, G, 1>(v);
+    if constexpr (G > 4)
+        if (x & 4) reg_flip<T, G, 2>(v);
+    if constexpr (G > 8)
+        if (x & 8) reg_flip<T, G, 3>(v);
 }
 
 template <class T, int G>
@@ -982,9 +1036,37 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                     }
                 }
                 if (sk) skipmask |= 1ull << s;
+                // Pauli and projection stages in group form, once per branch:
+                // Pauli: bits 0-3 flip mask, bit 4 the (-i) factor, bits 8+
+                // the sign of each group element; projection: bits 0-15 the
+                // kept elements, bits 16-19 the flips of a reset
+                int info = packed;
+                if (!sk && st.kind == ST_PAULI_BR) {
+                    const int xm = packed & 15, zm = (packed >> 4) & 15, ny = (packed >> 8) & 3;
+                    int xg = 0, zg = 0;
+                    for (int j = 0; j < st.k; ++j) {
+                        if ((xm >> j) & 1) xg |= 1 << st.pos[j];
+                        if ((zm >> j) & 1) zg |= 1 << st.pos[j];
+                    }
+                    int sign = 0;
+                    for (int e = 0; e < G; ++e)
+                        if ((((ny >> 1) & 1) ^ (__popc(zg & e) & 1)) != 0) sign |= 1 << e;
+                    info = xg | ((ny & 1) << 4) | (sign << 8);
+                } else if (!sk && st.kind == ST_PROJ_BR) {
+                    int keep = 0, xr = 0;
+                    for (int e = 0; e < G; ++e) {
+                        int o = 0;
+                        for (int j = 0; j < st.k; ++j) o |= ((e >> st.pos[j]) & 1) << j;
+                        if (o == sel) keep |= 1 << e;
+                    }
+                    if (st.reset)
+                        for (int j = 0; j < st.k; ++j)
+                            if ((sel >> j) & 1) xr |= 1 << st.pos[j];
+                    info = keep | (xr << 16);
+                }
                 if (lane == 0) {
                     w_sel[s] = sel;
-                    w_packed[s] = packed;
+                    w_packed[s] = info;
                 }
                 if (!sk && (st.kind == ST_DENSE || st.kind == ST_DENSE_BR)) {
                     const int D2 = 1 << (2 * st.k);
@@ -1089,37 +1171,31 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                             reg_apply2_dyn<T, G>(v, st.pos[0], st.pos[1], mats + st.mat);
                     }
                 } else if (st.kind == ST_PAULI_BR) {
-                    const int packed = w_packed[s];
-                    int zg = 0;
-                    for (int j = 0; j < st.k; ++j) {
-                        if ((packed >> j) & 1) reg_flip_dyn<T, G>(v, st.pos[j]);
-                        if ((packed >> (4 + j)) & 1) zg |= 1 << st.pos[j];
-                    }
-                    const int ny = (packed >> 8) & 3;
+                    // out[e] = (-i)^ny (-1)^popcount(z & e) in[e ^ x]
+                    const int info = w_packed[s];
+                    reg_xor_mask<T, G>(v, info & 15);
+                    const bool rot = (info >> 4) & 1;
+                    const int sign = info >> 8;
 #pragma unroll
                     for (int e = 0; e < G; ++e) {
-                        // (-i)^ny, then the sign of the destination index
                         T t = v[e];
-                        if (ny & 1) {
+                        if (rot) {
                             const R x = t.x;
                             t.x = t.y;
                             t.y = -x;
                         }
-                        const bool neg = ((ny >> 1) & 1) ^ (__popc(zg & e) & 1);
-                        if (neg) {
+                        if ((sign >> e) & 1) {
                             t.x = -t.x;
                             t.y = -t.y;
                         }
                         v[e] = t;
                     }
                 } else {  // ST_PROJ_BR
-                    const int sel = w_sel[s];
+                    const int info = w_packed[s];
                     const R sc = mats[st.mat].x;
 #pragma unroll
                     for (int e = 0; e < G; ++e) {
-                        int o = 0;
-                        for (int j = 0; j < st.k; ++j) o |= ((e >> st.pos[j]) & 1) << j;
-                        if (o == sel) {
+                        if ((info >> e) & 1) {
                             v[e].x *= sc;
                             v[e].y *= sc;
                         } else {
@@ -1127,9 +1203,7 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                             v[e].y = 0;
                         }
                     }
-                    if (st.reset)
-                        for (int j = 0; j < st.k; ++j)
-                            if ((sel >> j) & 1) reg_flip_dyn<T, G>(v, st.pos[j]);
+                    reg_xor_mask<T, G>(v, (info >> 16) & 15);
                 }
             }
             if (p.red_kind == RED_FORMS)
@@ -1151,6 +1225,8 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
 #pragma unroll
             for (int r = 0; r < REG_MAX_RED; ++r) {
                 if (r >= p.red_R) break;
+                // a unit is short: a float64 shuffle tree costs less here
+                // than float-float pairs
                 double x = acc[r].get();
                 for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
                 if (lane == 0) d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED + r] = x;

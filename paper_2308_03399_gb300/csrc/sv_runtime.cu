@@ -109,6 +109,7 @@ struct sv_batch_s {
     size_t amp_bytes = 8, state_bytes = 0;
     int n_slots = 0;
     int tb = 11, chunks = 1, chunks_final = 1;
+    int red_chunks = 1;  // chunk records written by the last pass with a reduction
     int threads = 256, grid_pass = 0, grid_small = 0, n_sm = 0;
     int max_active = 8, max_stages = MAX_STAGES;  // max_active is set in sv_alloc_batch
     bool branch = false;
@@ -396,14 +397,20 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
     p.n_nontile = 0;
     for (int q = 0; q < b->n; ++q)
         if (std::find(tq.begin(), tq.end(), q) == tq.end()) p.nontile_q[p.n_nontile++] = q;
-    p.chunks = b->chunks;
     p.reg_wp = wp;
     if (wp > 0) {
+        p.chunks = b->chunks;
         p.tiles_per_chunk = 1;
     } else {
+        // tile path: a chunk spans at least eight tiles (or the whole
+        // state), so the fixed-order combination of its reduction is paid
+        // once per several tiles
         const int64_t tiles = 1ll << (b->n - p.tb);
-        p.tiles_per_chunk = (int)(tiles / b->chunks);
+        const int64_t tpc = std::max<int64_t>(tiles / b->chunks, std::min<int64_t>(tiles, 8));
+        p.chunks = (int)(tiles / tpc);
+        p.tiles_per_chunk = (int)tpc;
     }
+    if (red.kind != RED_NONE) b->red_chunks = p.chunks;
     int mat = 0;
     p.n_stages = (int)b->pend.size();
     for (int s = 0; s < p.n_stages; ++s) {
@@ -530,7 +537,7 @@ sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cu
     d.kind = kind;
     d.R = R;
     d.pend = pend;
-    d.chunks = b->chunks;
+    d.chunks = b->red_chunks;  // the pass just emitted wrote these
     d.fork = b->branch;
     d.m = m;
     d.r2 = r2;
@@ -963,18 +970,18 @@ sv_status run_plain(sv_batch b, const sv_circuit* c) {
                     }
                     if ((st = upload_pool(b))) return st;
                     if ((st = emit_pass(b, red))) return st;
-                    std::vector<double> part(MAX_RED * b->chunks);
-                    CU(cudaMemcpyAsync(part.data(), b->dev.partials, sizeof(double) * MAX_RED * b->chunks,
+                    std::vector<double> part(MAX_RED * b->red_chunks);
+                    CU(cudaMemcpyAsync(part.data(), b->dev.partials, sizeof(double) * MAX_RED * b->red_chunks,
                                        cudaMemcpyDeviceToHost, b->stream));
                     CU(cudaStreamSynchronize(b->stream));
                     if (kind == SV_OP_KRAUS) {
                         double s = 0;
-                        for (int ch = 0; ch < b->chunks; ++ch) s += part[ch * MAX_RED];
+                        for (int ch = 0; ch < b->red_chunks; ++ch) s += part[ch * MAX_RED];
                         p[t] = s;
                     } else {
                         for (int o = 0; o < R; ++o) {
                             double s = 0;
-                            for (int ch = 0; ch < b->chunks; ++ch) s += part[ch * MAX_RED + o];
+                            for (int ch = 0; ch < b->red_chunks; ++ch) s += part[ch * MAX_RED + o];
                             p[o] = s;
                         }
                         break;
