@@ -75,7 +75,6 @@ struct DecideDesc {
     int32_t m;                 // measured qubits
     int32_t clbit[MAX_STAGE_Q];
     int32_t r2;                // joint Kraus: terms of the second op (partials stride)
-    int32_t npend;             // pending-choice columns in use (copied to forks)
     int32_t pend_prev;         // DEC_KRAUS_J2: pending column of the first op's choice
     int32_t* log_sel;          // per shot id, nullable
     double* log_thr;           // 2 per shot id, nullable
@@ -109,12 +108,6 @@ struct DevBatch {
     uint32_t* perm;            // shot ids, grouped by branch
     uint32_t* perm_tmp;
     int32_t* shot_sel;         // per perm position
-    int32_t* grp_n;            // per branch: groups after the last decide
-    int32_t* grp_sel;          // [cap_br][MAX_TERMS]
-    int32_t* grp_start;
-    int32_t* grp_cnt;
-    double* grp_scale;
-    uint64_t* grp_clbits;
     int32_t* free_slots;
     uint32_t* wait_shots;
     double* partials;          // [n_slots][max_chunks][MAX_RED]

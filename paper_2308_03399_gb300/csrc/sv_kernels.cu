@@ -97,7 +97,7 @@ template <> struct Acc<float> {
 // multiplies with the published multipliers and Weyl key increments.
 // key = (seed lo, seed hi), counter = (shot lo, shot hi, op, 0).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, uint32_t op) {
+__device__ __forceinline__ uint64_t philox_k53(uint64_t seed, uint64_t shot, uint32_t op) {
     uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
     uint32_t w0 = (uint32_t)shot, w1 = (uint32_t)(shot >> 32), w2 = op, w3 = 0u;
 #pragma unroll
@@ -113,14 +113,25 @@ __device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, u
         key0 += 0x9E3779B9u;
         key1 += 0xBB67AE85u;
     }
-    const uint64_t top53 = ((((uint64_t)w0) << 32) | (uint64_t)w1) >> 11;
-    return (double)top53 * 0x1.0p-53;
+    return ((((uint64_t)w0) << 32) | (uint64_t)w1) >> 11;  // top 53 bits of words 0, 1
 }
 
-// first t with u < cum[t]; past the end, the last t with nonzero probability
-__device__ __forceinline__ int select_cum(double u, const double* cum, int R) {
+// the uniform draw u = k * 2^-53 in [0, 1)
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, uint32_t op) {
+    return (double)philox_k53(seed, shot, op) * 0x1.0p-53;
+}
+
+// Selection in the integer domain: for u = k * 2^-53, u < c exactly when
+// k < ceil(c * 2^53) (the scaling by 2^53 is exact), so a branch turns its
+// cumulative table into integer thresholds once and each shot compares
+// integers.  Past the last threshold (a table summing to just under 1) the
+// choice is the last term with nonzero probability.
+__device__ __forceinline__ uint64_t cum_threshold(double c) {
+    return c > 0.0 ? __double2ull_ru(c * 0x1.0p53) : 0ull;
+}
+__device__ __forceinline__ int select_k(uint64_t k, const uint64_t* thr, const double* cum, int R) {
     for (int t = 0; t < R; ++t)
-        if (u < cum[t]) return t;
+        if (k < thr[t]) return t;
     for (int t = R - 1; t >= 0; --t) {
         const double prev = t ? cum[t - 1] : 0.0;
         if (cum[t] > prev) return t;
@@ -1311,70 +1322,88 @@ __device__ void warp_probs(const DevBatch& d, const DecideDesc& dd, int b, int s
     __syncwarp();
 }
 
-// group records of branch b (one thread): outcome, 1/sqrt(p) in float64,
-// classical bits; the branch itself keeps the smallest outcome
+// Groups of branch b after a decide, built by one whole warp: the outcomes
+// with shots, in outcome order.  The branch keeps the first (smallest
+// outcome); with shot-branching every other group becomes a new branch
+// (Section IV-B-2: a state forks where its shots' outcomes differ) or, with
+// no free slot left, parks its shots on the waiting list.  One atomic on the
+// allocation counter reserves the ids of all of the branch's new branches,
+// and each group's lane writes its own branch, so a fork costs the same
+// whatever the number of groups.  Which branch gets which id depends on
+// timing, but no result does: a branch's arithmetic never depends on its id
+// or slot.  k_copy folds the counters into the branch count.
 __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, int start, const int* bincnt,
                               const int* binbase, const double* p) {
+    const int lane = threadIdx.x & 31;
+    const int R = dd.R;
+    // group index of outcomes lane and lane + 32 (-1: no shots)
+    int gidx[2] = {-1, -1};
     int g = 0;
-    int64_t g0 = (int64_t)b * MAX_TERMS;
-    for (int r = 0; r < dd.R; ++r) {
-        if (bincnt[r] == 0) continue;
-        const int64_t gi = g0 + g;
-        const double scale = dd.kind == DEC_PAULI ? 1.0 : 1.0 / sqrt(p[r]);
-        uint64_t cl = d.br_clbits[b];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int r = lane + 32 * h;
+        const bool nz = r < R && bincnt[r] > 0;
+        const unsigned m = __ballot_sync(0xffffffffu, nz);
+        if (nz) gidx[h] = g + __popc(m & ((1u << lane) - 1u));
+        g += __popc(m);
+    }
+    const unsigned f0 = __ballot_sync(0xffffffffu, gidx[0] == 0), f1 = __ballot_sync(0xffffffffu, gidx[1] == 0);
+    const int r0 = f0 ? __ffs(f0) - 1 : 32 + __ffs(f1) - 1;
+    const uint64_t cl_parent = d.br_clbits[b];
+    auto scale_of = [&](int r) { return dd.kind == DEC_PAULI ? 1.0 : 1.0 / sqrt(p[r]); };
+    auto clbits_of = [&](int r) {
+        uint64_t cl = cl_parent;
         if (dd.kind == DEC_MEASURE)
             for (int j = 0; j < dd.m; ++j) {
                 const uint64_t bit = (uint64_t)((r >> j) & 1);
                 cl = (cl & ~(1ull << dd.clbit[j])) | (bit << dd.clbit[j]);
             }
-        d.grp_sel[gi] = r;
-        d.grp_start[gi] = start + binbase[r];
-        d.grp_cnt[gi] = bincnt[r];
-        d.grp_scale[gi] = scale;
-        d.grp_clbits[gi] = cl;
-        ++g;
-    }
-    d.grp_n[b] = g;
-    d.br_sel[(int64_t)dd.pend * d.cap_br + b] = d.grp_sel[g0];
-    d.br_scale[(int64_t)dd.pend * d.cap_br + b] = d.grp_scale[g0];
-    d.br_clbits[b] = d.grp_clbits[g0];
-    if (g > 1 && !dd.fork) set_err(d, ERR_GROUPS, b);
-    if (g <= 1 || !dd.fork) return;
-    // Fork (Section IV-B-2): the smallest outcome keeps this branch; every
-    // other group takes the next branch id and the next free slot, or parks
-    // its shots on the waiting list when no slot is left.  Ids and slots come
-    // from atomic counters, so which branch gets which id depends on timing,
-    // but no result does: a branch's arithmetic never depends on its id or
-    // slot.  k_copy folds the counters into the branch count.
-    const int n_br0 = d.ctl[CTL_NBR], n_free = d.ctl[CTL_NFREE];
-    if (d.fork_log) {
-        const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
-        if (e < d.fork_log_cap) {
-            int64_t* ev = d.fork_log + 5 * (int64_t)e;
-            ev[0] = dd.op; ev[1] = b; ev[2] = b; ev[3] = d.grp_sel[g0]; ev[4] = d.grp_cnt[g0];
+        return cl;
+    };
+    const bool forks = g > 1 && dd.fork;
+    int j0 = 0;
+    if (lane == 0) {
+        d.br_sel[(int64_t)dd.pend * d.cap_br + b] = r0;
+        d.br_scale[(int64_t)dd.pend * d.cap_br + b] = scale_of(r0);
+        d.br_clbits[b] = clbits_of(r0);
+        if (g > 1 && !dd.fork) set_err(d, ERR_GROUPS, b);
+        if (forks) {
+            j0 = atomicAdd(&d.ctl[CTL_NALLOC], g - 1);
+            d.br_count[b] = bincnt[r0];
+            if (d.fork_log) {
+                const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
+                if (e < d.fork_log_cap) {
+                    int64_t* ev = d.fork_log + 5 * (int64_t)e;
+                    ev[0] = dd.op; ev[1] = b; ev[2] = b; ev[3] = r0; ev[4] = bincnt[r0];
+                }
+            }
         }
     }
-    d.br_count[b] = d.grp_cnt[g0];
-    for (int gi = 1; gi < g; ++gi) {
-        const int64_t gx = g0 + gi;
-        const int j = atomicAdd(&d.ctl[CTL_NALLOC], 1);
+    if (!forks) return;
+    j0 = __shfl_sync(0xffffffffu, j0, 0);
+    const int n_br0 = d.ctl[CTL_NBR], n_free = d.ctl[CTL_NFREE];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int gi = gidx[h];
+        if (gi < 1) continue;
+        const int r = lane + 32 * h;
+        const int j = j0 + gi - 1;
+        const int cnt = bincnt[r], st = start + binbase[r];
         int child = -1;
         if (j < n_free) {
             child = n_br0 + j;
             d.br_slot[child] = d.free_slots[n_free - 1 - j];
-            d.br_start[child] = d.grp_start[gx];
-            d.br_count[child] = d.grp_cnt[gx];
-            d.br_clbits[child] = d.grp_clbits[gx];
+            d.br_start[child] = st;
+            d.br_count[child] = cnt;
+            d.br_clbits[child] = clbits_of(r);
             d.br_parent[child] = b;
-            d.grp_n[child] = 1;
-            for (int q = 0; q < dd.npend; ++q) {
+            for (int q = 0; q < dd.pend; ++q) {  // earlier pending choices of the parent
                 d.br_sel[(int64_t)q * d.cap_br + child] = d.br_sel[(int64_t)q * d.cap_br + b];
                 d.br_scale[(int64_t)q * d.cap_br + child] = d.br_scale[(int64_t)q * d.cap_br + b];
             }
-            d.br_sel[(int64_t)dd.pend * d.cap_br + child] = d.grp_sel[gx];
-            d.br_scale[(int64_t)dd.pend * d.cap_br + child] = d.grp_scale[gx];
+            d.br_sel[(int64_t)dd.pend * d.cap_br + child] = r;
+            d.br_scale[(int64_t)dd.pend * d.cap_br + child] = scale_of(r);
         } else {
-            const int cnt = d.grp_cnt[gx], st = d.grp_start[gx];
             const int w = atomicAdd(&d.ctl[CTL_NWAIT], cnt);
             for (int i = 0; i < cnt; ++i) d.wait_shots[w + i] = d.perm[st + i];
         }
@@ -1382,15 +1411,15 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
             const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
             if (e < d.fork_log_cap) {
                 int64_t* ev = d.fork_log + 5 * (int64_t)e;
-                ev[0] = dd.op; ev[1] = b; ev[2] = child; ev[3] = d.grp_sel[gx]; ev[4] = d.grp_cnt[gx];
+                ev[0] = dd.op; ev[1] = b; ev[2] = child; ev[3] = r; ev[4] = cnt;
             }
         }
     }
 }
 
-__device__ __forceinline__ int draw_choice(const DevBatch& d, const DecideDesc& dd, uint32_t shot, const double* cum) {
-    const double u = philox_uniform(d.seed, d.shot_base + shot, dd.op);
-    const int sel = select_cum(u, cum, dd.R);
+__device__ __forceinline__ int draw_choice(const DevBatch& d, const DecideDesc& dd, uint32_t shot, const double* cum,
+                                           const uint64_t* thr) {
+    const int sel = select_k(philox_k53(d.seed, d.shot_base + shot, dd.op), thr, cum, dd.R);
     if (dd.log_sel) dd.log_sel[shot] = sel;
     if (dd.log_thr) {
         dd.log_thr[2 * (int64_t)shot] = sel ? cum[sel - 1] : 0.0;
@@ -1399,18 +1428,25 @@ __device__ __forceinline__ int draw_choice(const DevBatch& d, const DecideDesc& 
     return sel;
 }
 
-// Branches of up to DEC_THREADS * DEC_SPT shots keep their shot ids and
-// choices in registers: one load of the branch's perm range, the draws, the
-// bin counts, and the partition written straight back into perm (every read
-// of the range has completed before the first write).  Larger branches
-// stream through perm_tmp.
+// Branches of up to DEC_THREADS * DEC_SPT shots are staged in shared
+// memory: one load of the branch's perm range (all loads of a thread in
+// flight together), the draws and bin counts, and the partition written
+// straight back into perm (every read of the range has completed before the
+// first write).  The loops over the staged shots are not unrolled: they run
+// once per launch, on an SM whose instruction cache the pass kernels have
+// just filled.  Larger branches stream through perm_tmp.
 constexpr int DEC_SPT = 20;
+constexpr size_t DEC_BIG_SMEM = (size_t)DEC_SPT * DEC_THREADS * (sizeof(uint32_t) + sizeof(uint8_t));
 
 __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __grid_constant__ DecideDesc dd) {
     __shared__ double p_sh[MAX_TERMS], cum_sh[MAX_TERMS];
+    __shared__ uint64_t thr_sh[MAX_TERMS];
     __shared__ int bincnt[MAX_TERMS], binbase[MAX_TERMS], binrun[MAX_TERMS];
     __shared__ int ng_sh, nlist_sh;
     __shared__ int list_sh[DEC_THREADS];
+    extern __shared__ __align__(16) unsigned char dec_smem[];
+    uint32_t* sm_shot = reinterpret_cast<uint32_t*>(dec_smem);
+    uint8_t* sm_sel = reinterpret_cast<uint8_t*>(sm_shot + DEC_SPT * DEC_THREADS);
     const int n_br = d.ctl[CTL_NBR];
     const int R = dd.R;
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -1431,14 +1467,13 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
             const int b = list_sh[li];
             const int cnt = d.br_count[b];
             const int slot = d.br_slot[b], start = d.br_start[b];
-            const bool regs = cnt <= DEC_SPT * nth;
-            uint32_t sh[DEC_SPT];
-            int sl[DEC_SPT];
-            if (regs) {
+            const bool onchip = cnt <= DEC_SPT * nth;
+            const int nk = (cnt + nth - 1) / nth;
+            if (onchip) {
 #pragma unroll
                 for (int k = 0; k < DEC_SPT; ++k) {
                     const int i = tid + k * nth;
-                    sh[k] = i < cnt ? d.perm[start + i] : 0u;
+                    sm_shot[k * nth + tid] = i < cnt ? d.perm[start + i] : 0u;
                 }
             }
             __syncthreads();
@@ -1453,21 +1488,27 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
                 for (int r = 0; r < R; ++r) cum_sh[r] = (acc += p_sh[r]);
             }
             __syncthreads();
-            if (regs) {
-#pragma unroll
-                for (int k = 0; k < DEC_SPT; ++k) {
-                    if (k * nth >= cnt) break;  // uniform over the block
+            for (int r = tid; r < R; r += nth) thr_sh[r] = cum_threshold(cum_sh[r]);
+            __syncthreads();
+            if (onchip) {
+#pragma unroll 1
+                for (int k = 0; k < nk; ++k) {
                     const int i = tid + k * nth;
-                    sl[k] = i < cnt ? draw_choice(d, dd, sh[k], cum_sh) : -1;
-                    const unsigned peers = __match_any_sync(0xffffffffu, sl[k]);
-                    if (sl[k] >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&bincnt[sl[k]], __popc(peers));
+                    int sel = -1;
+                    if (i < cnt) {
+                        sel = draw_choice(d, dd, sm_shot[k * nth + tid], cum_sh, thr_sh);
+                        sm_sel[k * nth + tid] = (uint8_t)sel;
+                    }
+                    const unsigned peers = __match_any_sync(0xffffffffu, sel);
+                    if (sel >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&bincnt[sel], __popc(peers));
                 }
             } else {
+#pragma unroll 1
                 for (int base = 0; base < cnt; base += nth) {  // warp-aggregated bin counts
                     const int i = base + tid;
                     int sel = -1;
                     if (i < cnt) {
-                        sel = draw_choice(d, dd, d.perm[start + i], cum_sh);
+                        sel = draw_choice(d, dd, d.perm[start + i], cum_sh, thr_sh);
                         d.shot_sel[start + i] = sel;
                     }
                     const unsigned peers = __match_any_sync(0xffffffffu, sel);
@@ -1490,20 +1531,21 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
                 // partition by outcome in one sweep: positions within a group come
                 // from warp-aggregated shared-memory counters, so the order of shots
                 // inside a group is not fixed (no result depends on it)
-                if (regs) {
-#pragma unroll
-                    for (int k = 0; k < DEC_SPT; ++k) {
-                        if (k * nth >= cnt) break;
-                        const int sel = sl[k];
+                if (onchip) {
+#pragma unroll 1
+                    for (int k = 0; k < nk; ++k) {
+                        const int i = tid + k * nth;
+                        const int sel = i < cnt ? (int)sm_sel[k * nth + tid] : -1;
                         const unsigned peers = __match_any_sync(0xffffffffu, sel);
                         const int rank = __popc(peers & ((1u << lane) - 1u));
                         const int leader = __ffs(peers) - 1;
                         int pos = 0;
                         if (sel >= 0 && rank == 0) pos = atomicAdd(&binrun[sel], __popc(peers));
                         pos = __shfl_sync(0xffffffffu, pos, leader);
-                        if (sel >= 0) d.perm[start + binbase[sel] + pos + rank] = sh[k];
+                        if (sel >= 0) d.perm[start + binbase[sel] + pos + rank] = sm_shot[k * nth + tid];
                     }
                 } else {
+#pragma unroll 1
                     for (int base = 0; base < cnt; base += nth) {
                         const int i = base + tid;
                         const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
@@ -1520,7 +1562,7 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
                 }
                 __syncthreads();
             }
-            if (tid == 0) decide_groups(d, dd, b, start, bincnt, binbase, p_sh);
+            if (warp == 0) decide_groups(d, dd, b, start, bincnt, binbase, p_sh);
         }
     }
 }
@@ -1531,6 +1573,7 @@ constexpr int DECS_WARPS = 8;
 // held in registers from the first load to the in-place partition
 __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, const __grid_constant__ DecideDesc dd) {
     __shared__ double p_sh[DECS_WARPS][MAX_TERMS], cum_sh[DECS_WARPS][MAX_TERMS];
+    __shared__ uint64_t thr_sh[DECS_WARPS][MAX_TERMS];
     __shared__ int bincnt[DECS_WARPS][MAX_TERMS], binbase[DECS_WARPS][MAX_TERMS], binrun[DECS_WARPS][MAX_TERMS];
     static_assert(DEC_SMALL == 64, "two shots per lane");
     const int n_br = d.ctl[CTL_NBR];
@@ -1538,6 +1581,7 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double* p = p_sh[warp];
     double* cum = cum_sh[warp];
+    uint64_t* thr = thr_sh[warp];
     int* bc = bincnt[warp];
     int* bb = binbase[warp];
     int* br = binrun[warp];
@@ -1560,10 +1604,12 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
             for (int r = 0; r < R; ++r) cum[r] = (acc += p[r]);
         }
         __syncwarp();
+        for (int r = lane; r < R; r += 32) thr[r] = cum_threshold(cum[r]);
+        __syncwarp();
         int sl[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            sl[k] = lane + 32 * k < cnt ? draw_choice(d, dd, sh[k], cum) : -1;
+            sl[k] = lane + 32 * k < cnt ? draw_choice(d, dd, sh[k], cum, thr) : -1;
             if (sl[k] >= 0) atomicAdd(&bc[sl[k]], 1);
         }
         __syncwarp();
@@ -1591,7 +1637,7 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
                 __syncwarp();
             }
         }
-        if (lane == 0) decide_groups(d, dd, b, start, bc, bb, p);
+        decide_groups(d, dd, b, start, bc, bb, p);
         __syncwarp();
     }
 }
@@ -1741,7 +1787,6 @@ __global__ void __launch_bounds__(256) k_reset(DevBatch d, int branch_mode, int 
         d.br_count[b] = branch_mode ? n_run : 1;
         d.br_clbits[b] = 0;
         d.br_parent[b] = -1;
-        d.grp_n[b] = 1;
         for (int q = 0; q < MAX_PEND; ++q) {
             d.br_sel[(int64_t)q * d.cap_br + b] = 0;
             d.br_scale[(int64_t)q * d.cap_br + b] = 1.0;
@@ -1771,6 +1816,8 @@ cudaError_t init_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_decide_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DEC_BIG_SMEM);
     return e;
 }
 
@@ -1832,9 +1879,9 @@ cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int thre
     return cudaGetLastError();
 }
 
-static int resident_blocks(const void* fn, int threads) {
+static int resident_blocks(const void* fn, int threads, size_t smem = 0) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         n = 1;
     }
@@ -1847,9 +1894,9 @@ cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int n_sm, cud
     // kernels are latency-bound and grid-stride over the branches, so each
     // launches exactly one resident wave
     static const int small_per_sm = resident_blocks((const void*)k_decide_small, DECS_WARPS * 32);
-    static const int big_per_sm = resident_blocks((const void*)k_decide_big, DEC_THREADS);
+    static const int big_per_sm = resident_blocks((const void*)k_decide_big, DEC_THREADS, DEC_BIG_SMEM);
     k_decide_small<<<small_per_sm * n_sm, DECS_WARPS * 32, 0, s>>>(d, dd);
-    k_decide_big<<<big_per_sm * n_sm, DEC_THREADS, 0, s>>>(d, dd);
+    k_decide_big<<<big_per_sm * n_sm, DEC_THREADS, DEC_BIG_SMEM, s>>>(d, dd);
     return cudaGetLastError();
 }
 

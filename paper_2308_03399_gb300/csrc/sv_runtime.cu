@@ -542,7 +542,6 @@ sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cu
     d.m = m;
     d.r2 = r2;
     d.pend_prev = pend_prev;
-    d.npend = pend + 1;
     for (int j = 0; j < m; ++j) d.clbit[j] = clbits[j];
     if (cum)
         for (int t = 0; t < R; ++t) d.cum[t] = cum[t];
@@ -1139,7 +1138,7 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
     cudaMemGetInfo(&free_b, &total_b);
     const int max_chunks = std::max(b->chunks, b->chunks_final);
     const size_t per_slot = b->state_bytes + (size_t)max_chunks * MAX_RED * 8;
-    const size_t per_shot = 4 * 8 + MAX_PEND * 12 + (size_t)MAX_TERMS * 32 + 64;
+    const size_t per_shot = 4 * 8 + MAX_PEND * 12 + 64;
     const size_t fixed = per_shot * n_shots + (64ull << 20);
     size_t budget = mem_budget;
     if (budget == 0) {
@@ -1179,9 +1178,6 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
         (st = dalloc(b, &d.br_count, S)) || (st = dalloc(b, &d.br_clbits, S)) || (st = dalloc(b, &d.br_parent, S)) ||
         (st = dalloc(b, &d.br_sel, S * MAX_PEND)) || (st = dalloc(b, &d.br_scale, S * MAX_PEND)) ||
         (st = dalloc(b, &d.perm, S)) || (st = dalloc(b, &d.perm_tmp, S)) || (st = dalloc(b, &d.shot_sel, S)) ||
-        (st = dalloc(b, &d.grp_n, S)) || (st = dalloc(b, &d.grp_sel, S * MAX_TERMS)) ||
-        (st = dalloc(b, &d.grp_start, S * MAX_TERMS)) || (st = dalloc(b, &d.grp_cnt, S * MAX_TERMS)) ||
-        (st = dalloc(b, &d.grp_scale, S * MAX_TERMS)) || (st = dalloc(b, &d.grp_clbits, S * MAX_TERMS)) ||
         (st = dalloc(b, &d.free_slots, b->n_slots)) || (st = dalloc(b, &d.wait_shots, S)) ||
 
         (st = dalloc(b, &d.partials, (size_t)b->n_slots * max_chunks * MAX_RED)) || (st = dalloc(b, &d.keys, S)) ||
