@@ -12,6 +12,7 @@ constexpr int MAX_TILE_BITS = 12;  // amplitudes of one CTA tile <= 2^12
 constexpr int MAX_STAGES = 40;     // ops fused into one pass
 constexpr int MAX_PEND = 16;       // random ops whose per-branch choice is applied in one pass
 constexpr int MAX_TERMS = 64;      // terms of one random op (Pauli strings)
+constexpr int64_t REG_UNIT_MIN_AMPS = 8192;  // smallest register-path unit
 constexpr int MAX_RED = 16;        // probabilities reduced by one pass (Kraus terms, 2^m outcomes)
 constexpr int MAX_CHUNKS = 1024;   // reduction partials per state
 constexpr int MAX_STAGE_Q = 4;     // qubits of one stage

@@ -399,7 +399,11 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
         if (std::find(tq.begin(), tq.end(), q) == tq.end()) p.nontile_q[p.n_nontile++] = q;
     p.reg_wp = wp;
     if (wp > 0) {
-        p.chunks = b->chunks;
+        // register path: a warp's unit holds at least REG_UNIT_MIN_AMPS
+        // amplitudes, so the fixed-order combination of its reduction is
+        // paid once per several hundred groups
+        const int64_t unit = std::max<int64_t>(b->dim / b->chunks, REG_UNIT_MIN_AMPS);
+        p.chunks = (int)std::max<int64_t>(1, b->dim / unit);
         p.tiles_per_chunk = 1;
     } else {
         // tile path: a chunk spans at least eight tiles (or the whole
