@@ -118,12 +118,15 @@ typedef enum {
     SV_OPT_JOINT_KRAUS = 10, /* 1 (default): sv_run_circuit decides two back-to-back
                                one-qubit Kraus ops on different qubits from one pass
                                (joint probabilities ||K2_j K1_i psi||^2)             */
-    SV_OPT_SHOT_BASE = 11   /* global id of the batch's shot 0 (default 0): shot s
+    SV_OPT_SHOT_BASE = 11,  /* global id of the batch's shot 0 (default 0): shot s
                                draws its random numbers as shot shot_base + s, so
                                disjoint shot ranges of one seed, run by separate
                                processes or devices, merge into the histogram of
                                one run over the union (shots are independent,
                                Section IV-C).  Keys stay indexed by local shot. */
+    SV_OPT_CHAIN_DECIDES = 12 /* 1 (default): sv_run_circuit decides, in one launch,
+                               an op and the ops after it that need no new pass
+                               (the second op of a joint Kraus pair, Pauli ops) */
 } sv_option;
 
 /* Allocate a batch of n_shots shots of an n_qubits register.

@@ -66,6 +66,22 @@ struct PassDesc {
     Stage st[MAX_STAGES];
 };
 
+// An op decided in the same launch as the decide's head op, after it in
+// program order, with no pass between: the second op of a joint Kraus pair
+// (DEC_KRAUS_J2, probabilities conditional on the head's choice, from the
+// same reduction) or a Pauli op (state-independent table).
+constexpr int MAX_TAIL = 3;
+constexpr int MAX_TAIL_TERMS = 64;
+struct DecideTail {
+    uint32_t op;
+    int32_t kind;              // DEC_KRAUS_J2 (right after a DEC_KRAUS_J1 head) or DEC_PAULI
+    int32_t R;
+    int32_t pend;
+    int32_t cum_off;           // DEC_PAULI: offset of its table in tail_cum / tail_thr
+    int32_t* log_sel;
+    double* log_thr;
+};
+
 struct DecideDesc {
     uint32_t op;
     int32_t kind;              // DEC_*
@@ -80,6 +96,13 @@ struct DecideDesc {
     int32_t* log_sel;          // per shot id, nullable
     double* log_thr;           // 2 per shot id, nullable
     double cum[MAX_TERMS];     // Pauli cumulative table
+    // chain: ops decided after the head in the same launch; a shot's outcome
+    // is the tuple (head, tail[0], ...), numbered in mixed radix, nk in all
+    int32_t n_tail;
+    int32_t nk;                // R times the tail's R (<= MAX_TERMS)
+    DecideTail tail[MAX_TAIL];
+    double tail_cum[MAX_TAIL_TERMS];
+    uint64_t tail_thr[MAX_TAIL_TERMS];  // ceil(cum * 2^53), see cum_threshold
 };
 
 struct FinalDesc {

@@ -1248,23 +1248,37 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
 
 // ---------------------------------------------------------------------------
 // k_decide: per branch, probabilities (fixed-order float64 sums of the
-// partials), one Philox draw per shot, the shot's choice, and a stable
-// partition of the branch's shots by choice.  Branches with more than
-// DEC_SMALL shots take a whole CTA (k_decide_big); the others one warp
+// partials), one Philox draw per shot and op, the shot's outcome, and a
+// partition of the branch's shots by outcome.  A decide may carry a chain
+// (DecideDesc::tail): the ops after the head that need no pass in between.
+// A shot then draws every op of the chain in program order, each from its
+// own counter (shot, op), and its outcome is the tuple.  Branches with more
+// than DEC_SMALL shots take a whole CTA (k_decide_big); the others one warp
 // (k_decide_small).
 // ---------------------------------------------------------------------------
 constexpr int DEC_THREADS = 512;
 constexpr int DEC_SMALL = 64;
 
-// probabilities of branch b into p_out (and, for Pauli, the table into
-// cum_out); one whole warp: lanes read chunks lane, lane+32, ... and the
-// per-lane sums are combined by a fixed shuffle tree (deterministic)
 __device__ __forceinline__ double warp_sum(double x) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
 }
 
-__device__ void warp_probs(const DevBatch& d, const DecideDesc& dd, int b, int slot, double* p_out, double* cum_out) {
+// per-branch tables of one decide (shared memory: one per warp or per CTA)
+struct DecTab {
+    double p[MAX_TERMS], cum[MAX_TERMS];  // head op: probabilities, running sums
+    uint64_t thr[MAX_TERMS];              // head op: integer thresholds
+    double jp[MAX_RED], jcum[MAX_RED];    // chained DEC_KRAUS_J2: p(j | i), row i at i * R2
+    uint64_t jthr[MAX_RED];
+    int bincnt[MAX_TERMS], binbase[MAX_TERMS], binrun[MAX_TERMS];
+    int leaf[MAX_TERMS];                  // fork log: branch of each outcome tuple
+};
+
+// probabilities of branch b into p_out (and, for Pauli, the table into
+// cum_out); one whole warp.  With joint_out (a DEC_KRAUS_J1 head), the
+// joint probabilities p_ij are kept there too.
+__device__ void warp_probs(const DevBatch& d, const DecideDesc& dd, int b, int slot, double* p_out, double* cum_out,
+                           double* joint_out) {
     const int lane = threadIdx.x & 31;
     const int R = dd.R;
     if (dd.kind == DEC_PAULI) {
@@ -1309,6 +1323,8 @@ __device__ void warp_probs(const DevBatch& d, const DecideDesc& dd, int b, int s
         }
     __syncwarp();
     if (lane == 0) {
+        if (joint_out)
+            for (int k = 0; k < nk; ++k) joint_out[k] = cum_out[k];
         double pi = 0.0;
         for (int r = 0; r < R; ++r) {
             double t = 0.0;
@@ -1322,27 +1338,168 @@ __device__ void warp_probs(const DevBatch& d, const DecideDesc& dd, int b, int s
     __syncwarp();
 }
 
-// Groups of branch b after a decide, built by one whole warp: the outcomes
-// with shots, in outcome order.  The branch keeps the first (smallest
-// outcome); with shot-branching every other group becomes a new branch
-// (Section IV-B-2: a state forks where its shots' outcomes differ) or, with
-// no free slot left, parks its shots on the waiting list.  One atomic on the
-// allocation counter reserves the ids of all of the branch's new branches,
-// and each group's lane writes its own branch, so a fork costs the same
-// whatever the number of groups.  Which branch gets which id depends on
-// timing, but no result does: a branch's arithmetic never depends on its id
-// or slot.  k_copy folds the counters into the branch count.
-__device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, int start, const int* bincnt,
-                              const int* binbase, const double* p) {
+__device__ __forceinline__ bool chained_j2(const DecideDesc& dd) {
+    return dd.n_tail > 0 && dd.tail[0].kind == DEC_KRAUS_J2;
+}
+
+// the branch's tables (one warp): head probabilities, running sums and
+// thresholds; for a chained DEC_KRAUS_J2, the conditional tables
+// p(j | i) = p_ij / sum_j p_ij of every head outcome i (the arithmetic of a
+// separate DEC_KRAUS_J2 decide, row by row)
+__device__ void branch_tables(const DevBatch& d, const DecideDesc& dd, int b, int slot, DecTab& T) {
     const int lane = threadIdx.x & 31;
-    const int R = dd.R;
-    // group index of outcomes lane and lane + 32 (-1: no shots)
+    const bool j2 = chained_j2(dd);
+    warp_probs(d, dd, b, slot, T.p, T.cum, j2 ? T.jp : nullptr);
+    if (lane == 0) {
+        if (dd.kind != DEC_PAULI) {
+            double acc = 0.0;
+            for (int r = 0; r < dd.R; ++r) T.cum[r] = (acc += T.p[r]);
+        }
+        if (j2) {
+            const int R2 = dd.tail[0].R;
+            for (int i = 0; i < dd.R; ++i) {
+                double* row = T.jp + i * R2;
+                double pi = 0.0;
+                for (int j = 0; j < R2; ++j) pi += row[j];
+                double acc = 0.0;
+                for (int j = 0; j < R2; ++j) {
+                    row[j] = row[j] / pi;
+                    T.jcum[i * R2 + j] = (acc += row[j]);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    for (int r = lane; r < dd.R; r += 32) T.thr[r] = cum_threshold(T.cum[r]);
+    if (j2)
+        for (int k = lane; k < dd.R * dd.tail[0].R; k += 32) T.jthr[k] = cum_threshold(T.jcum[k]);
+    __syncwarp();
+}
+
+__device__ __forceinline__ void log_choice(int32_t* log_sel, double* log_thr, uint32_t shot, int sel,
+                                           const double* cum) {
+    if (log_sel) log_sel[shot] = sel;
+    if (log_thr) {
+        log_thr[2 * (int64_t)shot] = sel ? cum[sel - 1] : 0.0;
+        log_thr[2 * (int64_t)shot + 1] = cum[sel];
+    }
+}
+
+// a shot's outcome tuple over the chain, as a mixed-radix number
+__device__ __forceinline__ int chain_draw(const DevBatch& d, const DecideDesc& dd, const DecTab& T, uint32_t shot) {
+    const uint64_t gs = d.shot_base + shot;
+    int o = select_k(philox_k53(d.seed, gs, dd.op), T.thr, T.cum, dd.R);
+    log_choice(dd.log_sel, dd.log_thr, shot, o, T.cum);
+    int key = o;
+    for (int t = 0; t < dd.n_tail; ++t) {
+        const DecideTail& tl = dd.tail[t];
+        const double* cum;
+        const uint64_t* thr;
+        if (tl.kind == DEC_KRAUS_J2) {  // only right after the head: o is the head's outcome
+            cum = T.jcum + o * tl.R;
+            thr = T.jthr + o * tl.R;
+        } else {
+            cum = dd.tail_cum + tl.cum_off;
+            thr = dd.tail_thr + tl.cum_off;
+        }
+        o = select_k(philox_k53(d.seed, gs, tl.op), thr, cum, tl.R);
+        log_choice(tl.log_sel, tl.log_thr, shot, o, cum);
+        key = key * tl.R + o;
+    }
+    return key;
+}
+
+// per-op choices and scales of outcome tuple `key` into branch `leaf`'s
+// pending columns; returns the head outcome
+__device__ int write_choices(const DevBatch& d, const DecideDesc& dd, const DecTab& T, int leaf, int key) {
+    int outc[1 + MAX_TAIL];
+    int rest = key;
+    for (int t = dd.n_tail - 1; t >= 0; --t) {
+        outc[1 + t] = rest % dd.tail[t].R;
+        rest /= dd.tail[t].R;
+    }
+    outc[0] = rest;
+    const int oh = outc[0];
+    d.br_sel[(int64_t)dd.pend * d.cap_br + leaf] = oh;
+    d.br_scale[(int64_t)dd.pend * d.cap_br + leaf] = dd.kind == DEC_PAULI ? 1.0 : 1.0 / sqrt(T.p[oh]);
+    for (int t = 0; t < dd.n_tail; ++t) {
+        const DecideTail& tl = dd.tail[t];
+        const int o = outc[1 + t];
+        d.br_sel[(int64_t)tl.pend * d.cap_br + leaf] = o;
+        d.br_scale[(int64_t)tl.pend * d.cap_br + leaf] =
+            tl.kind == DEC_KRAUS_J2 ? 1.0 / sqrt(T.jp[oh * tl.R + o]) : 1.0;
+    }
+    return oh;
+}
+
+// fork events of one branch's decide, per op of the chain (one thread): at
+// each op, every node (shots sharing the earlier ops' outcomes) whose shots
+// take two or more outcomes logs one event per outcome: (op, node's branch,
+// the outcome's branch, outcome, shots).  A node's branch is that of its
+// first outcome tuple, so the events are those of deciding the ops one at a
+// time.
+__device__ void log_fork_events(const DevBatch& d, const DecideDesc& dd, const DecTab& T) {
+    const int M = 1 + dd.n_tail;
+    int stride = dd.nk;
+    for (int m = 0; m < M; ++m) {
+        const int Rm = m == 0 ? dd.R : dd.tail[m - 1].R;
+        const uint32_t op = m == 0 ? dd.op : dd.tail[m - 1].op;
+        const int node = stride;  // keys per node at this level
+        stride /= Rm;             // keys per outcome of this op within a node
+        for (int n0 = 0; n0 < dd.nk; n0 += node) {
+            int distinct = 0, first = -1;
+            for (int o = 0; o < Rm; ++o) {
+                int c = 0, f = -1;
+                for (int k = n0 + o * stride; k < n0 + (o + 1) * stride; ++k)
+                    if (T.bincnt[k] > 0) {
+                        c += T.bincnt[k];
+                        if (f < 0) f = k;
+                    }
+                if (c > 0) {
+                    ++distinct;
+                    if (first < 0) first = f;
+                }
+            }
+            if (distinct < 2) continue;
+            const int parent = T.leaf[first];
+            for (int o = 0; o < Rm; ++o) {
+                int c = 0, f = -1;
+                for (int k = n0 + o * stride; k < n0 + (o + 1) * stride; ++k)
+                    if (T.bincnt[k] > 0) {
+                        c += T.bincnt[k];
+                        if (f < 0) f = k;
+                    }
+                if (c == 0) continue;
+                const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
+                if (e < d.fork_log_cap) {
+                    int64_t* ev = d.fork_log + 5 * (int64_t)e;
+                    ev[0] = op; ev[1] = parent; ev[2] = T.leaf[f]; ev[3] = o; ev[4] = c;
+                }
+            }
+        }
+    }
+}
+
+// Groups of branch b after a decide, built by one whole warp: the outcome
+// tuples with shots, in tuple order.  The branch keeps the first; with
+// shot-branching every other group becomes a new branch (Section IV-B-2: a
+// state forks where its shots' outcomes differ) or, with no free slot left,
+// parks its shots on the waiting list.  One atomic on the allocation counter
+// reserves the ids of all of the branch's new branches, and each group's
+// lane writes its own branch, so a fork costs the same whatever the number
+// of groups.  Which branch gets which id depends on timing, but no result
+// does: a branch's arithmetic never depends on its id or slot.  k_copy folds
+// the counters into the branch count.
+__device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, int start, DecTab& T) {
+    const int lane = threadIdx.x & 31;
+    const int NK = dd.nk;
+    // group index of tuples lane and lane + 32 (-1: no shots)
     int gidx[2] = {-1, -1};
     int g = 0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int r = lane + 32 * h;
-        const bool nz = r < R && bincnt[r] > 0;
+        const bool nz = r < NK && T.bincnt[r] > 0;
         const unsigned m = __ballot_sync(0xffffffffu, nz);
         if (nz) gidx[h] = g + __popc(m & ((1u << lane) - 1u));
         g += __popc(m);
@@ -1350,33 +1507,28 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
     const unsigned f0 = __ballot_sync(0xffffffffu, gidx[0] == 0), f1 = __ballot_sync(0xffffffffu, gidx[1] == 0);
     const int r0 = f0 ? __ffs(f0) - 1 : 32 + __ffs(f1) - 1;
     const uint64_t cl_parent = d.br_clbits[b];
-    auto scale_of = [&](int r) { return dd.kind == DEC_PAULI ? 1.0 : 1.0 / sqrt(p[r]); };
-    auto clbits_of = [&](int r) {
+    const int tail_prod = NK / dd.R;
+    auto clbits_of = [&](int key) {
         uint64_t cl = cl_parent;
-        if (dd.kind == DEC_MEASURE)
+        if (dd.kind == DEC_MEASURE) {
+            const int oh = key / tail_prod;
             for (int j = 0; j < dd.m; ++j) {
-                const uint64_t bit = (uint64_t)((r >> j) & 1);
+                const uint64_t bit = (uint64_t)((oh >> j) & 1);
                 cl = (cl & ~(1ull << dd.clbit[j])) | (bit << dd.clbit[j]);
             }
+        }
         return cl;
     };
     const bool forks = g > 1 && dd.fork;
     int j0 = 0;
     if (lane == 0) {
-        d.br_sel[(int64_t)dd.pend * d.cap_br + b] = r0;
-        d.br_scale[(int64_t)dd.pend * d.cap_br + b] = scale_of(r0);
+        write_choices(d, dd, T, b, r0);
         d.br_clbits[b] = clbits_of(r0);
         if (g > 1 && !dd.fork) set_err(d, ERR_GROUPS, b);
         if (forks) {
             j0 = atomicAdd(&d.ctl[CTL_NALLOC], g - 1);
-            d.br_count[b] = bincnt[r0];
-            if (d.fork_log) {
-                const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
-                if (e < d.fork_log_cap) {
-                    int64_t* ev = d.fork_log + 5 * (int64_t)e;
-                    ev[0] = dd.op; ev[1] = b; ev[2] = b; ev[3] = r0; ev[4] = bincnt[r0];
-                }
-            }
+            d.br_count[b] = T.bincnt[r0];
+            if (d.fork_log) T.leaf[r0] = b;
         }
     }
     if (!forks) return;
@@ -1388,7 +1540,7 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
         if (gi < 1) continue;
         const int r = lane + 32 * h;
         const int j = j0 + gi - 1;
-        const int cnt = bincnt[r], st = start + binbase[r];
+        const int cnt = T.bincnt[r], st = start + T.binbase[r];
         int child = -1;
         if (j < n_free) {
             child = n_br0 + j;
@@ -1401,31 +1553,18 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
                 d.br_sel[(int64_t)q * d.cap_br + child] = d.br_sel[(int64_t)q * d.cap_br + b];
                 d.br_scale[(int64_t)q * d.cap_br + child] = d.br_scale[(int64_t)q * d.cap_br + b];
             }
-            d.br_sel[(int64_t)dd.pend * d.cap_br + child] = r;
-            d.br_scale[(int64_t)dd.pend * d.cap_br + child] = scale_of(r);
+            write_choices(d, dd, T, child, r);
         } else {
             const int w = atomicAdd(&d.ctl[CTL_NWAIT], cnt);
             for (int i = 0; i < cnt; ++i) d.wait_shots[w + i] = d.perm[st + i];
         }
-        if (d.fork_log) {
-            const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
-            if (e < d.fork_log_cap) {
-                int64_t* ev = d.fork_log + 5 * (int64_t)e;
-                ev[0] = dd.op; ev[1] = b; ev[2] = child; ev[3] = r; ev[4] = cnt;
-            }
-        }
+        if (d.fork_log) T.leaf[r] = child;
     }
-}
-
-__device__ __forceinline__ int draw_choice(const DevBatch& d, const DecideDesc& dd, uint32_t shot, const double* cum,
-                                           const uint64_t* thr) {
-    const int sel = select_k(philox_k53(d.seed, d.shot_base + shot, dd.op), thr, cum, dd.R);
-    if (dd.log_sel) dd.log_sel[shot] = sel;
-    if (dd.log_thr) {
-        dd.log_thr[2 * (int64_t)shot] = sel ? cum[sel - 1] : 0.0;
-        dd.log_thr[2 * (int64_t)shot + 1] = cum[sel];
+    if (d.fork_log) {
+        __syncwarp();
+        if (lane == 0) log_fork_events(d, dd, T);
+        __syncwarp();
     }
-    return sel;
 }
 
 // Branches of up to DEC_THREADS * DEC_SPT shots are staged in shared
@@ -1438,17 +1577,15 @@ __device__ __forceinline__ int draw_choice(const DevBatch& d, const DecideDesc& 
 constexpr int DEC_SPT = 20;
 constexpr size_t DEC_BIG_SMEM = (size_t)DEC_SPT * DEC_THREADS * (sizeof(uint32_t) + sizeof(uint8_t));
 
-__global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __grid_constant__ DecideDesc dd) {
-    __shared__ double p_sh[MAX_TERMS], cum_sh[MAX_TERMS];
-    __shared__ uint64_t thr_sh[MAX_TERMS];
-    __shared__ int bincnt[MAX_TERMS], binbase[MAX_TERMS], binrun[MAX_TERMS];
+__global__ void __launch_bounds__(DEC_THREADS, 1) k_decide_big(DevBatch d, const __grid_constant__ DecideDesc dd) {
+    __shared__ DecTab T;
     __shared__ int ng_sh, nlist_sh;
     __shared__ int list_sh[DEC_THREADS];
     extern __shared__ __align__(16) unsigned char dec_smem[];
     uint32_t* sm_shot = reinterpret_cast<uint32_t*>(dec_smem);
-    uint8_t* sm_sel = reinterpret_cast<uint8_t*>(sm_shot + DEC_SPT * DEC_THREADS);
+    uint8_t* sm_key = reinterpret_cast<uint8_t*>(sm_shot + DEC_SPT * DEC_THREADS);
     const int n_br = d.ctl[CTL_NBR];
-    const int R = dd.R;
+    const int NK = dd.nk;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
     // this CTA's branches are blockIdx.x + j * gridDim.x; its threads look at
@@ -1477,51 +1614,44 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
                 }
             }
             __syncthreads();
-            if (warp == 0) warp_probs(d, dd, b, slot, p_sh, cum_sh);
-            if (tid < R) {
-                bincnt[tid] = 0;
-                binrun[tid] = 0;
+            if (warp == 0) branch_tables(d, dd, b, slot, T);
+            if (tid < NK) {
+                T.bincnt[tid] = 0;
+                T.binrun[tid] = 0;
             }
-            __syncthreads();
-            if (tid == 0 && dd.kind != DEC_PAULI) {
-                double acc = 0.0;
-                for (int r = 0; r < R; ++r) cum_sh[r] = (acc += p_sh[r]);
-            }
-            __syncthreads();
-            for (int r = tid; r < R; r += nth) thr_sh[r] = cum_threshold(cum_sh[r]);
             __syncthreads();
             if (onchip) {
 #pragma unroll 1
                 for (int k = 0; k < nk; ++k) {
                     const int i = tid + k * nth;
-                    int sel = -1;
+                    int key = -1;
                     if (i < cnt) {
-                        sel = draw_choice(d, dd, sm_shot[k * nth + tid], cum_sh, thr_sh);
-                        sm_sel[k * nth + tid] = (uint8_t)sel;
+                        key = chain_draw(d, dd, T, sm_shot[k * nth + tid]);
+                        sm_key[k * nth + tid] = (uint8_t)key;
                     }
-                    const unsigned peers = __match_any_sync(0xffffffffu, sel);
-                    if (sel >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&bincnt[sel], __popc(peers));
+                    const unsigned peers = __match_any_sync(0xffffffffu, key);
+                    if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&T.bincnt[key], __popc(peers));
                 }
             } else {
 #pragma unroll 1
                 for (int base = 0; base < cnt; base += nth) {  // warp-aggregated bin counts
                     const int i = base + tid;
-                    int sel = -1;
+                    int key = -1;
                     if (i < cnt) {
-                        sel = draw_choice(d, dd, d.perm[start + i], cum_sh, thr_sh);
-                        d.shot_sel[start + i] = sel;
+                        key = chain_draw(d, dd, T, d.perm[start + i]);
+                        d.shot_sel[start + i] = key;
                     }
-                    const unsigned peers = __match_any_sync(0xffffffffu, sel);
-                    if (sel >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&bincnt[sel], __popc(peers));
+                    const unsigned peers = __match_any_sync(0xffffffffu, key);
+                    if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&T.bincnt[key], __popc(peers));
                 }
             }
             __syncthreads();
             if (tid == 0) {
                 int ng = 0, acc = 0;
-                for (int r = 0; r < R; ++r)
-                    if (bincnt[r] > 0) {
-                        binbase[r] = acc;
-                        acc += bincnt[r];
+                for (int r = 0; r < NK; ++r)
+                    if (T.bincnt[r] > 0) {
+                        T.binbase[r] = acc;
+                        acc += T.bincnt[r];
                         ++ng;
                     }
                 ng_sh = ng;
@@ -1535,34 +1665,34 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decide_big(DevBatch d, const __
 #pragma unroll 1
                     for (int k = 0; k < nk; ++k) {
                         const int i = tid + k * nth;
-                        const int sel = i < cnt ? (int)sm_sel[k * nth + tid] : -1;
-                        const unsigned peers = __match_any_sync(0xffffffffu, sel);
+                        const int key = i < cnt ? (int)sm_key[k * nth + tid] : -1;
+                        const unsigned peers = __match_any_sync(0xffffffffu, key);
                         const int rank = __popc(peers & ((1u << lane) - 1u));
                         const int leader = __ffs(peers) - 1;
                         int pos = 0;
-                        if (sel >= 0 && rank == 0) pos = atomicAdd(&binrun[sel], __popc(peers));
+                        if (key >= 0 && rank == 0) pos = atomicAdd(&T.binrun[key], __popc(peers));
                         pos = __shfl_sync(0xffffffffu, pos, leader);
-                        if (sel >= 0) d.perm[start + binbase[sel] + pos + rank] = sm_shot[k * nth + tid];
+                        if (key >= 0) d.perm[start + T.binbase[key] + pos + rank] = sm_shot[k * nth + tid];
                     }
                 } else {
 #pragma unroll 1
                     for (int base = 0; base < cnt; base += nth) {
                         const int i = base + tid;
-                        const int sel = (i < cnt) ? d.shot_sel[start + i] : -1;
-                        const unsigned peers = __match_any_sync(0xffffffffu, sel);
+                        const int key = (i < cnt) ? d.shot_sel[start + i] : -1;
+                        const unsigned peers = __match_any_sync(0xffffffffu, key);
                         const int rank = __popc(peers & ((1u << lane) - 1u));
                         const int leader = __ffs(peers) - 1;
                         int pos = 0;
-                        if (sel >= 0 && rank == 0) pos = atomicAdd(&binrun[sel], __popc(peers));
+                        if (key >= 0 && rank == 0) pos = atomicAdd(&T.binrun[key], __popc(peers));
                         pos = __shfl_sync(0xffffffffu, pos, leader);
-                        if (sel >= 0) d.perm_tmp[start + binbase[sel] + pos + rank] = d.perm[start + i];
+                        if (key >= 0) d.perm_tmp[start + T.binbase[key] + pos + rank] = d.perm[start + i];
                     }
                     __syncthreads();
                     for (int i = tid; i < cnt; i += nth) d.perm[start + i] = d.perm_tmp[start + i];
                 }
                 __syncthreads();
             }
-            if (warp == 0) decide_groups(d, dd, b, start, bincnt, binbase, p_sh);
+            if (warp == 0) decide_groups(d, dd, b, start, T);
         }
     }
 }
@@ -1572,19 +1702,12 @@ constexpr int DECS_WARPS = 8;
 // one warp per branch of at most DEC_SMALL (= 64) shots: two shots per lane,
 // held in registers from the first load to the in-place partition
 __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, const __grid_constant__ DecideDesc dd) {
-    __shared__ double p_sh[DECS_WARPS][MAX_TERMS], cum_sh[DECS_WARPS][MAX_TERMS];
-    __shared__ uint64_t thr_sh[DECS_WARPS][MAX_TERMS];
-    __shared__ int bincnt[DECS_WARPS][MAX_TERMS], binbase[DECS_WARPS][MAX_TERMS], binrun[DECS_WARPS][MAX_TERMS];
+    __shared__ DecTab tabs[DECS_WARPS];
     static_assert(DEC_SMALL == 64, "two shots per lane");
     const int n_br = d.ctl[CTL_NBR];
-    const int R = dd.R;
+    const int NK = dd.nk;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double* p = p_sh[warp];
-    double* cum = cum_sh[warp];
-    uint64_t* thr = thr_sh[warp];
-    int* bc = bincnt[warp];
-    int* bb = binbase[warp];
-    int* br = binrun[warp];
+    DecTab& T = tabs[warp];
     const int gw = blockIdx.x * DECS_WARPS + warp, nw = gridDim.x * DECS_WARPS;
     for (int b = gw; b < n_br; b += nw) {
         const int cnt = d.br_count[b];
@@ -1593,33 +1716,26 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
         uint32_t sh[2];
         sh[0] = lane < cnt ? d.perm[start + lane] : 0u;
         sh[1] = lane + 32 < cnt ? d.perm[start + lane + 32] : 0u;
-        warp_probs(d, dd, b, slot, p, cum);
-        for (int r = lane; r < R; r += 32) {
-            bc[r] = 0;
-            br[r] = 0;
+        branch_tables(d, dd, b, slot, T);
+        for (int r = lane; r < NK; r += 32) {
+            T.bincnt[r] = 0;
+            T.binrun[r] = 0;
         }
         __syncwarp();
-        if (lane == 0 && dd.kind != DEC_PAULI) {
-            double acc = 0.0;
-            for (int r = 0; r < R; ++r) cum[r] = (acc += p[r]);
-        }
-        __syncwarp();
-        for (int r = lane; r < R; r += 32) thr[r] = cum_threshold(cum[r]);
-        __syncwarp();
-        int sl[2];
+        int key[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            sl[k] = lane + 32 * k < cnt ? draw_choice(d, dd, sh[k], cum, thr) : -1;
-            if (sl[k] >= 0) atomicAdd(&bc[sl[k]], 1);
+            key[k] = lane + 32 * k < cnt ? chain_draw(d, dd, T, sh[k]) : -1;
+            if (key[k] >= 0) atomicAdd(&T.bincnt[key[k]], 1);
         }
         __syncwarp();
         int ng = 0;
         if (lane == 0) {
             int acc = 0;
-            for (int r = 0; r < R; ++r)
-                if (bc[r] > 0) {
-                    bb[r] = acc;
-                    acc += bc[r];
+            for (int r = 0; r < NK; ++r)
+                if (T.bincnt[r] > 0) {
+                    T.binbase[r] = acc;
+                    acc += T.bincnt[r];
                     ++ng;
                 }
         }
@@ -1628,16 +1744,16 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
         if (ng > 1 && dd.fork) {
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const int sel = sl[k];
-                const unsigned peers = __match_any_sync(0xffffffffu, sel);
+                const int kk = key[k];
+                const unsigned peers = __match_any_sync(0xffffffffu, kk);
                 const int rank = __popc(peers & ((1u << lane) - 1u));
-                if (sel >= 0) d.perm[start + bb[sel] + br[sel] + rank] = sh[k];
+                if (kk >= 0) d.perm[start + T.binbase[kk] + T.binrun[kk] + rank] = sh[k];
                 __syncwarp();
-                if (sel >= 0 && rank == 0) br[sel] += __popc(peers);
+                if (kk >= 0 && rank == 0) T.binrun[kk] += __popc(peers);
                 __syncwarp();
             }
         }
-        decide_groups(d, dd, b, start, bc, bb, p);
+        decide_groups(d, dd, b, start, T);
         __syncwarp();
     }
 }

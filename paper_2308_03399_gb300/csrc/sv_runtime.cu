@@ -162,6 +162,7 @@ struct sv_batch_s {
     // graph replays only while the generations it captured are current
     uint64_t pool_gen = 0, graph_gen = 0;
     bool joint = true;  // decide back-to-back one-qubit Kraus pairs from one pass
+    bool chain = true;  // decide ops that need no pass between in one launch
     std::map<int, int> reg_occ;
     int slot_limit = 0;
 };
@@ -531,8 +532,56 @@ sv_status get_log(sv_batch b, uint32_t op, int32_t** sel, double** thr) {
 }
 
 // decide (+ fork) for random op `op`; the chosen term is then queued as a stage
+// A decide that directly follows another in the recorded launch list (no
+// pass between) joins it as a tail op when it needs no new reduction: the
+// second op of a joint Kraus pair right after the first, or any Pauli op.
+// One launch and one copy then serve the whole chain.
+bool chain_decide(sv_batch b, uint32_t op, int kind, int R, const double* cum, int pend) {
+    if (!b->rec || b->rec->empty()) return false;
+    std::vector<Launch>& rec = *b->rec;
+    size_t i = rec.size() - 1;
+    if (b->branch) {
+        if (rec[i].type != L_COPY || i == 0) return false;
+        --i;
+    }
+    if (rec[i].type != L_DECIDE) return false;
+    DecideDesc& h = rec[i].dec;
+    if (h.n_tail >= MAX_TAIL || (int64_t)h.nk * R > MAX_TERMS) return false;
+    if (kind == DEC_KRAUS_J2) {
+        if (h.kind != DEC_KRAUS_J1 || h.n_tail != 0 || R != h.r2) return false;
+    } else if (kind != DEC_PAULI) {
+        return false;
+    }
+    int used = 0;
+    for (int t = 0; t < h.n_tail; ++t)
+        if (h.tail[t].kind == DEC_PAULI) used = std::max(used, h.tail[t].cum_off + h.tail[t].R);
+    if (kind == DEC_PAULI && used + R > MAX_TAIL_TERMS) return false;
+    DecideTail& tl = h.tail[h.n_tail];
+    memset(&tl, 0, sizeof(tl));
+    tl.op = op;
+    tl.kind = kind;
+    tl.R = R;
+    tl.pend = pend;
+    if (get_log(b, op, &tl.log_sel, &tl.log_thr)) return false;
+    if (kind == DEC_PAULI) {
+        tl.cum_off = used;
+        for (int t = 0; t < R; ++t) {
+            h.tail_cum[used + t] = cum[t];
+            // ceil(c * 2^53): the scaling is exact, as on the device
+            h.tail_thr[used + t] = cum[t] > 0.0 ? (uint64_t)std::ceil(cum[t] * 9007199254740992.0) : 0ull;
+        }
+    }
+    h.n_tail += 1;
+    h.nk *= R;
+    return true;
+}
+
 sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cum, int pend, int m,
                       const int* clbits, int r2 = 0, int pend_prev = -1) {
+    if (b->chain && chain_decide(b, op, kind, R, cum, pend)) {
+        b->last_random = op;
+        return SV_OK;
+    }
     Launch L;
     L.type = L_DECIDE;
     DecideDesc& d = L.dec;
@@ -546,6 +595,7 @@ sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cu
     d.m = m;
     d.r2 = r2;
     d.pend_prev = pend_prev;
+    d.nk = R;
     for (int j = 0; j < m; ++j) d.clbit[j] = clbits[j];
     if (cum)
         for (int t = 0; t < R; ++t) d.cum[t] = cum[t];
@@ -1231,8 +1281,18 @@ sv_status sv_free_batch(sv_batch b) {
     return SV_OK;
 }
 
+static sv_status set_option(sv_batch b, sv_option opt, int64_t v);
+
 sv_status sv_set_option(sv_batch b, sv_option opt, int64_t v) {
     if (!b) return fail(SV_EINVAL, "batch is NULL");
+    const sv_status st = set_option(b, opt, v);
+    // options shape the recorded launches (and the device struct the
+    // kernels take by value): a cached graph is recorded again
+    if (st == SV_OK && opt != SV_OPT_UPLOAD && opt != SV_OPT_PROFILE) b->pool_gen += 1;
+    return st;
+}
+
+static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
     switch (opt) {
     case SV_OPT_LOG:
         if (v && !b->dev.fork_log) {
@@ -1269,8 +1329,8 @@ sv_status sv_set_option(sv_batch b, sv_option opt, int64_t v) {
         if (v < 0) return fail(SV_EINVAL, "shot base must be >= 0");
         if (!b->pend.empty()) return fail(SV_EINVAL, "per-op calls are in progress on this batch");
         b->dev.shot_base = (uint64_t)v;
-        b->pool_gen += 1;  // kernels take the batch by value: cached graphs are stale
         return SV_OK;
+    case SV_OPT_CHAIN_DECIDES: b->chain = v != 0; return SV_OK;
     case SV_OPT_SLOT_LIMIT:
         if (v < 0) return fail(SV_EINVAL, "slot limit must be >= 0");
         b->slot_limit = (int)v;

@@ -272,3 +272,18 @@ def test_shot_ranges_concatenate_to_one_run(prec):
         b.set_option(sv.SV_OPT_SHOT_BASE, 201)
         b.run_circuit(cs)
         assert np.array_equal(b.get_keys(), whole[201:301])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", ["su4_kraus", "midmeasure", "brickwork"])
+def test_chained_and_separate_decides_agree(name, mode, prec):
+    # a chain (head op, the second op of a Kraus pair, Pauli ops) decided in
+    # one launch takes the same choices as one launch per op
+    c = SMALL[name]()
+    a = run_gpu(c, 12, 200, mode, prec)
+    b = run_gpu(c, 12, 200, mode, prec, opts={sv.SV_OPT_CHAIN_DECIDES: 0})
+    for op in c.random_ops():
+        assert np.array_equal(a["sel"][op], b["sel"][op]), op
+    assert np.array_equal(a["keys"], b["keys"])
+    assert a["stats"]["launches"] < b["stats"]["launches"]
