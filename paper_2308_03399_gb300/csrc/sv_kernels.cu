@@ -976,6 +976,8 @@ __device__ __forceinline__ void reg_diag(const typename Cplx<R>::T* v, const Pas
 // registers (five CTAs, 20 warps per SM; the pass is latency-bound, so
 // resident warps matter more than a few spilled words); complex128 at 256
 // threads, where the same cap would spill kilobytes
+constexpr int REG_PREFETCH = 1;  // groups ahead of a lane's loads that go to L2
+
 template <class R> struct RegCta;
 template <> struct RegCta<float> { static constexpr int threads = 128, min_blocks = 5; };
 template <> struct RegCta<double> { static constexpr int threads = 256, min_blocks = 1; };
@@ -1147,8 +1149,8 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
             };
             // the lane's next group goes to L2 ahead of its loads (no
             // registers held): the pass is latency-bound at 16 warps per SM
-            if (gi + 32 < gpu) {
-                const T* gn = gstate + group_base(c * gpu + gi + 32);
+            if (gi + 32 * REG_PREFETCH < gpu) {
+                const T* gn = gstate + group_base(c * gpu + gi + 32 * REG_PREFETCH);
 #pragma unroll
                 for (int e = 0; e < G; e += (sizeof(T) == 8 && PAIRED) ? 2 : 1)
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(gn + off(e)));
