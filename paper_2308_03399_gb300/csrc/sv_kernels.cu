@@ -1261,8 +1261,14 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
 constexpr int DEC_THREADS = 512;
 constexpr int DEC_SMALL = 64;
 
-__device__ __forceinline__ double warp_sum(double x) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+// Sum over the lanes by a fixed xor tree.  Lanes at or past `used` hold
+// exact zeros, and adding a zero changes nothing, so the tree can start at
+// the level that first mixes the used lanes: the same result in fewer
+// float64 adds (each a 16-cycle FP64-pipe instruction on GB300).
+__device__ __forceinline__ double warp_sum(double x, int used) {
+    int o = 16;
+    while (o > 1 && o >= used) o >>= 1;
+    for (; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
 }
 
@@ -1320,7 +1326,7 @@ __device__ void warp_probs(const DevBatch& d, const DecideDesc& dd, int b, int s
 #pragma unroll
     for (int k = 0; k < MAX_RED; ++k)
         if (k < nk) {
-            const double t = warp_sum(u[k]);
+            const double t = warp_sum(u[k], dd.chunks);
             if (lane == 0) cum_out[k] = t;  // scratch until the caller forms the table
         }
     __syncwarp();
