@@ -105,7 +105,7 @@ typedef enum {
     SV_OPT_LOG = 0,         /* 1: record per-shot outcomes, thresholds and fork events */
     SV_OPT_TILE_BITS = 1,   /* amplitudes per CTA tile = 2^value (0 = default)          */
     SV_OPT_MAX_ACTIVE = 2,  /* most distinct qubits fused into one pass (0 = default:
-                               8 when the state fits one tile, else 4)               */
+                               all when the state fits one tile, else 4)             */
     SV_OPT_MAX_STAGES = 3,  /* most ops fused into one pass (0 = default)               */
     SV_OPT_THREADS = 4,     /* threads per CTA of the pass kernel (0 = default)         */
     SV_OPT_GRID = 5,        /* CTAs of the persistent kernels (0 = default)             */
@@ -124,9 +124,13 @@ typedef enum {
                                processes or devices, merge into the histogram of
                                one run over the union (shots are independent,
                                Section IV-C).  Keys stay indexed by local shot. */
-    SV_OPT_CHAIN_DECIDES = 12 /* 1 (default): sv_run_circuit decides, in one launch,
+    SV_OPT_CHAIN_DECIDES = 12, /* 1 (default): sv_run_circuit decides, in one launch,
                                an op and the ops after it that need no new pass
                                (the second op of a joint Kraus pair, Pauli ops) */
+    SV_OPT_PREDRAW_PAULI = 13 /* 1 (default): in batch mode, sv_run_circuit draws the
+                               Pauli choices of every shot in one launch before the
+                               first gate (up to 1 GiB of one-byte choices)
+                               instead of one decide per Pauli op */
 } sv_option;
 
 /* Allocate a batch of n_shots shots of an n_qubits register.

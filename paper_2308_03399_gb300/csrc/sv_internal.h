@@ -13,6 +13,8 @@ constexpr int MAX_STAGES = 40;     // ops fused into one pass
 constexpr int MAX_PEND = 16;       // random ops whose per-branch choice is applied in one pass
 constexpr int MAX_TERMS = 64;      // terms of one random op (Pauli strings)
 constexpr int64_t REG_UNIT_MIN_AMPS = 8192;  // smallest register-path unit
+constexpr int PRE_WORDS = 8;                 // integer-pool words per pre-drawn Pauli row
+constexpr uint64_t PRE_TABLE_BYTES = 1ull << 30;  // largest pre-drawn Pauli table
 constexpr int MAX_RED = 16;        // probabilities reduced by one pass (Kraus terms, 2^m outcomes)
 constexpr int MAX_CHUNKS = 1024;   // reduction partials per state
 constexpr int MAX_STAGE_Q = 4;     // qubits of one stage
@@ -45,6 +47,7 @@ struct Stage {
     int32_t off;               // pool offset (real units) / ipool offset (ST_PAULI_BR)
     int32_t stride;            // real units between terms (ST_DENSE_BR)
     int32_t mat;               // offset of this stage's matrix in the shared-memory matrix area
+    int32_t pre;               // ST_PAULI_BR: the choice is row `pend` of the pre-drawn table
 };
 
 struct PassDesc {
@@ -139,6 +142,7 @@ struct DevBatch {
     const void* pool;          // real-typed constants (matrices, forms)
     const int32_t* ipool;      // integer constants (Pauli parameters)
     uint64_t* keys;            // per shot id
+    uint8_t* pre_sel;          // pre-drawn Pauli choices, [row][shot id] (batch mode)
     int32_t* pos_branch;       // branch owning each perm position (final sampling)
     int64_t* fork_log;         // 5 per event, nullable
     int32_t fork_log_cap;
@@ -169,6 +173,7 @@ cudaError_t launch_reset(const DevBatch& d, int mode_branch, int n_shots_run, in
                          cudaStream_t s);
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s);
 cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int n_sm, cudaStream_t s);
+cudaError_t launch_predraw(const DevBatch& d, int n_rows, int table, int n_shots, int grid, cudaStream_t s);
 cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s);
 cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s);
 size_t pass_smem_bytes(int prec, const PassDesc& p, int threads);

@@ -584,7 +584,11 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
                 int sk = 0, sel = 0, packed = 0;
                 double scale = 1.0;
                 if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val) sk = 1;
-                if (st.kind != ST_DENSE) {
+                if (st.pre) {  // batch mode: the branch's one shot, pre-drawn
+                    sel = d.pre_sel[(int64_t)st.pend * d.cap_br + d.perm[d.br_start[b]]];
+                    packed = d.ipool[st.off + sel];
+                    if ((packed & 0xff) == 0) sk = 1;
+                } else if (st.kind != ST_DENSE) {
                     sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
                     scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
                     if (sel < 0) sk = 1;
@@ -1039,7 +1043,11 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                 int sk = 0, sel = 0, packed = 0;
                 double scale = 1.0;
                 if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val) sk = 1;
-                if (st.kind != ST_DENSE) {
+                if (st.pre) {  // batch mode: the branch's one shot, pre-drawn
+                    sel = d.pre_sel[(int64_t)st.pend * d.cap_br + d.perm[d.br_start[b]]];
+                    packed = d.ipool[st.off + sel];
+                    if ((packed & 0xff) == 0) sk = 1;
+                } else if (st.kind != ST_DENSE) {
                     sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
                     scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
                     if (sel < 0) sk = 1;
@@ -1764,6 +1772,44 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
         decide_groups(d, dd, b, start, T);
         __syncwarp();
     }
+}
+
+// ---------------------------------------------------------------------------
+// k_predraw: Pauli choices of every shot for the Pauli ops of a batch-mode
+// circuit, drawn before the first gate (Section IV-A-3 samples Pauli noise
+// ahead of applying it).  With one shot per branch a Pauli choice never
+// forks anything, so no decide is needed: row q of pre_sel holds op q's
+// choice per shot id, and the pass reads its branch's shot's entry.  The
+// rows' descriptors sit in the integer pool at `table`, PRE_WORDS each: op,
+// R, pool offsets of the R thresholds ceil(C * 2^53) and of the R running
+// sums (both 64-bit words as int32 pairs), then the two log pointers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t ipool_u64(const int32_t* ip, int64_t off) {
+    return (uint64_t)(uint32_t)ip[off] | ((uint64_t)(uint32_t)ip[off + 1] << 32);
+}
+
+__global__ void __launch_bounds__(256) k_predraw(DevBatch d, int n_rows, int table, int n_shots) {
+    const int64_t total = (int64_t)n_rows * n_shots;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int q = (int)(i / n_shots);
+        const uint32_t s = (uint32_t)(i % n_shots);
+        const int32_t* e = d.ipool + table + (int64_t)PRE_WORDS * q;
+        const uint32_t op = (uint32_t)e[0];
+        const int R = e[1];
+        const uint64_t* thr = reinterpret_cast<const uint64_t*>(d.ipool + e[2]);
+        const double* cum = reinterpret_cast<const double*>(d.ipool + e[3]);
+        const int sel = select_k(philox_k53(d.seed, d.shot_base + s, op), thr, cum, R);
+        d.pre_sel[(int64_t)q * d.cap_br + s] = (uint8_t)sel;
+        int32_t* log_sel = reinterpret_cast<int32_t*>(ipool_u64(d.ipool, table + (int64_t)PRE_WORDS * q + 4));
+        double* log_thr = reinterpret_cast<double*>(ipool_u64(d.ipool, table + (int64_t)PRE_WORDS * q + 6));
+        log_choice(log_sel, log_thr, s, sel, cum);
+    }
+}
+
+cudaError_t launch_predraw(const DevBatch& d, int n_rows, int table, int n_shots, int grid, cudaStream_t s) {
+    k_predraw<<<grid, 256, 0, s>>>(d, n_rows, table, n_shots);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -46,9 +46,19 @@ struct PendStage {
     int kind, k;
     int q[MAX_STAGE_Q];
     int cond_clbit, cond_val, pend, reset, off, stride;
+    int pre;  // ST_PAULI_BR: row of the pre-drawn table (batch mode), not a pending column
 };
 
-enum LType { L_INIT, L_RESET, L_PASS, L_DECIDE, L_ALLOC, L_COPY, L_FINAL };
+// a Pauli op of a batch-mode circuit whose choices are drawn up front
+struct PreRow {
+    uint32_t op;
+    int R;
+    int thr_off, cum_off;  // integer-pool offsets of the thresholds and running sums
+    int32_t* log_sel;
+    double* log_thr;
+};
+
+enum LType { L_INIT, L_RESET, L_PASS, L_DECIDE, L_ALLOC, L_COPY, L_FINAL, L_PREDRAW };
 enum PClass { P_PASS = 0, P_DECIDE, P_ALLOC, P_COPY, P_FINAL, P_INIT, P_OTHER, P_N };
 
 struct Launch {
@@ -163,6 +173,9 @@ struct sv_batch_s {
     uint64_t pool_gen = 0, graph_gen = 0;
     bool joint = true;  // decide back-to-back one-qubit Kraus pairs from one pass
     bool chain = true;  // decide ops that need no pass between in one launch
+    bool predraw = true;  // batch mode: Pauli choices drawn up front, no decides
+    std::vector<PreRow> pre_rows;  // of the circuit being recorded
+    int pre_cap = 0;               // rows the device table holds
     std::map<int, int> reg_occ;
     int slot_limit = 0;
 };
@@ -186,6 +199,7 @@ int pclass(LType t) {
     switch (t) {
     case L_PASS: return P_PASS;
     case L_DECIDE: return P_DECIDE;
+    case L_PREDRAW: return P_DECIDE;
     case L_ALLOC: return P_ALLOC;
     case L_COPY: return P_COPY;
     case L_FINAL: return P_FINAL;
@@ -227,6 +241,7 @@ cudaError_t exec_one(sv_batch b, const Launch& L) {
     case L_ALLOC: return cudaSuccess;
     case L_COPY: return launch_copy(b->dev, prec, b->n_sm * 4, b->stream);
     case L_FINAL: return launch_final(b->dev, prec, L.fin, b->grid_small, b->stream);
+    case L_PREDRAW: return launch_predraw(b->dev, L.a0, L.a1, L.a2, b->n_sm * 4, b->stream);
     }
     return cudaErrorInvalidValue;
 }
@@ -430,6 +445,7 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
         st.reset = ps.reset;
         st.off = ps.off;
         st.stride = ps.stride;
+        st.pre = ps.pre;
         st.mat = 0;
         if (ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) {
             st.mat = mat;
@@ -671,13 +687,44 @@ sv_status op_pauli(sv_batch b, uint32_t op, int k, const int* q, int n_terms, co
             if (!strchr("IXYZ", paulis[t * k + j]) || !paulis[t * k + j]) return fail(SV_EINVAL, "bad Pauli character");
     }
     if ((st = ensure_started(b))) return st;
-    if ((st = make_room(b, q, k, 0, true))) return st;
-    const int pend = b->n_pend++;
+    // batch mode, whole circuits: the choice of every shot is drawn up front
+    // (k_predraw), so the op needs no decide and no pending column
+    const bool pre = b->rec && !b->branch && b->predraw &&
+                     (uint64_t)(b->pre_rows.size() + 1) * b->n_shots <= PRE_TABLE_BYTES;
+    if ((st = make_room(b, q, k, 0, !pre))) return st;
     const int off = (int)b->ipool.size();
     for (int t = 0; t < n_terms; ++t) b->ipool.push_back(pauli_packed(paulis + t * k, k));
-    if ((st = upload_pool(b))) return st;
-    if ((st = emit_decide(b, op, DEC_PAULI, n_terms, cum, pend, 0, nullptr))) return st;
+    int pend;
+    if (pre) {
+        PreRow r{};
+        r.op = op;
+        r.R = n_terms;
+        if (b->ipool.size() & 1) b->ipool.push_back(0);  // 64-bit words start 8-byte aligned
+        r.thr_off = (int)b->ipool.size();
+        for (int t = 0; t < n_terms; ++t) {
+            // ceil(C * 2^53): the scaling is exact, as on the device
+            const uint64_t thr = cum[t] > 0.0 ? (uint64_t)std::ceil(cum[t] * 9007199254740992.0) : 0ull;
+            b->ipool.push_back((int32_t)(uint32_t)thr);
+            b->ipool.push_back((int32_t)(uint32_t)(thr >> 32));
+        }
+        r.cum_off = (int)b->ipool.size();
+        for (int t = 0; t < n_terms; ++t) {
+            uint64_t bits;
+            memcpy(&bits, &cum[t], 8);
+            b->ipool.push_back((int32_t)(uint32_t)bits);
+            b->ipool.push_back((int32_t)(uint32_t)(bits >> 32));
+        }
+        if ((st = get_log(b, op, &r.log_sel, &r.log_thr))) return st;
+        pend = (int)b->pre_rows.size();
+        b->pre_rows.push_back(r);
+        b->last_random = op;
+    } else {
+        pend = b->n_pend++;
+        if ((st = upload_pool(b))) return st;
+        if ((st = emit_decide(b, op, DEC_PAULI, n_terms, cum, pend, 0, nullptr))) return st;
+    }
     PendStage s{};
+    s.pre = pre ? 1 : 0;
     s.kind = ST_PAULI_BR;
     s.k = k;
     for (int j = 0; j < k; ++j) s.q[j] = q[j];
@@ -1084,6 +1131,33 @@ sv_status run_plain(sv_batch b, const sv_circuit* c) {
 
 // the launch sequence of a whole circuit (without the reset / init of the
 // root), with its constants uploaded
+// the pre-drawn rows of a recorded circuit: their descriptors go to the
+// integer pool, the device table grows to hold them, and the draw is the
+// circuit's first launch
+sv_status finish_predraw(sv_batch b, std::vector<Launch>& launches) {
+    const int n = (int)b->pre_rows.size();
+    const int table = (int)b->ipool.size();
+    for (const PreRow& r : b->pre_rows) {
+        const uint64_t ls = (uint64_t)(uintptr_t)r.log_sel, lt = (uint64_t)(uintptr_t)r.log_thr;
+        const int32_t w[PRE_WORDS] = {(int32_t)r.op, r.R, r.thr_off, r.cum_off, (int32_t)(uint32_t)ls,
+                                      (int32_t)(uint32_t)(ls >> 32), (int32_t)(uint32_t)lt, (int32_t)(uint32_t)(lt >> 32)};
+        b->ipool.insert(b->ipool.end(), w, w + PRE_WORDS);
+    }
+    if (n > b->pre_cap) {
+        sv_status st = dalloc(b, &b->dev.pre_sel, (size_t)n * b->n_shots);
+        if (st) return st;
+        b->pre_cap = n;
+        b->pool_gen += 1;  // kernels take the batch by value
+    }
+    Launch L;
+    L.type = L_PREDRAW;
+    L.a0 = n;
+    L.a1 = table;
+    L.a2 = (int)b->n_shots;
+    launches.insert(launches.begin(), L);
+    return SV_OK;
+}
+
 sv_status record_circuit(sv_batch b, const sv_circuit* c, std::vector<Launch>& launches) {
     sv_status st = reset_pool(b);
     if (st) return st;
@@ -1091,6 +1165,7 @@ sv_status record_circuit(sv_batch b, const sv_circuit* c, std::vector<Launch>& l
     b->started = true;  // reset / init are issued by the caller, per run
     b->rec = &launches;
     b->n_pend = 0;
+    b->pre_rows.clear();
     for (int i = 0; i < c->n_ops && !st; ++i) {
         if (b->joint && i + 1 < c->n_ops && c->kind[i] == SV_OP_KRAUS && c->kind[i + 1] == SV_OP_KRAUS &&
             c->nq[i] == 1 && c->nq[i + 1] == 1 && c->qubits[c->q_off[i]] != c->qubits[c->q_off[i + 1]] &&
@@ -1105,6 +1180,7 @@ sv_status record_circuit(sv_batch b, const sv_circuit* c, std::vector<Launch>& l
     }
     if (!st) st = flush(b);
     b->rec = nullptr;
+    if (!st && !b->pre_rows.empty()) st = finish_predraw(b, launches);
     if (st) return st;
     return upload_pool(b);
 }
@@ -1170,11 +1246,12 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
     cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
     b->grid_small = 2 * b->n_sm;
     b->tb = std::min(n_qubits, prec == SV_C128 ? 10 : 11);
-    // Fusion width: when the whole state is one tile, fuse up to 8 qubits per
-    // pass; otherwise at most 4, so passes run on the register path (wider
-    // passes over a bigger state leave the tile few contiguous low qubits
-    // and its bulk copies turn short)
-    b->max_active = n_qubits <= b->tb ? 8 : 4;
+    // Fusion width: when the whole state is one tile, a pass may touch every
+    // qubit (the state sits in shared memory); otherwise at most 4, so
+    // passes run on the register path (wider passes over a bigger state
+    // leave the tile few contiguous low qubits and its bulk copies turn
+    // short)
+    b->max_active = n_qubits <= b->tb ? n_qubits : 4;
     const int64_t tiles = 1ll << (n_qubits - b->tb);
     b->chunks = (int)std::min<int64_t>(tiles, MAX_CHUNKS);
     b->chunks_final = (int)std::min<int64_t>(std::max<int64_t>(b->dim / 2048, 1), MAX_CHUNKS);
@@ -1310,7 +1387,7 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
         b->chunks = (int)std::min<int64_t>(1ll << (b->n - b->tb), b->dev.max_chunks);
         return SV_OK;
     case SV_OPT_MAX_ACTIVE:
-        b->max_active = v ? (int)std::max<int64_t>(2, v) : (b->n <= b->tb ? 8 : 4);
+        b->max_active = v ? (int)std::max<int64_t>(2, v) : (b->n <= b->tb ? b->n : 4);
         return SV_OK;
     case SV_OPT_MAX_STAGES: b->max_stages = v ? (int)std::min<int64_t>(std::max<int64_t>(v, 1), MAX_STAGES) : MAX_STAGES; return SV_OK;
     case SV_OPT_THREADS:
@@ -1331,6 +1408,7 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
         b->dev.shot_base = (uint64_t)v;
         return SV_OK;
     case SV_OPT_CHAIN_DECIDES: b->chain = v != 0; return SV_OK;
+    case SV_OPT_PREDRAW_PAULI: b->predraw = v != 0; return SV_OK;
     case SV_OPT_SLOT_LIMIT:
         if (v < 0) return fail(SV_EINVAL, "slot limit must be >= 0");
         b->slot_limit = (int)v;

@@ -281,9 +281,26 @@ def test_chained_and_separate_decides_agree(name, mode, prec):
     # a chain (head op, the second op of a Kraus pair, Pauli ops) decided in
     # one launch takes the same choices as one launch per op
     c = SMALL[name]()
-    a = run_gpu(c, 12, 200, mode, prec)
-    b = run_gpu(c, 12, 200, mode, prec, opts={sv.SV_OPT_CHAIN_DECIDES: 0})
+    # batch mode would draw the Pauli ops up front: keep them as decides here
+    a = run_gpu(c, 12, 200, mode, prec, opts={sv.SV_OPT_PREDRAW_PAULI: 0})
+    b = run_gpu(c, 12, 200, mode, prec, opts={sv.SV_OPT_PREDRAW_PAULI: 0, sv.SV_OPT_CHAIN_DECIDES: 0})
     for op in c.random_ops():
         assert np.array_equal(a["sel"][op], b["sel"][op]), op
     assert np.array_equal(a["keys"], b["keys"])
     assert a["stats"]["launches"] < b["stats"]["launches"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["brickwork", "midmeasure", "su4_kraus"])
+def test_predrawn_pauli_choices_match_decides(name, prec):
+    # batch mode draws every shot's Pauli choices in one launch up front;
+    # the choices, logs and keys are those of one decide per Pauli op
+    c = SMALL[name]()
+    a = run_gpu(c, 13, 150, sv.SV_BATCH, prec)
+    b = run_gpu(c, 13, 150, sv.SV_BATCH, prec, opts={sv.SV_OPT_PREDRAW_PAULI: 0})
+    for op in c.random_ops():
+        assert np.array_equal(a["sel"][op], b["sel"][op]), op
+        assert np.array_equal(a["thr"][op], b["thr"][op]), op
+    assert np.array_equal(a["keys"], b["keys"])
+    assert a["stats"]["launches"] < b["stats"]["launches"]
+    compare_shots(c, 13, a, range(0, 150, 7), prec)
