@@ -130,6 +130,7 @@ struct DevBatch {
     int32_t* br_count;
     uint64_t* br_clbits;
     int32_t* br_parent;
+    int32_t* br_big;           // op whose big-branch decide changed the branch's count (-1: none)
     int32_t* br_sel;           // [MAX_PEND][cap_br]
     double* br_scale;          // [MAX_PEND][cap_br]
     uint32_t* perm;            // shot ids, grouped by branch
@@ -172,7 +173,8 @@ cudaError_t launch_init(const DevBatch& d, int prec, int n_init_slots, int grid,
 cudaError_t launch_reset(const DevBatch& d, int mode_branch, int n_shots_run, int from_wait, int grid,
                          cudaStream_t s);
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s);
-cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int n_sm, cudaStream_t s);
+cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int n_sm, cudaStream_t s, cudaStream_t side,
+                          cudaEvent_t ev_fork, cudaEvent_t ev_join);
 cudaError_t launch_predraw(const DevBatch& d, int n_rows, int table, int n_shots, int grid, cudaStream_t s);
 cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s);
 cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s);

@@ -1506,7 +1506,7 @@ __device__ void log_fork_events(const DevBatch& d, const DecideDesc& dd, const D
 // of groups.  Which branch gets which id depends on timing, but no result
 // does: a branch's arithmetic never depends on its id or slot.  k_copy folds
 // the counters into the branch count.
-__device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, int start, DecTab& T) {
+__device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, int start, DecTab& T, bool big) {
     const int lane = threadIdx.x & 31;
     const int NK = dd.nk;
     // group index of tuples lane and lane + 32 (-1: no shots)
@@ -1543,7 +1543,13 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
         if (g > 1 && !dd.fork) set_err(d, ERR_GROUPS, b);
         if (forks) {
             j0 = atomicAdd(&d.ctl[CTL_NALLOC], g - 1);
-            d.br_count[b] = T.bincnt[r0];
+            if (big) {
+                // the small-branch kernel runs at the same time: mark the
+                // branch before its count may drop to its range
+                *reinterpret_cast<volatile int32_t*>(&d.br_big[b]) = (int32_t)dd.op;
+                __threadfence();
+            }
+            *reinterpret_cast<volatile int32_t*>(&d.br_count[b]) = T.bincnt[r0];
             if (d.fork_log) T.leaf[r0] = b;
         }
     }
@@ -1565,6 +1571,7 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
             d.br_count[child] = cnt;
             d.br_clbits[child] = clbits_of(r);
             d.br_parent[child] = b;
+            d.br_big[child] = -1;
             for (int q = 0; q < dd.pend; ++q) {  // earlier pending choices of the parent
                 d.br_sel[(int64_t)q * d.cap_br + child] = d.br_sel[(int64_t)q * d.cap_br + b];
                 d.br_scale[(int64_t)q * d.cap_br + child] = d.br_scale[(int64_t)q * d.cap_br + b];
@@ -1708,7 +1715,7 @@ __global__ void __launch_bounds__(DEC_THREADS, 1) k_decide_big(DevBatch d, const
                 }
                 __syncthreads();
             }
-            if (warp == 0) decide_groups(d, dd, b, start, T);
+            if (warp == 0) decide_groups(d, dd, b, start, T, true);
         }
     }
 }
@@ -1726,8 +1733,11 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
     DecTab& T = tabs[warp];
     const int gw = blockIdx.x * DECS_WARPS + warp, nw = gridDim.x * DECS_WARPS;
     for (int b = gw; b < n_br; b += nw) {
-        const int cnt = d.br_count[b];
+        const int cnt = *reinterpret_cast<const volatile int32_t*>(&d.br_count[b]);
         if (cnt > DEC_SMALL) continue;
+        // a count the big kernel has just lowered comes after its mark
+        __threadfence();
+        if (*reinterpret_cast<const volatile int32_t*>(&d.br_big[b]) == (int32_t)dd.op) continue;
         const int slot = d.br_slot[b], start = d.br_start[b];
         uint32_t sh[2];
         sh[0] = lane < cnt ? d.perm[start + lane] : 0u;
@@ -1769,7 +1779,7 @@ __global__ void __launch_bounds__(DECS_WARPS * 32) k_decide_small(DevBatch d, co
                 __syncwarp();
             }
         }
-        decide_groups(d, dd, b, start, T);
+        decide_groups(d, dd, b, start, T, false);
         __syncwarp();
     }
 }
@@ -1957,6 +1967,7 @@ __global__ void __launch_bounds__(256) k_reset(DevBatch d, int branch_mode, int 
         d.br_count[b] = branch_mode ? n_run : 1;
         d.br_clbits[b] = 0;
         d.br_parent[b] = -1;
+        d.br_big[b] = -1;
         for (int q = 0; q < MAX_PEND; ++q) {
             d.br_sel[(int64_t)q * d.cap_br + b] = 0;
             d.br_scale[(int64_t)q * d.cap_br + b] = 1.0;
@@ -2058,16 +2069,26 @@ static int resident_blocks(const void* fn, int threads, size_t smem = 0) {
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int n_sm, cudaStream_t s) {
-    // small branches first: a branch the big kernel partitions may end up
-    // with DEC_SMALL shots or fewer and must not be decided twice.  Both
-    // kernels are latency-bound and grid-stride over the branches, so each
-    // launches exactly one resident wave
+cudaError_t launch_decide(const DevBatch& d, const DecideDesc& dd, int n_sm, cudaStream_t s, cudaStream_t side,
+                          cudaEvent_t ev_fork, cudaEvent_t ev_join) {
+    // The two kernels run side by side: the big one on the side stream,
+    // forked from and joined back to the batch's stream (a fork / join that
+    // graph capture records as two parallel nodes).  A big branch whose
+    // count drops to DEC_SMALL or fewer is marked before its count changes,
+    // so the small kernel never decides it again (br_big).  Both kernels are
+    // latency-bound and grid-stride over the branches, so each launches
+    // exactly one resident wave.
     static const int small_per_sm = resident_blocks((const void*)k_decide_small, DECS_WARPS * 32);
     static const int big_per_sm = resident_blocks((const void*)k_decide_big, DEC_THREADS, DEC_BIG_SMEM);
+    cudaError_t e = cudaEventRecord(ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    k_decide_big<<<big_per_sm * n_sm, DEC_THREADS, DEC_BIG_SMEM, side>>>(d, dd);
     k_decide_small<<<small_per_sm * n_sm, DECS_WARPS * 32, 0, s>>>(d, dd);
-    k_decide_big<<<big_per_sm * n_sm, DEC_THREADS, DEC_BIG_SMEM, s>>>(d, dd);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(ev_join, side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join, 0);
+    return e;
 }
 
 

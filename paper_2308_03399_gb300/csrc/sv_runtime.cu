@@ -115,6 +115,10 @@ struct sv_batch_s {
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // side stream and fork / join events: the two decide kernels run side
+    // by side (also inside captured graphs)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t dim = 0;
     size_t amp_bytes = 8, state_bytes = 0;
     int n_slots = 0;
@@ -237,7 +241,7 @@ cudaError_t exec_one(sv_batch b, const Launch& L) {
     case L_INIT: return launch_init(b->dev, prec, L.a0, b->n_sm * 4, b->stream);
     case L_RESET: return launch_reset(b->dev, L.a0, L.a1, L.a2, b->n_sm * 2, b->stream);
     case L_PASS: return launch_pass(b->dev, prec, L.pass, b->threads, pass_grid(b, L.pass), b->stream);
-    case L_DECIDE: return launch_decide(b->dev, L.dec, b->n_sm, b->stream);
+    case L_DECIDE: return launch_decide(b->dev, L.dec, b->n_sm, b->stream, b->side, b->ev_fork, b->ev_join);
     case L_ALLOC: return cudaSuccess;
     case L_COPY: return launch_copy(b->dev, prec, b->n_sm * 4, b->stream);
     case L_FINAL: return launch_final(b->dev, prec, L.fin, b->grid_small, b->stream);
@@ -1264,6 +1268,13 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
         }
         b->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        sv_free_batch(b);
+        return fail(SV_ECUDA, "cannot create the decide side stream");
+    }
     // slots
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
@@ -1306,7 +1317,7 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
     d.states = states;
     const uint64_t S = n_shots;
     if ((st = dalloc(b, &d.ctl, CTL_WORDS)) || (st = dalloc(b, &d.br_slot, S)) || (st = dalloc(b, &d.br_start, S)) ||
-        (st = dalloc(b, &d.br_count, S)) || (st = dalloc(b, &d.br_clbits, S)) || (st = dalloc(b, &d.br_parent, S)) ||
+        (st = dalloc(b, &d.br_count, S)) || (st = dalloc(b, &d.br_clbits, S)) || (st = dalloc(b, &d.br_parent, S)) || (st = dalloc(b, &d.br_big, S)) ||
         (st = dalloc(b, &d.br_sel, S * MAX_PEND)) || (st = dalloc(b, &d.br_scale, S * MAX_PEND)) ||
         (st = dalloc(b, &d.perm, S)) || (st = dalloc(b, &d.perm_tmp, S)) || (st = dalloc(b, &d.shot_sel, S)) ||
         (st = dalloc(b, &d.free_slots, b->n_slots)) || (st = dalloc(b, &d.wait_shots, S)) ||
@@ -1353,6 +1364,12 @@ sv_status sv_free_batch(sv_batch b) {
     if (b->d_ipool) cudaFree(b->d_ipool);
     if (b->h_pool) cudaFreeHost(b->h_pool);
     if (b->h_ipool) cudaFreeHost(b->h_ipool);
+    if (b->side) {
+        cudaStreamSynchronize(b->side);
+        cudaStreamDestroy(b->side);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return SV_OK;
