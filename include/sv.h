@@ -59,7 +59,7 @@ typedef enum {
     SV_ENOMEM = 2,       /* device memory exhausted or budget too small */
     SV_ECUDA = 3,        /* a CUDA runtime call failed */
     SV_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
-    SV_EUNSUPPORTED = 5, /* valid but not supported by this build (size limits) */
+    SV_EUNSUPPORTED = 5, /* valid but beyond the library's limits (sizes, qubit counts) */
     SV_EINTERNAL = 6     /* the device error word was set */
 } sv_status;
 

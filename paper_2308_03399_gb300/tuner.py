@@ -10,7 +10,7 @@ keeps the fastest; it writes every timing to a JSONL log.  The cost model
 is a small MLP (sv_mlp_*, trained by the library's CUDA kernels) that
 predicts log run time from circuit features and a candidate's encoding and
 picks the argmin; the autotuner stays as its fallback (verify=k times the
-model's k best candidates) and as the judge of its picks.
+model's k best candidates) and as the check on its picks.
 """
 from __future__ import annotations
 
