@@ -46,8 +46,8 @@ def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0, amp_err
     """Compare the GPU's logs of `shots` with the oracle.  Local shot s of the
     GPU batch is the oracle's global shot base + s.  Returns counts of
     checked draws and flagged draws; raises AssertionError on an unexplained
-    mismatch.  With amp_errs, each compared shot's largest amplitude error is
-    appended to it."""
+    mismatch.  With amp_errs, each compared shot's (largest absolute, relative
+    L2) amplitude error is appended to it."""
     tol = TOL[prec]
     oc = O.OracleCircuit(circ)
     kinds = circ.to_arrays()["kind"]
@@ -82,7 +82,7 @@ def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0, amp_err
             st = O.run_shot(oc, seed, base + int(s), overrides=overrides, want_state=True)["state"]
             err = np.abs(gpu["amps"][s] - st).max()
             if amp_errs is not None:
-                amp_errs.append(float(err))
+                amp_errs.append((float(err), float(np.linalg.norm(gpu["amps"][s] - st) / np.linalg.norm(st))))
             assert err <= tol["amp"], f"shot {s}: amplitude error {err:.3g} > {tol['amp']}"
     return n_draws, n_flag
 
