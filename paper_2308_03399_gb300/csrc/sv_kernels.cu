@@ -7,22 +7,29 @@
 // is its own branch.  Shot ids are kept grouped by branch in `perm`.
 //
 // Kernels
-//   k_pass          one read + (optional) write of every live state, applying
-//                   a fused sequence of ops (gates; each branch's chosen
-//                   Pauli string, Kraus matrix or measurement projection) in
-//                   shared memory, then reducing the probabilities the next
-//                   random op needs.  Persistent over (branch, chunk) items.
+//   k_pass_reg      a pass over at most 4 qubits: one read and one write of
+//                   every live state, each lane holding whole groups of 2^W
+//                   amplitudes in registers, applying the fused sequence of
+//                   ops (gates; each branch's chosen Pauli string, Kraus
+//                   matrix or measurement projection) and reducing the
+//                   probabilities the next random op needs.  Persistent over
+//                   (branch, unit) items, one warp each.
+//   k_pass          the same for wider passes and measurements, on tiles
+//                   staged in shared memory by bulk asynchronous copies.
 //   k_decide_*      per branch: sum the reduced probabilities in a fixed
-//                   order (float64), draw every shot's Philox number, choose
-//                   its outcome, partition the branch's shots by outcome, and
-//                   give every new outcome group a branch id and a free slot
-//                   (or park its shots on the waiting list when none is left).
+//                   order (float64), draw every shot's Philox number for each
+//                   op of the decide's chain, choose the outcome tuple,
+//                   partition the branch's shots by it, and give every new
+//                   group a branch id and a free slot (or park its shots on
+//                   the waiting list when none is left).  The small- and
+//                   big-branch kernels run side by side.
+//   k_predraw       batch mode: every shot's Pauli choices, before the gates.
 //   k_copy          copy parent states into the new branches' slots.
 //   k_final_*       sampling of all qubits from each branch (sampling measure).
 //
 // Reductions are deterministic: every (branch, chunk) partial is produced by
-// one CTA in a fixed order, so a branch's result does not depend on how many
-// other branches run beside it.
+// one warp or CTA in a fixed order, so a branch's result does not depend on
+// how many other branches run beside it.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -1156,7 +1163,7 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                 return o;
             };
             // the lane's next group goes to L2 ahead of its loads (no
-            // registers held): the pass is latency-bound at 16 warps per SM
+            // registers held): the pass is latency-bound at 20 warps per SM
             if (gi + 32 * REG_PREFETCH < gpu) {
                 const T* gn = gstate + group_base(c * gpu + gi + 32 * REG_PREFETCH);
 #pragma unroll

@@ -3,13 +3,15 @@
 //
 // Scheduler.  Ops are not launched one by one.  Gates and the per-branch
 // application of already-sampled noise/measurement choices are queued as
-// *stages*; a queue is flushed as one k_pass launch (one read and one write of
+// *stages*; a queue is flushed as one pass launch (one read and one write of
 // every live state) when a random op needs probabilities from the current
-// state (Kraus, measurement), when the tile cannot hold more distinct qubits,
+// state (Kraus, measurement), when the pass would exceed its fusion width,
 // or when the state is read.  Pauli choices do not depend on the state
-// (Section IV-A-3) and are sampled without touching it.  Every random op is
-// followed by k_decide, and in shot-branching mode by k_copy, so
-// no host synchronisation happens inside a circuit (Section IV-A-4).
+// (Section IV-A-3) and are sampled without touching it: in batch mode all
+// of them up front (k_predraw), otherwise by a decide.  A decide that
+// follows another with no pass between joins it as a chain, and in
+// shot-branching mode each decide is followed by k_copy, so no host
+// synchronisation happens inside a circuit (Section IV-A-4).
 #include <cuda_runtime.h>
 
 #include <algorithm>
