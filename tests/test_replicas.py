@@ -62,10 +62,10 @@ def _run_ranks(tmp_path, name, n_shots, seed, world=2, mistake="none"):
     return res
 
 
-@pytest.mark.parametrize("name,n_shots", [("mid", 37), ("su4", 64), ("su4", 1)])
-def test_gloo_merge_equals_one_run(tmp_path, name, n_shots):
+@pytest.mark.parametrize("name,n_shots,world", [("mid", 37, 2), ("su4", 64, 2), ("su4", 1, 2), ("mid", 50, 3)])
+def test_gloo_merge_equals_one_run(tmp_path, name, n_shots, world):
     seed = 2024
-    merged = _run_ranks(tmp_path, name, n_shots, seed)
+    merged = _run_ranks(tmp_path, name, n_shots, seed, world=world)
     keys = O.run_shots(replica_worker.circuit(name), seed, 0, n_shots, want_outcomes=False)[0]
     want = O.counts(keys)
     for m in merged:  # every rank holds the merged histogram
