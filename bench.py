@@ -243,6 +243,7 @@ def run_config4(args):
             budget = s * st_bytes + (1 << 20) if mode == sv.SV_BATCH else \
                 max(min(s * st_bytes, rest * nd // br_need), 2 * st_bytes)
             b = sv.Batch(c.n_qubits, s, 1, sv.SV_C64, mode, 4000 + i, mem_budget=budget, stream=stream.cuda_stream)
+            b.set_option(sv.SV_OPT_TILE_BITS, p.get("tile", 0))
             b.set_option(sv.SV_OPT_MAX_ACTIVE, p["max_active"])
             b.set_option(sv.SV_OPT_PASS_PATH, p["path"])
             b.set_option(sv.SV_OPT_JOINT_KRAUS, p["joint"])
@@ -282,7 +283,7 @@ def run_config4(args):
             "cost_model": res}
     if args.autotune:
         t0 = time.perf_counter()
-        small = [c for c in cands if c["joint"] == 1 and c["path"] == 0 and c["max_active"] in (3, 8)]
+        small = [c for c in cands if c["joint"] == 1 and c["path"] == 0 and c["tile"] == 0 and c["max_active"] in (0, 3, 8)]
         tuned = picks_by(lambda c, s, ok: T.autotune(c, s, cands=[x for x in small if x in ok], reps=1)[0])
         line["autotune_search_s"] = time.perf_counter() - t0
         line["autotuned"] = run(tuned, "autotuner")

@@ -4,8 +4,8 @@ The library's run-time decisions are exposed as batch options: batch or
 shot-branching mode (the paper's trade-off, Section V-B and Section VI:
 batching suits few qubits, branching more qubits, and the technique has to
 be chosen per circuit), the fusion width of a pass (SV_OPT_MAX_ACTIVE), the
-pass path (registers or shared-memory tiles) and the joint decision of
-back-to-back Kraus ops.  The autotuner times every candidate on the GPU and
+tile size (SV_OPT_TILE_BITS), the pass path (registers or shared-memory
+tiles) and the joint decision of back-to-back Kraus ops.  The autotuner times every candidate on the GPU and
 keeps the fastest; it writes every timing to a JSONL log.  The cost model
 is a small MLP (sv_mlp_*, trained by the library's CUDA kernels) that
 predicts log run time from circuit features and a candidate's encoding and
@@ -26,13 +26,17 @@ import numpy as np
 from . import sv
 from . import workloads as W
 
-DEFAULT = dict(mode="branch", max_active=8, path=0, joint=1)
+DEFAULT = dict(mode="branch", max_active=0, path=0, joint=1, tile=0)  # the library's defaults
 
 
 def candidates():
+    """Batch or branch mode x fusion width (0: the library's default, all
+    qubits when the state is one tile, else 4) x pass path x joint Kraus
+    decisions x tile size (0: 2^11 amplitudes for complex64; 10: 2^10)."""
     out = []
-    for mode, fuse, path, joint in itertools.product(("batch", "branch"), (3, 5, 8), (0, 1), (1, 0)):
-        out.append(dict(mode=mode, max_active=fuse, path=path, joint=joint))
+    for mode, fuse, path, joint, tile in itertools.product(("batch", "branch"), (0, 3, 5, 8), (0, 1), (1, 0),
+                                                           (0, 10)):
+        out.append(dict(mode=mode, max_active=fuse, path=path, joint=joint, tile=tile))
     return out
 
 
@@ -69,12 +73,17 @@ def features(circ, shots):
     ], np.float32)
 
 
-def encode(cfg):
-    return np.array([1.0 if cfg["mode"] == "branch" else 0.0, cfg["max_active"] / 8.0, float(cfg["path"]),
-                     float(cfg["joint"])], np.float32)
+def encode(cfg, n_qubits):
+    """The configuration as the model sees it: mode, the fusion width and
+    tile size in effect for an n-qubit complex64 state, pass path, joint
+    decisions."""
+    tb = min(n_qubits, cfg.get("tile", 0) or 11)
+    width = cfg["max_active"] or (n_qubits if n_qubits <= tb else 4)
+    return np.array([1.0 if cfg["mode"] == "branch" else 0.0, width / 8.0, float(cfg["path"]),
+                     float(cfg["joint"]), tb / 11.0], np.float32)
 
 
-N_IN = 14
+N_IN = 15
 
 
 def measure(circ, shots, cfg, seed=1, reps=3, warmup=1):
@@ -89,6 +98,7 @@ def measure(circ, shots, cfg, seed=1, reps=3, warmup=1):
             return None
         raise
     try:
+        b.set_option(sv.SV_OPT_TILE_BITS, cfg.get("tile", 0))
         b.set_option(sv.SV_OPT_MAX_ACTIVE, cfg["max_active"])
         b.set_option(sv.SV_OPT_PASS_PATH, cfg["path"])
         b.set_option(sv.SV_OPT_JOINT_KRAUS, cfg["joint"])
@@ -123,7 +133,7 @@ def autotune(circ, shots, cands=None, log=None, seed=1, reps=3):
 
 def dataset(records):
     rows = [r for r in records if r["ms"] is not None]
-    X = np.stack([np.concatenate([np.asarray(r["features"], np.float32), encode(r["cfg"])]) for r in rows])
+    X = np.stack([np.concatenate([np.asarray(r["features"], np.float32), encode(r["cfg"], r["n"])]) for r in rows])
     y = np.log(np.array([r["ms"] for r in rows], np.float32))
     return X, y
 
@@ -152,7 +162,7 @@ class CostModel:
     def predict(self, circ, shots, cands=None):
         cands = cands or candidates()
         f = features(circ, shots)
-        X = np.stack([np.concatenate([f, encode(c)]) for c in cands])
+        X = np.stack([np.concatenate([f, encode(c, circ.n_qubits)]) for c in cands])
         return np.exp(self.mlp.forward(X) + self.mu[0])
 
     def pick(self, circ, shots, cands=None, verify=0, seed=1):

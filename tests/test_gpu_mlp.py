@@ -58,7 +58,7 @@ def test_trained_cost_model_gains_over_fixed_configuration():
     import os
     log = os.path.join(os.path.dirname(T.__file__), "data", "tuner_log_gb300.jsonl")
     recs = [json.loads(ln) for ln in open(log)]
-    cands = [c for c in T.candidates() if c["joint"] == 1 and c["path"] == 0 and c["max_active"] in (3, 8)]
+    cands = [c for c in T.candidates() if c["joint"] == 1 and c["path"] == 0 and c["max_active"] in (0, 3, 8)]
     held = T.training_circuits(seed=21, count=8, max_n=18)
     held = [(c, s) for c, s in held if c.n_qubits >= 10]
     model = T.CostModel(seed=0)
@@ -81,4 +81,4 @@ def test_trained_cost_model_gains_over_fixed_configuration():
 
 
 def json_key(cfg):
-    return (cfg["mode"], cfg["max_active"], cfg["path"], cfg["joint"])
+    return (cfg["mode"], cfg["max_active"], cfg["path"], cfg["joint"], cfg.get("tile", 0))
