@@ -311,23 +311,28 @@ int orc_run_shot(const orc_circuit *c, uint64_t seed, uint64_t shot,
             double u = orc_uniform(seed, shot, (uint32_t)op);
             double sum = 0.0, before = 0.0;
             int64_t chosen = -1, last_nonzero = -1;
-            for (uint64_t j = 0; j < dim; ++j) {
-                double p = creal(psi[j]) * creal(psi[j]) + cimag(psi[j]) * cimag(psi[j]);
-                before = sum;
-                sum += p;
-                if (p > 0) last_nonzero = (int64_t)j;
-                if (u < sum) { chosen = (int64_t)j; break; }
+            int ov = find_override((uint32_t)op, n_ovr, ovr_op, ovr_out);
+            if (ov < 0) {
+                for (uint64_t j = 0; j < dim; ++j) {
+                    double p = creal(psi[j]) * creal(psi[j]) + cimag(psi[j]) * cimag(psi[j]);
+                    before = sum;
+                    sum += p;
+                    if (p > 0) last_nonzero = (int64_t)j;
+                    if (u < sum) { chosen = (int64_t)j; break; }
+                }
+                if (chosen < 0) chosen = last_nonzero >= 0 ? last_nonzero : (int64_t)dim - 1;
+            } else {
+                chosen = ov;
             }
-            if (chosen < 0) {
-                chosen = last_nonzero >= 0 ? last_nonzero : (int64_t)dim - 1;
+            if (ov >= 0 || u >= sum) {
+                /* a forced key, or the fallback: the running sums around the
+                 * key that is actually taken */
                 before = 0.0;
                 for (int64_t j = 0; j < chosen; ++j)
                     before += creal(psi[j]) * creal(psi[j]) + cimag(psi[j]) * cimag(psi[j]);
                 double p = creal(psi[chosen]) * creal(psi[chosen]) + cimag(psi[chosen]) * cimag(psi[chosen]);
                 sum = before + p;
             }
-            int ov = find_override((uint32_t)op, n_ovr, ovr_op, ovr_out);
-            if (ov >= 0) chosen = ov;
             key = (uint64_t)chosen;
             if (outcome) outcome[op] = (int32_t)chosen;
             if (u_log) u_log[op] = u;

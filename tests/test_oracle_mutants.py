@@ -27,6 +27,14 @@ MUTANTS = {
     "norm_drops_imag": ("s += creal(psi[j]) * creal(psi[j]) + cimag(psi[j]) * cimag(psi[j]);",
                         "s += creal(psi[j]) * creal(psi[j]);"),
     "final_off_by_one": ("if (u < sum) { chosen = (int64_t)j; break; }", "if (u < before) { chosen = (int64_t)j; break; }"),
+    "select_fallback_last_entry": ("        double prev = t ? cum[t - 1] : 0.0;\n        if (cum[t] > prev) return t;",
+                                   "        return n - 1;"),
+    "select_not_strict": ("        if (u < cum[t]) return t;", "        if (u <= cum[t]) return t;"),
+    "kraus_fallback_last_entry": ("chosen = last_nonzero >= 0 ? last_nonzero : nt - 1;", "chosen = nt - 1;"),
+    "kraus_not_strict": ("int take = (ov >= 0) ? (i == ov) : (u < sum);", "int take = (ov >= 0) ? (i == ov) : (u <= sum);"),
+    "final_fallback_last_entry": ("if (chosen < 0) chosen = last_nonzero >= 0 ? last_nonzero : (int64_t)dim - 1;",
+                                  "if (chosen < 0) chosen = (int64_t)dim - 1;"),
+    "final_override_keeps_old_sums": ("if (ov >= 0 || u >= sum) {", "if (ov < 0 && u >= sum) {"),
 }
 
 
@@ -43,7 +51,8 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                            str(mut), "-o", str(so), "-lm"])
     env = dict(os.environ, ORACLE_SO=str(so))
     pins = [os.path.join(ROOT, "tests", f) for f in
-            ("test_oracle_philox.py", "test_oracle_gates.py", "test_oracle_noise.py", "test_oracle_dm.py")]
+            ("test_oracle_philox.py", "test_oracle_gates.py", "test_oracle_noise.py", "test_oracle_dm.py",
+             "test_oracle_fallbacks.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *pins],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
