@@ -148,11 +148,14 @@ sv_status sv_free_batch(sv_batch b);
 
 sv_status sv_set_option(sv_batch b, sv_option opt, int64_t value);
 
-/* Section IV-A-1: apply one k-qubit gate (k <= 3) to every live state.
+/* Section IV-A-1: apply one k-qubit gate (1 <= k <= 5: a fused block of
+ * gates given as one dense 2^k x 2^k unitary) to every live state.
  * mat is host, 2^k x 2^k complex float64.  cond_clbit = -1 for an
  * unconditional gate; otherwise shots whose classical bit cond_clbit differs
  * from cond_value are left alone (Section IV-A-5).  SV_EINVAL for repeated or
- * out-of-range qubits or a matrix that is not unitary within 1e-10.        */
+ * out-of-range qubits or a matrix that is not unitary within 1e-10;
+ * SV_EUNSUPPORTED for k > 5 or when the gate's qubits plus qubit 0 exceed
+ * the tile (SV_OPT_TILE_BITS).                                              */
 sv_status sv_apply_gate_batch(sv_batch b, int k, const int *qubits, const double *mat, int cond_clbit,
                               int cond_value);
 
@@ -174,10 +177,17 @@ sv_status sv_sample_noise(sv_batch b, uint32_t op, sv_noise_kind kind, int k, co
  * the measured qubits to |0>.                                              */
 sv_status sv_measure_batch(sv_batch b, uint32_t op, int m, const int *qubits, const int *clbits, int reset);
 
-/* Section IV-B-2: commit the forks of random op `op`.  The sampling calls
- * already commit their forks, so this only checks that `op` was the last
- * random op sampled and returns SV_OK; it exists so that callers written
- * against a sample-then-branch sequence keep working.                       */
+/* Section IV-B-2: commit the forks of random op `op`, the last op sampled.
+ * In shot-branching modes sv_sample_noise / sv_measure_batch draw and log
+ * every shot's choice (sv_get_outcomes sees them) without changing any
+ * branch; sv_branch then groups each branch's shots by their choice, keeps
+ * the group with the smallest choice in the branch's state, and gives every
+ * other group a copy of the state in a free slot (or parks it on the waiting
+ * list).  The fork draws again with the same keys (seed, shot, op), so it
+ * takes exactly the logged choices.  Any later call on the batch commits a
+ * pending fork first, so calling sv_branch is optional.  In SV_BATCH mode
+ * every shot is its own branch and there is nothing to commit.  SV_EINVAL
+ * if `op` is not the last random op sampled.                                */
 sv_status sv_branch(sv_batch b, uint32_t op);
 
 /* Section IV-B-2 / Section I: sample every qubit of every live shot with
@@ -222,10 +232,40 @@ sv_status sv_get_amplitudes(sv_batch b, uint64_t shot, double *out_re_im, uint64
  * cumulative values just below and at the choice.  Synchronises.            */
 sv_status sv_get_outcomes(sv_batch b, uint32_t op, int32_t *per_shot_outcome, double *thresholds);
 
-/* With SV_OPT_LOG: fork events, 5 int64 each: (op, parent branch, child
- * branch or -1 for the waiting list, outcome, shots).  A parent's own
- * continuing group is reported with child == parent.  Synchronises.         */
+/* With SV_OPT_LOG: fork events of the last run (sv_run_circuit, or the
+ * per-op calls since the batch was last started), 5 int64 each: (op, parent
+ * branch, child branch or -1 for the waiting list, outcome, shots).  A
+ * parent's own continuing group is reported with child == parent.
+ * Synchronises.                                                             */
 sv_status sv_get_fork_events(sv_batch b, int64_t *events, uint64_t cap, uint64_t *n_out);
+
+/* Section IV-B-2: with SV_OPT_LOG in shot-branching modes, the branch tree
+ * of the last run with the shot set of every fork.  One record per group of
+ * a fork (a fork splits a node's shots by their sampled outcome of op),
+ * SV_TREE_WORDS int64 each:
+ *   (round, op, parent, child, outcome, shot_offset, shot_count,
+ *    parent_offset, parent_count)
+ *   round    0 for the first pass through the circuit, r for the r-th
+ *            restart of the waiting list (each restart is a new root: the
+ *            shots that waited)
+ *   parent   branch id (within the round) of the forking node; shots
+ *            [parent_offset .. +parent_count) are the node's shot set
+ *   child    branch id of the group (== parent for the group that keeps the
+ *            parent's state, -1 for a group parked on the waiting list)
+ *   shots[shot_offset .. shot_offset + shot_count) are the group's shots
+ *            (local shot ids)
+ * Records come in decide order (the ops of a chained decide together).  A
+ * decide that chains several ops assigns slots to its final groups, so a
+ * group of an earlier op of the chain may be parked only in part: its
+ * record then shows child -1 (or the branch of its first part) and the
+ * records of the later op split it.
+ * records: host, cap records; shots: host, shot_cap ids.  With both NULL
+ * the call only reports *n_records and *n_shot_ids.  SV_EINVAL when a
+ * buffer is too small, SV_EUNSUPPORTED when the device log overflowed
+ * (8 x shots + 4096 events).  Synchronises.                                 */
+#define SV_TREE_WORDS 9
+sv_status sv_get_branch_tree(sv_batch b, int64_t *records, uint64_t cap, uint64_t *n_records, uint32_t *shots,
+                             uint64_t shot_cap, uint64_t *n_shot_ids);
 
 /* Live branches and run statistics since the previous call.  stats (8
  * doubles): live branches, waiting shots, kernel launches issued, passes,
@@ -248,20 +288,25 @@ sv_status sv_profile(sv_batch b, double *ms, int64_t *launches);
  * chunked float64 prefix), from states and into keys the caller provides:
  *   states   device, n_states consecutive states of 2^n_qubits amplitudes
  *            (float2 for SV_C64, double2 for SV_C128), read only
- *   shots    device, n_states shot ids: state i draws with counter
- *            (shots[i], op)
+ *   shots    device, n_states 64-bit global shot ids: state i draws with
+ *            counter (shots[i], op), as the batch path draws for its shot
+ *            shot_base + s (SV_OPT_SHOT_BASE)
  *   keys     device, n_states outputs (sampled indices)
  *   cuda_stream  stream to run on (NULL = default stream); asynchronous
+ * Draws within rounding distance of a cumulative threshold are not flagged
+ * here (the batch path's log reports the thresholds; this call does not).
  * Scratch is a static 1 MiB device array (131072 float64 partial sums) that
  * every GPU loading the library holds until exit; n_states x chunks (chunks
  * = min(max(2^n_qubits / 2048, 1), 1024)) above that limit gives
  * SV_EINVAL.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the array and it keeps
+ * address (cudaGetSymbolAddress) with that device current and keeps it for
+ * the life of the process; make that first call before any stream capture,
+ * and do not call again after a cudaDeviceReset (the module, and with it the
+ * array, may then sit elsewhere).  All calls share the array and it keeps
  * the last call's contents (every value read is written first in the same
  * call); calls whose work overlaps on the GPU race on it.                    */
 sv_status sv_final_sample_noalloc(const void *states, sv_prec prec, int n_qubits, uint32_t n_states,
-                                  const uint32_t *shots, uint64_t seed, uint32_t op, uint64_t *keys,
+                                  const uint64_t *shots, uint64_t seed, uint32_t op, uint64_t *keys,
                                   void *cuda_stream);
 
 /* Learned cost model ------------------------------------------------------

@@ -19,6 +19,11 @@ constexpr int MAX_RED = 16;        // probabilities reduced by one pass (Kraus t
 constexpr int MAX_CHUNKS = 1024;   // reduction partials per state
 constexpr int MAX_STAGE_Q = 4;     // qubits of one stage
 constexpr int MAT_SMEM = 1024;     // complex matrix entries staged in shared memory per pass
+// fork log record: op, parent branch, child branch (-1: waiting list), outcome,
+// shots, first perm position of the group's shots at the fork, first perm
+// position and shots of the forking node
+constexpr int FORK_WORDS = 8;
+constexpr int MAX_GATE_Q = 5;      // qubits of one dense gate (a 5-qubit matrix fills MAT_SMEM alone)
 
 // Stage kinds: what one fused op does to a group of 2^k amplitudes.
 enum : int32_t {
@@ -92,6 +97,8 @@ struct DecideDesc {
     int32_t pend;
     int32_t chunks;            // partials to sum
     int32_t fork;              // shot-branching on
+    int32_t sample_only;       // draw and log the choices, change no branch (per-op
+                               // calls in shot-branching mode: sv_branch commits)
     int32_t m;                 // measured qubits
     int32_t clbit[MAX_STAGE_Q];
     int32_t r2;                // joint Kraus: terms of the second op (partials stride)
@@ -145,7 +152,7 @@ struct DevBatch {
     uint64_t* keys;            // per shot id
     uint8_t* pre_sel;          // pre-drawn Pauli choices, [row][shot id] (batch mode)
     int32_t* pos_branch;       // branch owning each perm position (final sampling)
-    int64_t* fork_log;         // 5 per event, nullable
+    int64_t* fork_log;         // FORK_WORDS per event, nullable
     int32_t fork_log_cap;
     int32_t* pass_log;         // live branches seen by each pass (profiling), nullable
     int32_t pass_log_cap;

@@ -99,34 +99,10 @@ template <> struct Acc<float> {
     __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
 };
 
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
-// multiplies with the published multipliers and Weyl key increments.
-// key = (seed lo, seed hi), counter = (shot lo, shot hi, op, 0).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t philox_k53(uint64_t seed, uint64_t shot, uint32_t op) {
-    uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
-    uint32_t w0 = (uint32_t)shot, w1 = (uint32_t)(shot >> 32), w2 = op, w3 = 0u;
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint32_t a_hi = __umulhi(0xD2511F53u, w0), a_lo = 0xD2511F53u * w0;
-        const uint32_t b_hi = __umulhi(0xCD9E8D57u, w2), b_lo = 0xCD9E8D57u * w2;
-        const uint32_t n0 = b_hi ^ w1 ^ key0;
-        const uint32_t n2 = a_hi ^ w3 ^ key1;
-        w0 = n0;
-        w1 = b_lo;
-        w2 = n2;
-        w3 = a_lo;
-        key0 += 0x9E3779B9u;
-        key1 += 0xBB67AE85u;
-    }
-    return ((((uint64_t)w0) << 32) | (uint64_t)w1) >> 11;  // top 53 bits of words 0, 1
-}
-
-// the uniform draw u = k * 2^-53 in [0, 1)
-__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, uint32_t op) {
-    return (double)philox_k53(seed, shot, op) * 0x1.0p-53;
-}
+// Philox4x32-10 draws keyed by (seed; shot, op): svs::philox_k53 /
+// svs::philox_uniform (sv_sample.cuh), shared with sv_noalloc.cu
+using svs::philox_k53;
+using svs::philox_uniform;
 
 // Selection in the integer domain: for u = k * 2^-53, u < c exactly when
 // k < ceil(c * 2^53) (the scaling by 2^53 is exact), so a branch turns its
@@ -287,7 +263,9 @@ __device__ __forceinline__ void stage_dispatch(typename Cplx<R>::T* tile, int tb
     if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
         if (st.k == 1) stage_dense<R, 1>(tile, tb, st.pos, M);
         else if (st.k == 2) stage_dense<R, 2>(tile, tb, st.pos, M);
-        else stage_dense<R, 3>(tile, tb, st.pos, M);
+        else if (st.k == 3) stage_dense<R, 3>(tile, tb, st.pos, M);
+        else if (st.k == 4) stage_dense<R, 4>(tile, tb, st.pos, M);
+        else stage_dense<R, 5>(tile, tb, st.pos, M);
     } else if (st.kind == ST_PAULI_BR) {
         if (st.k == 1) stage_pauli<R, 1>(tile, tb, st.pos, packed);
         else if (st.k == 2) stage_pauli<R, 2>(tile, tb, st.pos, packed);
@@ -1458,10 +1436,15 @@ __device__ int write_choices(const DevBatch& d, const DecideDesc& dd, const DecT
 // fork events of one branch's decide, per op of the chain (one thread): at
 // each op, every node (shots sharing the earlier ops' outcomes) whose shots
 // take two or more outcomes logs one event per outcome: (op, node's branch,
-// the outcome's branch, outcome, shots).  A node's branch is that of its
-// first outcome tuple, so the events are those of deciding the ops one at a
-// time.
-__device__ void log_fork_events(const DevBatch& d, const DecideDesc& dd, const DecTab& T) {
+// the outcome's branch, outcome, shots, first perm position, and the node's
+// first perm position and shots).  A node's
+// branch is that of its first outcome tuple, so the events are those of
+// deciding the ops one at a time.  The branch's shots are partitioned in
+// tuple order, so a node's and an outcome's shots are contiguous perm ranges
+// that start at their first tuple's group; later forks only reorder shots inside
+// their own branch's range, so the range keeps this set of shot ids until
+// the waiting list restarts.
+__device__ void log_fork_events(const DevBatch& d, const DecideDesc& dd, const DecTab& T, int start) {
     const int M = 1 + dd.n_tail;
     int stride = dd.nk;
     for (int m = 0; m < M; ++m) {
@@ -1470,7 +1453,7 @@ __device__ void log_fork_events(const DevBatch& d, const DecideDesc& dd, const D
         const int node = stride;  // keys per node at this level
         stride /= Rm;             // keys per outcome of this op within a node
         for (int n0 = 0; n0 < dd.nk; n0 += node) {
-            int distinct = 0, first = -1;
+            int distinct = 0, first = -1, total = 0;
             for (int o = 0; o < Rm; ++o) {
                 int c = 0, f = -1;
                 for (int k = n0 + o * stride; k < n0 + (o + 1) * stride; ++k)
@@ -1480,6 +1463,7 @@ __device__ void log_fork_events(const DevBatch& d, const DecideDesc& dd, const D
                     }
                 if (c > 0) {
                     ++distinct;
+                    total += c;
                     if (first < 0) first = f;
                 }
             }
@@ -1495,8 +1479,11 @@ __device__ void log_fork_events(const DevBatch& d, const DecideDesc& dd, const D
                 if (c == 0) continue;
                 const int e = atomicAdd(&d.ctl[CTL_NFORK], 1);
                 if (e < d.fork_log_cap) {
-                    int64_t* ev = d.fork_log + 5 * (int64_t)e;
+                    int64_t* ev = d.fork_log + FORK_WORDS * (int64_t)e;
                     ev[0] = op; ev[1] = parent; ev[2] = T.leaf[f]; ev[3] = o; ev[4] = c;
+                    ev[5] = start + T.binbase[f];
+                    ev[6] = start + T.binbase[first];  // the node's own range
+                    ev[7] = total;
                 }
             }
         }
@@ -1514,6 +1501,7 @@ __device__ void log_fork_events(const DevBatch& d, const DecideDesc& dd, const D
 // does: a branch's arithmetic never depends on its id or slot.  k_copy folds
 // the counters into the branch count.
 __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, int start, DecTab& T, bool big) {
+    if (dd.sample_only) return;  // the choices are drawn and logged; the commit forks
     const int lane = threadIdx.x & 31;
     const int NK = dd.nk;
     // group index of tuples lane and lane + 32 (-1: no shots)
@@ -1592,7 +1580,7 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
     }
     if (d.fork_log) {
         __syncwarp();
-        if (lane == 0) log_fork_events(d, dd, T);
+        if (lane == 0) log_fork_events(d, dd, T, start);
         __syncwarp();
     }
 }

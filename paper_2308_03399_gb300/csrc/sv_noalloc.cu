@@ -36,25 +36,6 @@ static __device__ __align__(256) double na_scratch[NA_SCRATCH_DOUBLES];
 double* na_scratch_ptr[NA_MAX_DEVICES] = {};
 std::mutex na_mutex;
 
-// Philox4x32-10 (Salmon et al., SC'11), key = seed, counter = (shot, op, 0)
-__device__ __forceinline__ double na_uniform(uint64_t seed, uint64_t shot, uint32_t op) {
-    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    uint32_t c0 = (uint32_t)shot, c1 = (uint32_t)(shot >> 32), c2 = op, c3 = 0u;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t h0 = __umulhi(0xD2511F53u, c0), l0 = 0xD2511F53u * c0;
-        const uint32_t h1 = __umulhi(0xCD9E8D57u, c2), l1 = 0xCD9E8D57u * c2;
-        const uint32_t n0 = h1 ^ c1 ^ k0, n2 = h0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = l1;
-        c2 = n2;
-        c3 = l0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return (double)(((((uint64_t)c0) << 32) | (uint64_t)c1) >> 11) * 0x1.0p-53;
-}
-
 // per (state, chunk): sum of |psi_j|^2 over the chunk's contiguous range
 template <class R>
 __global__ void __launch_bounds__(256) na_partials(const typename svs::Cx<R>::T* states, int64_t dim, int chunks,
@@ -79,11 +60,11 @@ __global__ void __launch_bounds__(256) na_cum(int chunks, int n_states, double* 
 // per state (one warp): its key
 template <class R>
 __global__ void __launch_bounds__(256) na_sample(const typename svs::Cx<R>::T* states, int64_t dim, int chunks,
-                                                int n_states, const uint32_t* shots, uint64_t seed, uint32_t op,
+                                                int n_states, const uint64_t* shots, uint64_t seed, uint32_t op,
                                                 uint64_t* keys, const double* scratch) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int st = gw; st < n_states; st += nw) {
-        const double u = na_uniform(seed, shots[st], op);
+        const double u = svs::philox_uniform(seed, shots[st], op);
         double lo, hi;
         const int64_t key = svs::sample_warp<R>(states + (int64_t)st * dim, dim, chunks,
                                                 scratch + (int64_t)st * chunks, 1, u, &lo, &hi);
@@ -94,7 +75,7 @@ __global__ void __launch_bounds__(256) na_sample(const typename svs::Cx<R>::T* s
 }  // namespace
 
 extern "C" sv_status sv_final_sample_noalloc(const void* states, sv_prec prec, int n_qubits, uint32_t n_states,
-                                             const uint32_t* shots, uint64_t seed, uint32_t op, uint64_t* keys,
+                                             const uint64_t* shots, uint64_t seed, uint32_t op, uint64_t* keys,
                                              void* cuda_stream) {
     if (!states || !shots || !keys) {
         sv::set_last_error("sv_final_sample_noalloc: states, shots and keys must be device pointers");

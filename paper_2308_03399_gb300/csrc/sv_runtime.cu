@@ -149,6 +149,10 @@ struct sv_batch_s {
     std::vector<Launch>* rec = nullptr;
     bool started = false;
     uint32_t last_random = 0xffffffffu;
+    // per-op calls in shot-branching mode: the decide of the last random op
+    // has drawn its choices; sv_branch (or the next call) commits its forks
+    bool uncommitted = false;
+    Launch commit;
     // logging
     bool log = false;
     std::map<uint32_t, std::pair<int32_t*, double*>> logs;
@@ -184,6 +188,15 @@ struct sv_batch_s {
     int pre_cap = 0;               // rows the device table holds
     std::map<int, int> reg_occ;
     int slot_limit = 0;
+    // branch tree of the last run (with SV_OPT_LOG in shot-branching modes):
+    // per round (the first pass, then each waiting-list restart) the fork
+    // events logged by its end and the shot permutation as it stood then
+    struct TreeRound {
+        int64_t fork_end;
+        int n_run;
+        std::vector<uint32_t> perm;
+    };
+    std::vector<TreeRound> tree;
 };
 
 namespace {
@@ -381,6 +394,16 @@ int reg_width(sv_batch b, const RedSpec& red, uint64_t act) {
     if (red.kind == RED_BINS) return 0;
     if (red.kind == RED_FORMS && red.R > 4) return 0;
     if (red.kind == RED_FORMS && red.k != 1 && red.diag_off < 0) return 0;
+    // the per-warp matrix copies must fit the default 48 KB of dynamic
+    // shared memory of the register kernels; longer stage lists take tiles
+    PassDesc probe;
+    probe.mat_elems = 0;
+    for (const PendStage& ps : b->pend)
+        probe.mat_elems += (ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) ? 1 << (2 * ps.k)
+                                                                          : (ps.kind == ST_PROJ_BR ? 1 : 0);
+    if (red.kind == RED_FORMS) probe.mat_elems += red.diag_off >= 0 ? red.R << red.k : red.R << (2 * red.k);
+    const int prec = b->prec == SV_C128;
+    if (pass_reg_smem_bytes(prec, probe, pass_reg_threads(prec)) > 48 * 1024) return 0;
     return wp;
 }
 
@@ -504,8 +527,14 @@ void add_stage(sv_batch b, const PendStage& s) {
     if (s.kind == ST_DENSE || s.kind == ST_DENSE_BR) b->mat_used += 1 << (2 * s.k);
 }
 
+sv_status tree_begin(sv_batch b);
+
 sv_status ensure_started(sv_batch b) {
     if (b->started) return SV_OK;
+    if (!b->rec) {  // per-op calls: a new run, a new fork log
+        sv_status st = tree_begin(b);
+        if (st) return st;
+    }
     const int branch = b->branch;
     Launch r;
     r.type = L_RESET;
@@ -623,6 +652,19 @@ sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cu
         for (int t = 0; t < R; ++t) d.cum[t] = cum[t];
     sv_status st = get_log(b, op, &d.log_sel, &d.log_thr);
     if (st) return st;
+    if (b->branch && !b->rec) {
+        // per-op call in shot-branching mode (Section IV-B-2's sample, then
+        // branch): this launch draws and logs every shot's choice; the same
+        // keyed draws fork the branches when sv_branch commits
+        b->commit = L;
+        d.sample_only = 1;
+        d.fork = 0;
+        st = emit(b, std::move(L));
+        if (st) return st;
+        b->uncommitted = true;
+        b->last_random = op;
+        return SV_OK;
+    }
     st = emit(b, std::move(L));
     if (st) return st;
     if (b->branch) {
@@ -633,6 +675,17 @@ sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cu
     }
     b->last_random = op;
     return SV_OK;
+}
+
+// fork the branches of the last sampled op (per-op calls, shot-branching)
+sv_status commit_forks(sv_batch b) {
+    if (!b->uncommitted) return SV_OK;
+    b->uncommitted = false;
+    sv_status st = exec(b, b->commit);
+    if (st) return st;
+    Launch c;
+    c.type = L_COPY;
+    return exec(b, c);
 }
 
 bool is_unitary(const double* m, int k, double tol) {
@@ -652,8 +705,13 @@ bool is_unitary(const double* m, int k, double tol) {
 sv_status op_gate(sv_batch b, int k, const int* q, const double* mat, int cond_clbit, int cond_val) {
     sv_status st = check_qubits(b, k, q);
     if (st) return st;
-    if (k < 1 || k > 3) return fail(SV_EUNSUPPORTED, "gates act on 1 to 3 qubits");
+    if (k < 1 || k > MAX_GATE_Q) return fail(SV_EUNSUPPORTED, "gates act on 1 to 5 qubits");
     if (!mat) return fail(SV_EINVAL, "matrix is NULL");
+    {
+        uint64_t gq = 1ull;  // a tile always holds qubit 0
+        for (int j = 0; j < k; ++j) gq |= 1ull << q[j];
+        if (__builtin_popcountll(gq) > b->tb) return fail(SV_EUNSUPPORTED, "the gate's qubits do not fit one tile");
+    }
     if (cond_clbit >= b->n_clbits || cond_clbit < -1) return fail(SV_EINVAL, "condition bit out of range");
     if (!is_unitary(mat, k, 1e-10)) return fail(SV_EINVAL, "gate matrix is not unitary");
     if ((st = ensure_started(b))) return st;
@@ -958,6 +1016,29 @@ sv_status read_ctl(sv_batch b, int32_t* ctl) {
     return SV_OK;
 }
 
+// the end of a round of a logged shot-branching run: keep the shot
+// permutation (a fork event's shot set is a range of it, valid until the
+// waiting list restarts)
+sv_status tree_snapshot(sv_batch b, const int32_t* ctl, int n_run) {
+    if (!b->log || !b->branch || !b->dev.fork_log) return SV_OK;
+    sv_batch_s::TreeRound r;
+    r.fork_end = ctl[CTL_NFORK];
+    r.n_run = n_run;
+    r.perm.resize(b->n_shots);
+    CU(cudaMemcpyAsync(r.perm.data(), b->dev.perm, b->n_shots * 4, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    b->tree.push_back(std::move(r));
+    return SV_OK;
+}
+
+// a logged run starts a new fork log and branch tree
+sv_status tree_begin(sv_batch b) {
+    b->tree.clear();
+    if (!b->log || !b->dev.fork_log) return SV_OK;
+    CU(cudaMemsetAsync(b->dev.ctl + CTL_NFORK, 0, 4, b->stream));
+    return SV_OK;
+}
+
 // one op of a flattened circuit, batched modes
 sv_status circuit_op(sv_batch b, const sv_circuit* c, int i) {
     const int kind = c->kind[i], k = c->nq[i];
@@ -1194,11 +1275,14 @@ sv_status record_circuit(sv_batch b, const sv_circuit* c, std::vector<Launch>& l
 // restart the waiting list of a shot-branching batch until it is empty
 // (Section IV-B-2), launching one by one
 sv_status drain_waiting(sv_batch b, const std::vector<Launch>& launches) {
+    int n_run = (int)b->n_shots;
     for (;;) {
         int32_t ctl[CTL_WORDS];
         sv_status st = read_ctl(b, ctl);
         if (st) return st;
+        if ((st = tree_snapshot(b, ctl, n_run))) return st;
         if (ctl[CTL_ERR] || ctl[CTL_NWAIT] == 0) return SV_OK;
+        n_run = ctl[CTL_NWAIT];
         Launch r;
         r.type = L_RESET;
         r.a0 = 1;
@@ -1392,8 +1476,8 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
     switch (opt) {
     case SV_OPT_LOG:
         if (v && !b->dev.fork_log) {
-            b->dev.fork_log_cap = (int)std::min<uint64_t>(4 * b->n_shots + 1024, 1 << 24);
-            sv_status st = dalloc(b, &b->dev.fork_log, 5 * (size_t)b->dev.fork_log_cap);
+            b->dev.fork_log_cap = (int)std::min<uint64_t>(8 * b->n_shots + 4096, 1 << 24);
+            sv_status st = dalloc(b, &b->dev.fork_log, FORK_WORDS * (size_t)b->dev.fork_log_cap);
             if (st) return st;
         }
         b->log = v != 0;
@@ -1440,6 +1524,7 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
 
 sv_status sv_apply_gate_batch(sv_batch b, int k, const int* qubits, const double* mat, int cond_clbit, int cond_value) {
     if (!b) return fail(SV_EINVAL, "batch is NULL");
+    if (sv_status cs = commit_forks(b)) return cs;
     if (b->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "plain mode runs whole circuits (sv_run_circuit)");
     sv_status st = op_gate(b, k, qubits, mat, cond_clbit, cond_value);
     if (st) return st;
@@ -1449,6 +1534,7 @@ sv_status sv_apply_gate_batch(sv_batch b, int k, const int* qubits, const double
 sv_status sv_sample_noise(sv_batch b, uint32_t op, sv_noise_kind kind, int k, const int* qubits, int n_terms,
                           const double* cum_probs, const char* paulis, const double* kraus) {
     if (!b) return fail(SV_EINVAL, "batch is NULL");
+    if (sv_status cs = commit_forks(b)) return cs;
     if (b->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "plain mode runs whole circuits (sv_run_circuit)");
     if (kind == SV_NOISE_PAULI) return op_pauli(b, op, k, qubits, n_terms, cum_probs, paulis);
     if (kind == SV_NOISE_KRAUS) return op_kraus(b, op, k, qubits, n_terms, kraus);
@@ -1457,6 +1543,7 @@ sv_status sv_sample_noise(sv_batch b, uint32_t op, sv_noise_kind kind, int k, co
 
 sv_status sv_measure_batch(sv_batch b, uint32_t op, int m, const int* qubits, const int* clbits, int reset) {
     if (!b) return fail(SV_EINVAL, "batch is NULL");
+    if (sv_status cs = commit_forks(b)) return cs;
     if (b->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "plain mode runs whole circuits (sv_run_circuit)");
     return op_measure(b, op, m, qubits, clbits, reset);
 }
@@ -1464,7 +1551,7 @@ sv_status sv_measure_batch(sv_batch b, uint32_t op, int m, const int* qubits, co
 sv_status sv_branch(sv_batch b, uint32_t op) {
     if (!b) return fail(SV_EINVAL, "batch is NULL");
     if (b->last_random != op) return fail(SV_EINVAL, "op is not the last random op sampled");
-    return SV_OK;
+    return commit_forks(b);
 }
 
 sv_status sv_get_keys(sv_batch b, uint64_t* keys) {
@@ -1509,6 +1596,7 @@ static sv_status histogram(sv_batch b, uint64_t* keys, uint64_t* counts, uint64_
 sv_status sv_counts(sv_batch b, uint32_t final_op, uint64_t* keys, uint64_t* counts, uint64_t cap, uint64_t* n_out) {
     if (!b || !keys || !counts || !n_out) return fail(SV_EINVAL, "NULL argument");
     if (b->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "plain mode runs whole circuits (sv_run_circuit)");
+    if (sv_status cs = commit_forks(b)) return cs;
     sv_status st = op_final(b, final_op);
     if (st) return st;
     if ((st = check_device_error(b))) return st;
@@ -1517,6 +1605,7 @@ sv_status sv_counts(sv_batch b, uint32_t final_op, uint64_t* keys, uint64_t* cou
 
 sv_status sv_waiting(sv_batch b, uint64_t* n_waiting) {
     if (!b || !n_waiting) return fail(SV_EINVAL, "NULL argument");
+    if (sv_status cs = commit_forks(b)) return cs;
     int32_t ctl[CTL_WORDS];
     sv_status st = read_ctl(b, ctl);
     if (st) return st;
@@ -1529,7 +1618,7 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
     if (c->n_qubits != b->n) return fail(SV_EINVAL, "circuit qubit count differs from the batch");
     if (c->n_clbits > b->n_clbits) return fail(SV_EINVAL, "circuit needs more classical bits than the batch");
     sv_status st;
-    if (!b->pend.empty()) return fail(SV_EINVAL, "per-op calls are in progress on this batch");
+    if (!b->pend.empty() || b->uncommitted) return fail(SV_EINVAL, "per-op calls are in progress on this batch");
     if (b->mode == SV_PLAIN) {
         b->started = true;
         if ((st = reset_pool(b))) return st;
@@ -1550,6 +1639,7 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
     const int branch = b->branch;
     int from_wait = 0;
     int n_run = (int)b->n_shots;
+    if ((st = tree_begin(b))) return st;
     for (int round = 0;; ++round) {
         Launch r;
         r.type = L_RESET;
@@ -1599,6 +1689,7 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
         if (!branch) break;
         int32_t ctl[CTL_WORDS];
         if ((st = read_ctl(b, ctl))) return st;
+        if ((st = tree_snapshot(b, ctl, n_run))) return st;
         if (ctl[CTL_ERR]) break;
         if (ctl[CTL_NWAIT] == 0) break;
         // waiting list (Section IV-B-2): restart its shots from |0...0>
@@ -1651,6 +1742,8 @@ sv_status sv_run_circuits(sv_batch* bs, const sv_circuit* const* cs, int n, int 
             L.insert(L.end(), ops.begin(), ops.end());
         }
     }
+    for (int i = 0; i < n; ++i)
+        if ((st = tree_begin(bs[i]))) return st;
     if (use_graph) {
         if (!cached) {
             if (b0->multi_exec) {
@@ -1707,6 +1800,7 @@ sv_status sv_get_amplitudes(sv_batch b, uint64_t shot, double* out, uint64_t len
     if (!b || !out) return fail(SV_EINVAL, "NULL argument");
     if (len != (uint64_t)b->dim) return fail(SV_EINVAL, "len must be 2^n");
     if (shot >= b->n_shots) return fail(SV_EINVAL, "shot out of range");
+    if (sv_status cs = commit_forks(b)) return cs;
     sv_status st = upload_pool(b);
     if (st) return st;
     if ((st = flush(b))) return st;
@@ -1754,6 +1848,7 @@ sv_status sv_get_outcomes(sv_batch b, uint32_t op, int32_t* sel, double* thr) {
 
 sv_status sv_get_fork_events(sv_batch b, int64_t* ev, uint64_t cap, uint64_t* n_out) {
     if (!b || !n_out) return fail(SV_EINVAL, "NULL argument");
+    if (sv_status cs = commit_forks(b)) return cs;
     if (!b->dev.fork_log) return fail(SV_EINVAL, "enable SV_OPT_LOG first");
     int32_t ctl[CTL_WORDS];
     sv_status st = read_ctl(b, ctl);
@@ -1762,8 +1857,74 @@ sv_status sv_get_fork_events(sv_batch b, int64_t* ev, uint64_t cap, uint64_t* n_
     *n_out = n;
     if (n > cap) return fail(SV_EINVAL, "cap too small");
     if (n && ev) {
-        CU(cudaMemcpyAsync(ev, b->dev.fork_log, n * 5 * 8, cudaMemcpyDeviceToHost, b->stream));
+        std::vector<int64_t> raw(n * FORK_WORDS);
+        CU(cudaMemcpyAsync(raw.data(), b->dev.fork_log, n * FORK_WORDS * 8, cudaMemcpyDeviceToHost, b->stream));
         CU(cudaStreamSynchronize(b->stream));
+        for (uint64_t e = 0; e < n; ++e)
+            for (int w = 0; w < 5; ++w) ev[5 * e + w] = raw[FORK_WORDS * e + w];
+    }
+    return SV_OK;
+}
+
+sv_status sv_get_branch_tree(sv_batch b, int64_t* records, uint64_t cap, uint64_t* n_records, uint32_t* shots,
+                             uint64_t shot_cap, uint64_t* n_shot_ids) {
+    if (!b || !n_records || !n_shot_ids) return fail(SV_EINVAL, "NULL argument");
+    if (!b->dev.fork_log) return fail(SV_EINVAL, "enable SV_OPT_LOG first");
+    if (!b->branch) return fail(SV_EINVAL, "the branch tree exists in shot-branching modes only");
+    if (sv_status cs = commit_forks(b)) return cs;
+    int32_t ctl[CTL_WORDS];
+    sv_status st = read_ctl(b, ctl);
+    if (st) return st;
+    // per-op calls (no sv_run_circuit): one round, the permutation as it is now
+    std::vector<sv_batch_s::TreeRound> live;
+    const std::vector<sv_batch_s::TreeRound>* rounds = &b->tree;
+    if (b->tree.empty()) {
+        sv_batch_s::TreeRound r;
+        r.fork_end = ctl[CTL_NFORK];
+        r.n_run = (int)b->n_shots;
+        r.perm.resize(b->n_shots);
+        CU(cudaMemcpyAsync(r.perm.data(), b->dev.perm, b->n_shots * 4, cudaMemcpyDeviceToHost, b->stream));
+        CU(cudaStreamSynchronize(b->stream));
+        live.push_back(std::move(r));
+        rounds = &live;
+    }
+    const int64_t n_ev = rounds->back().fork_end;
+    if (n_ev > b->dev.fork_log_cap) return fail(SV_EUNSUPPORTED, "the fork log overflowed; the tree is incomplete");
+    std::vector<int64_t> raw((size_t)n_ev * FORK_WORDS);
+    if (n_ev) {
+        CU(cudaMemcpyAsync(raw.data(), b->dev.fork_log, raw.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+        CU(cudaStreamSynchronize(b->stream));
+    }
+    uint64_t n_ids = 0;
+    for (int64_t e = 0; e < n_ev; ++e) n_ids += (uint64_t)(raw[FORK_WORDS * e + 4] + raw[FORK_WORDS * e + 7]);
+    *n_records = (uint64_t)n_ev;
+    *n_shot_ids = n_ids;
+    if (!records && !shots) return SV_OK;  // size query
+    if (!records || !shots || (uint64_t)n_ev > cap || n_ids > shot_cap)
+        return fail(SV_EINVAL, "records / shots too small for the tree (query the sizes with NULL buffers)");
+    uint64_t off = 0;
+    size_t r = 0;
+    for (int64_t e = 0; e < n_ev; ++e) {
+        while (r + 1 < rounds->size() && e >= (*rounds)[r].fork_end) ++r;
+        const int64_t* ev = &raw[FORK_WORDS * e];
+        const int64_t start = ev[5], cnt = ev[4], pstart = ev[6], pcnt = ev[7];
+        if (start < 0 || cnt < 0 || start + cnt > (int64_t)b->n_shots || pstart < 0 || pcnt < cnt ||
+            pstart + pcnt > (int64_t)b->n_shots)
+            return fail(SV_EINTERNAL, "a fork event's shot range is out of bounds");
+        int64_t* rec = records + SV_TREE_WORDS * e;
+        rec[0] = (int64_t)r;
+        rec[1] = ev[0];
+        rec[2] = ev[1];
+        rec[3] = ev[2];
+        rec[4] = ev[3];
+        rec[5] = (int64_t)off;
+        rec[6] = cnt;
+        rec[7] = (int64_t)(off + cnt);
+        rec[8] = pcnt;
+        const std::vector<uint32_t>& perm = (*rounds)[r].perm;
+        for (int64_t i = 0; i < cnt; ++i) shots[off + i] = perm[start + i];
+        for (int64_t i = 0; i < pcnt; ++i) shots[off + cnt + i] = perm[pstart + i];
+        off += (uint64_t)(cnt + pcnt);
     }
     return SV_OK;
 }

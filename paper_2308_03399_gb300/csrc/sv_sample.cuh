@@ -1,4 +1,5 @@
-// Final sampling building blocks (Section IV-B-2's sampling measure), used by
+// Philox draws and the final sampling building blocks (Section IV-B-2's
+// sampling measure), used by
 // the batch path (sv_kernels.cu) and by sv_final_sample_noalloc
 // (sv_noalloc.cu), so both give the same key for the same state and draw.
 //
@@ -15,6 +16,34 @@
 #include <cstdint>
 
 namespace svs {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies with the published multipliers and Weyl key increments.
+// key = (seed lo, seed hi), counter = (shot lo, shot hi, op, 0); the draw is
+// the top 53 bits of words 0 and 1.
+__device__ __forceinline__ uint64_t philox_k53(uint64_t seed, uint64_t shot, uint32_t op) {
+    uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+    uint32_t w0 = (uint32_t)shot, w1 = (uint32_t)(shot >> 32), w2 = op, w3 = 0u;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t a_hi = __umulhi(0xD2511F53u, w0), a_lo = 0xD2511F53u * w0;
+        const uint32_t b_hi = __umulhi(0xCD9E8D57u, w2), b_lo = 0xCD9E8D57u * w2;
+        const uint32_t n0 = b_hi ^ w1 ^ key0;
+        const uint32_t n2 = a_hi ^ w3 ^ key1;
+        w0 = n0;
+        w1 = b_lo;
+        w2 = n2;
+        w3 = a_lo;
+        key0 += 0x9E3779B9u;
+        key1 += 0xBB67AE85u;
+    }
+    return ((((uint64_t)w0) << 32) | (uint64_t)w1) >> 11;
+}
+
+// the uniform draw u = k * 2^-53 in [0, 1)
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, uint32_t op) {
+    return (double)philox_k53(seed, shot, op) * 0x1.0p-53;
+}
 
 template <class R> struct Cx;
 template <> struct Cx<float> { using T = float2; };

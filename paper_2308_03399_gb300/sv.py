@@ -21,6 +21,7 @@ SV_NOISE_PAULI, SV_NOISE_KRAUS = 0, 1
 (SV_OPT_LOG, SV_OPT_TILE_BITS, SV_OPT_MAX_ACTIVE, SV_OPT_MAX_STAGES, SV_OPT_THREADS, SV_OPT_GRID,
  SV_OPT_PROFILE, SV_OPT_SLOT_LIMIT, SV_OPT_UPLOAD, SV_OPT_PASS_PATH, SV_OPT_JOINT_KRAUS,
  SV_OPT_SHOT_BASE, SV_OPT_CHAIN_DECIDES, SV_OPT_PREDRAW_PAULI) = range(14)
+SV_TREE_WORDS = 9
 PROFILE_CLASSES = ("pass", "decide", "alloc", "copy", "final", "init", "other", "total")
 
 _lock = threading.Lock()
@@ -70,6 +71,7 @@ def lib():
                 "sv_get_amplitudes": [P, U64, P, U64],
                 "sv_get_outcomes": [P, U32, P, P],
                 "sv_get_fork_events": [P, P, U64, P],
+                "sv_get_branch_tree": [P, P, U64, P, P, U64, P],
                 "sv_stats": [P, P],
                 "sv_profile": [P, P, P],
                 "sv_sync": [P, U64],
@@ -210,6 +212,18 @@ class Batch:
         _check(lib().sv_get_fork_events(self.h, _p(ev), cap, C.byref(n)))
         return ev[:5 * n.value].reshape(-1, 5)
 
+    def get_branch_tree(self):
+        """(records, shots): records is (n, 9) int64 rows (round, op, parent,
+        child, outcome, shot_offset, shot_count, parent_offset, parent_count)
+        indexing into shots (sv_get_branch_tree)."""
+        n_rec, n_ids = C.c_uint64(), C.c_uint64()
+        _check(lib().sv_get_branch_tree(self.h, None, 0, C.byref(n_rec), None, 0, C.byref(n_ids)))
+        rec = np.zeros(SV_TREE_WORDS * max(n_rec.value, 1), np.int64)
+        ids = np.zeros(max(n_ids.value, 1), np.uint32)
+        _check(lib().sv_get_branch_tree(self.h, _p(rec), n_rec.value, C.byref(n_rec), _p(ids), n_ids.value,
+                                        C.byref(n_ids)))
+        return rec[:SV_TREE_WORDS * n_rec.value].reshape(-1, SV_TREE_WORDS), ids[:n_ids.value]
+
     def stats(self):
         s = np.zeros(8, np.float64)
         _check(lib().sv_stats(self.h, _p(s)))
@@ -292,6 +306,6 @@ def exported_symbols():
     """Names of the entry points the header declares (checked by the tests)."""
     return ["sv_alloc_batch", "sv_free_batch", "sv_set_option", "sv_apply_gate_batch", "sv_sample_noise",
             "sv_measure_batch", "sv_branch", "sv_counts", "sv_get_keys", "sv_waiting", "sv_run_circuit",
-            "sv_get_amplitudes", "sv_get_outcomes", "sv_get_fork_events", "sv_stats", "sv_profile", "sv_sync",
+            "sv_get_amplitudes", "sv_get_outcomes", "sv_get_fork_events", "sv_get_branch_tree", "sv_stats", "sv_profile", "sv_sync",
             "sv_last_error", "sv_run_circuits", "sv_final_sample_noalloc", "sv_mlp_create", "sv_mlp_free", "sv_mlp_num_params",
             "sv_mlp_set_params", "sv_mlp_get_params", "sv_mlp_forward", "sv_mlp_gradient", "sv_mlp_train"]

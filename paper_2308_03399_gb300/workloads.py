@@ -64,13 +64,18 @@ X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
 H = np.array([[1, 1], [1, -1]], dtype=np.complex128) / math.sqrt(2)
 
 
-def haar_su4(rng: np.random.Generator) -> np.ndarray:
-    """Haar-random unitary of size 4 (QR of a complex Ginibre matrix with the
-    phase fix of Mezzadri 2007), scaled to determinant 1."""
-    z = (rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))) / math.sqrt(2)
+def haar_unitary(dim: int, rng: np.random.Generator) -> np.ndarray:
+    """Haar-random dim x dim unitary: QR of a complex Ginibre matrix with the
+    phase fix of Mezzadri 2007."""
+    z = (rng.standard_normal((dim, dim)) + 1j * rng.standard_normal((dim, dim))) / math.sqrt(2)
     q, r = np.linalg.qr(z)
     d = np.diag(r)
-    q = q * (d / np.abs(d))[None, :]
+    return q * (d / np.abs(d))[None, :]
+
+
+def haar_su4(rng: np.random.Generator) -> np.ndarray:
+    """Haar-random unitary of size 4, scaled to determinant 1."""
+    q = haar_unitary(4, rng)
     det = np.linalg.det(q)
     return q / det ** 0.25
 

@@ -21,10 +21,10 @@ from paper_2308_03399_gb300 import workloads as W
 TOL = {sv.SV_C128: dict(c=1e-10, amp=1e-12), sv.SV_C64: dict(c=1e-5, amp=1e-5)}
 
 
-def run_gpu(circ, seed, n_shots, mode, prec, use_graph=True, opts=None, want_amps=(), log=True):
+def run_gpu(circ, seed, n_shots, mode, prec, use_graph=True, opts=None, want_amps=(), log=True, mem_budget=0):
     arrays = circ.to_arrays()
     cs = sv.circuit_struct(arrays)
-    with sv.Batch(circ.n_qubits, n_shots, max(1, circ.n_clbits), prec, mode, seed) as b:
+    with sv.Batch(circ.n_qubits, n_shots, max(1, circ.n_clbits), prec, mode, seed, mem_budget=mem_budget) as b:
         if log:
             b.set_option(sv.SV_OPT_LOG, 1)
         for k, v in (opts or {}).items():
@@ -38,24 +38,42 @@ def run_gpu(circ, seed, n_shots, mode, prec, use_graph=True, opts=None, want_amp
                 res["sel"][op], res["thr"][op] = s, t
             if mode in (sv.SV_BRANCH, sv.SV_BATCH_BRANCH):
                 res["forks"] = b.get_fork_events()
+                res["tree"] = b.get_branch_tree()
         res["amps"] = {s: b.get_amplitudes(s) for s in want_amps}
     return res
 
 
-def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0, amp_errs=None):
+def oracle_refs(circ, seed, shots, state_shots=(), base=0):
+    """First oracle runs of several shots side by side (threads: the C
+    oracle releases the interpreter lock), for sizes where one shot takes
+    minutes.  Shots in state_shots also return their final state."""
+    from concurrent.futures import ThreadPoolExecutor
+    oc = O.OracleCircuit(circ)
+    shots = [int(s) for s in shots]
+    with ThreadPoolExecutor(max(1, len(shots))) as ex:
+        futs = {s: ex.submit(O.run_shot, oc, seed, base + s, None, s in state_shots) for s in shots}
+        return {s: f.result() for s, f in futs.items()}
+
+
+def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0, amp_errs=None, outcomes_out=None,
+                  refs=None):
     """Compare the GPU's logs of `shots` with the oracle.  Local shot s of the
     GPU batch is the oracle's global shot base + s.  Returns counts of
     checked draws and flagged draws; raises AssertionError on an unexplained
     mismatch.  With amp_errs, each compared shot's (largest absolute, relative
-    L2) amplitude error is appended to it."""
+    L2) amplitude error is appended to it.  With outcomes_out (a dict), the
+    oracle's outcome log of each shot (after following flagged draws) is
+    stored under the shot.  refs: first oracle runs (oracle_refs) to start
+    from instead of running each shot here."""
     tol = TOL[prec]
     oc = O.OracleCircuit(circ)
     kinds = circ.to_arrays()["kind"]
     rops = circ.random_ops()
     n_draws = n_flag = 0
+    fin_ops = {op for op in rops if kinds[op] == W.FINAL}
     for s in shots:
         overrides = {}
-        ref = O.run_shot(oc, seed, base + int(s))
+        ref = refs[int(s)] if refs is not None else O.run_shot(oc, seed, base + int(s))
         for op in rops:
             g = int(gpu["sel"][op][s])
             c = int(ref["outcome"][op])
@@ -74,12 +92,18 @@ def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0, amp_err
                         f"(thr {ref['c_lo'][op]:.17g},{ref['c_hi'][op]:.17g}) u={u:.17g}")
             n_flag += 1
             overrides[op] = g
-            ref = O.run_shot(oc, seed, base + int(s), overrides=overrides)
+            if op not in fin_ops:  # the final draw changes nothing after it
+                ref = O.run_shot(oc, seed, base + int(s), overrides=overrides)
+        if outcomes_out is not None:
+            outcomes_out[int(s)] = ref["outcome"].copy()
         fin = [op for op in rops if kinds[op] == W.FINAL]
         if fin:
             assert int(gpu["keys"][s]) == int(gpu["sel"][fin[0]][s])
         if check_amps and s in gpu.get("amps", {}):
-            st = O.run_shot(oc, seed, base + int(s), overrides=overrides, want_state=True)["state"]
+            if "state" in ref and not set(overrides) - fin_ops:
+                st = ref["state"]  # the state before the final draw
+            else:
+                st = O.run_shot(oc, seed, base + int(s), overrides=overrides, want_state=True)["state"]
             err = np.abs(gpu["amps"][s] - st).max()
             if amp_errs is not None:
                 amp_errs.append((float(err), float(np.linalg.norm(gpu["amps"][s] - st) / np.linalg.norm(st))))
@@ -108,3 +132,49 @@ def canonical_tree_records(sel, rops, n_shots):
         by.setdefault((op, parent), []).append((outcome, len(child)))
     del kinds_final
     return sorted((op, tuple(sorted(v))) for (op, _), v in by.items())
+
+
+def check_branch_tree(tree, outcomes, rops):
+    """The GPU's branch tree with shot sets (sv_get_branch_tree) against the
+    canonical tree of the oracle's per-shot outcome logs (oracle.branch_tree),
+    round by round.
+
+    Round 0 starts from all shots.  Its fork records must equal the canonical
+    tree of those shots, cut below the groups the GPU parked on the waiting
+    list (a parked group is a record with child -1 whose shots do not fork
+    again in the same round).  The shots of the parked groups are the root of
+    the next round, whose records must equal the canonical tree of just those
+    shots, and so on until no group is parked.  outcomes is (shots, ops), -1
+    where a shot made no draw; rops the random ops (final sampling
+    excluded).  Returns the number of rounds."""
+    records, ids = tree
+    n_shots = outcomes.shape[0]
+    by_round = {}
+    for r, op, parent, child, outc, off, cnt, poff, pcnt in records.tolist():
+        S = frozenset(ids[off:off + cnt].tolist())
+        P = frozenset(ids[poff:poff + pcnt].tolist())
+        assert len(S) == cnt and len(P) == pcnt and S <= P, "a group's shots lie inside its node's"
+        by_round.setdefault(r, []).append((op, P, S, outc, child))
+    root = frozenset(range(n_shots))
+    r = 0
+    while root:
+        evs = by_round.pop(r, [])
+        got = {(op, P, S, o) for op, P, S, o, _ in evs}
+        assert len(got) == len(evs), f"round {r}: a fork record appears twice"
+        for op, P, S, o, _ in evs:
+            assert P <= root, f"round {r}: a node holds shots that are not in the round"
+        later = {(op, P) for op, P, S, o, _ in evs}
+        parked = [S for op, P, S, o, child in evs
+                  if child == -1 and not any(P2 == S and op2 > op for op2, P2 in later)]
+        idx = sorted(root)
+        canon = O.branch_tree(outcomes[idx], rops, shot_ids=idx)
+        canon = {rec for rec in canon if not any(rec[1] <= pk for pk in parked)}
+        missing, extra = canon - got, got - canon
+        assert not missing and not extra, (f"round {r}: {len(missing)} canonical fork records missing, "
+                                           f"{len(extra)} unexpected (of {len(canon)})")
+        nxt = frozenset().union(*parked) if parked else frozenset()
+        assert sum(len(p) for p in parked) == len(nxt), f"round {r}: parked groups overlap"
+        root = nxt
+        r += 1
+    assert not by_round, f"records for rounds {sorted(by_round)} after the waiting list emptied"
+    return r

@@ -10,7 +10,7 @@ import pytest
 from oracle import oracle as O
 from paper_2308_03399_gb300 import sv
 from paper_2308_03399_gb300 import workloads as W
-from tests.parity import canonical_tree_records, compare_shots, gpu_tree_records, run_gpu
+from tests.parity import canonical_tree_records, check_branch_tree, compare_shots, gpu_tree_records, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -91,6 +91,43 @@ def test_fork_events_form_the_canonical_tree(prec):
     compare_shots(c, 5, gpu, range(0, n_shots, 7), prec, check_amps=False)
 
 
+def _oracle_outcomes(c, seed, gpu, n_shots, prec, **kw):
+    outs = {}
+    compare_shots(c, seed, gpu, range(n_shots), prec, check_amps=False, outcomes_out=outs, **kw)
+    return np.stack([outs[s] for s in range(n_shots)])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(SMALL))
+def test_branch_tree_shot_sets_match_oracle(name, prec):
+    # every fork's node and group shot sets equal the canonical tree derived
+    # from the oracle's outcome logs of all 300 shots (Section IV-B: a state
+    # forks exactly where its shots' sampled outcomes diverge)
+    c = SMALL[name]()
+    n_shots = 300
+    gpu = run_gpu(c, 7, n_shots, sv.SV_BRANCH, prec)
+    outc = _oracle_outcomes(c, 7, gpu, n_shots, prec)
+    rops = [op for op in c.random_ops() if c.ops[op].kind != W.FINAL]
+    assert check_branch_tree(gpu["tree"], outc, rops) == 1
+    assert len(gpu["tree"][0]) > 0
+
+
+@pytest.mark.parametrize("chain", [1, 0])
+@pytest.mark.parametrize("prec", PRECS)
+def test_branch_tree_with_waiting_list_matches_oracle(prec, chain):
+    # three slots: groups park on the waiting list and restart as new roots;
+    # each round's records are the canonical tree of that round's shots
+    c = W.random_su4(6, 4, 0.1, 0.15, seed=71)
+    n_shots = 300
+    gpu = run_gpu(c, 4, n_shots, sv.SV_BRANCH, prec,
+                  opts={sv.SV_OPT_SLOT_LIMIT: 3, sv.SV_OPT_CHAIN_DECIDES: chain})
+    assert gpu["stats"]["restarts"] > 0
+    outc = _oracle_outcomes(c, 4, gpu, n_shots, prec)
+    rops = [op for op in c.random_ops() if c.ops[op].kind != W.FINAL]
+    rounds = check_branch_tree(gpu["tree"], outc, rops)
+    assert rounds == gpu["stats"]["restarts"] + 1
+
+
 @pytest.mark.parametrize("prec,n", [(sv.SV_C64, 14), (sv.SV_C128, 13)])
 def test_several_tiles_and_chunks(prec, n):
     # 8 tiles per state: stages and reductions span tile and chunk borders
@@ -145,12 +182,83 @@ def test_per_op_calls_match_run_circuit():
                 b.sample_noise_pauli(i, o.qubits, o.cum, o.strings)
                 b.branch(i)
             elif o.kind == W.MEASURE:
-                b.measure_batch(i, o.qubits, o.clbits, o.reset)
+                b.measure_batch(i, o.qubits, o.clbits, o.reset)  # committed by the next call
             elif o.kind == W.FINAL:
                 cnt = b.counts(i)
         keys = b.get_keys()
     assert np.array_equal(keys, ref["keys"])
     assert sum(cnt.values()) == 64
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_sample_then_branch_commits_the_logged_choices(prec):
+    # per-op calls in shot-branching mode: sampling logs every shot's choice
+    # and forks nothing; sv_branch forks on exactly those choices.  The tree
+    # and the keys follow the oracle.
+    c = W.random_su4(5, 3, 0.1, 0.15, seed=94)
+    n_shots = 200
+    with sv.Batch(5, n_shots, 1, prec, sv.SV_BRANCH, 9) as b:
+        b.set_option(sv.SV_OPT_LOG, 1)
+        for i, o in enumerate(c.ops):
+            if o.kind == W.GATE:
+                b.apply_gate_batch(o.qubits, o.mat)
+                continue
+            if o.kind == W.FINAL:
+                b.counts(i)
+                continue
+            if o.kind == W.PAULI:
+                b.sample_noise_pauli(i, o.qubits, o.cum, o.strings)
+            else:
+                b.sample_noise_kraus(i, o.qubits, o.kraus)
+            before = b.stats()["live_branches"]
+            sel = b.get_outcomes(i)
+            assert b.stats()["live_branches"] == before  # nothing forked yet
+            if i % 2:
+                b.branch(i)  # explicit commit; even ops are committed by the next call
+                assert b.stats()["live_branches"] >= before
+            assert (sel >= 0).all()
+        gpu = dict(keys=b.get_keys(), sel={}, thr={}, tree=b.get_branch_tree(), amps={})
+        for op in c.random_ops():
+            gpu["sel"][op], gpu["thr"][op] = b.get_outcomes(op, thresholds=True)
+        with pytest.raises(sv.SvError):
+            b.branch(0)  # not the last random op sampled
+    outc = _oracle_outcomes(c, 9, gpu, n_shots, prec)
+    rops = [op for op in c.random_ops() if c.ops[op].kind != W.FINAL]
+    check_branch_tree(gpu["tree"], outc, rops)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("mode", MODES)
+def test_wide_dense_gates_match_oracle(mode, prec):
+    # fused blocks given as dense 4- and 5-qubit unitaries (shared-memory
+    # tile path), mixed with noise, on 9 qubits
+    rng = np.random.default_rng(123)
+    c = W.Circuit(9)
+    for _ in range(3):
+        qs = [int(x) for x in rng.choice(9, 5, replace=False)]
+        c.gate(qs, W.haar_unitary(32, rng))
+        c.depolarizing(qs[:2], 0.05)
+        c.kraus([qs[0]], W.amplitude_damping(0.1))
+        qs = [int(x) for x in rng.choice(9, 4, replace=False)]
+        c.gate(qs, W.haar_unitary(16, rng))
+    c.final()
+    gpu = run_gpu(c, 31, 150, mode, prec, want_amps=[0, 149])
+    compare_shots(c, 31, gpu, range(150), prec)
+
+
+def test_per_op_five_qubit_gate_matches_oracle():
+    rng = np.random.default_rng(5)
+    c = W.Circuit(7)
+    c.gate([6, 1, 3, 0, 4], W.haar_unitary(32, rng))
+    c.gate([2, 5, 1, 6], W.haar_unitary(16, rng))
+    c.final()
+    ref = O.run_shot(c, 1, 0, want_state=True)["state"]
+    with sv.Batch(7, 4, 1, sv.SV_C128, sv.SV_BATCH, 1) as b:
+        for o in c.ops[:-1]:
+            b.apply_gate_batch(o.qubits, o.mat)
+        assert np.abs(b.get_amplitudes(3) - ref).max() < 1e-12
+        with pytest.raises(sv.SvError):
+            b.apply_gate_batch([0, 1, 2, 3, 4, 5], np.eye(64))
 
 
 def test_edge_cases_one_qubit_one_shot():
