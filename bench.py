@@ -154,6 +154,102 @@ def plain_vs_batched(torch, flush_buf):
     return out
 
 
+def sm_peaks():
+    """SM clock from MEASURED_PEAKS.json (else the nominal 2070 MHz) and the
+    GB300 per-SM rates that bound a pass held in shared memory: 152 SMs,
+    32 banks x 4 B = 128 B of shared memory per clock per SM, and 128 FP32
+    FMA lanes (256 flop) per clock per SM."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    mhz, kind = 2070.0, "nominal clock"
+    if os.path.exists(p):
+        mhz, kind = float(json.load(open(p)).get("sm_max_mhz", 2070.0)), "measured max clock"
+    sms = 152
+    return {"smem_gbs": sms * 128 * mhz * 1e6 / 1e9, "fp32_tflops": sms * 256 * mhz * 1e6 / 1e12,
+            "derivation": f"152 SMs x (128 B smem | 256 FP32 flop) per clock x {mhz:.0f} MHz ({kind})"}
+
+
+def leg(torch, flush_buf, name, steps, warmup, mode="branch", prec="c64", graph=True):
+    """One more workload on the same GPU: shots/s over `steps` timed steps
+    (CUDA events, L2 flushed between steps, clocks sampled), then one
+    profiled step (CUDA events around every launch) for the pass kernels'
+    own time, algorithmic bytes and passes."""
+    from paper_2308_03399_gb300 import sv
+    circ, n_shots, seed = workload(name)
+    m = {"branch": sv.SV_BRANCH, "batch": sv.SV_BATCH}[mode]
+    pr = {"c64": sv.SV_C64, "c128": sv.SV_C128}[prec]
+    cs = sv.circuit_struct(circ.to_arrays())
+    stream = torch.cuda.current_stream()
+    b = sv.Batch(circ.n_qubits, n_shots, max(1, circ.n_clbits), pr, m, seed, stream=stream.cuda_stream)
+    for _ in range(warmup):
+        b.run_circuit(cs, use_graph=graph)
+    torch.cuda.synchronize()
+    b.stats()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms = []
+    for _ in range(steps):
+        flush_buf.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run_circuit(cs, use_graph=graph)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    st = b.stats()
+    b.set_option(sv.SV_OPT_PROFILE, 1)
+    b.profile()
+    flush_buf.fill_(1)
+    b.run_circuit(cs, use_graph=False)
+    prof = b.profile()
+    stp = b.stats()
+    b.close()
+    pass_ms, n_pass = prof["pass"]
+    hbm_peak, peak_kind = peaks()
+    step_ms = float(np.mean(ms))
+    out = {"workload": circ.name, "n_qubits": circ.n_qubits, "shots": n_shots, "mode": mode, "precision": prec,
+           "steps": steps, "warmup": warmup, "shots_per_s": n_shots / (step_ms / 1e3), "ms_per_step": step_ms,
+           "passes_per_step": st["passes"] / steps, "restarts_per_step": st["restarts"] / steps,
+           "algorithmic_pass_bytes_per_step": stp["pass_bytes"],
+           "pass_kernel_ms_per_step": pass_ms, "pass_launches_per_step": n_pass,
+           "profile_ms_per_step": {k: v[0] for k, v in prof.items()}, "clocks": clk}
+    if pass_ms > 0:
+        ach = stp["pass_bytes"] / (pass_ms / 1e3) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": "k_pass (all pass launches)", "achieved": ach,
+                           "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / hbm_peak}
+    return out, circ, n_shots, prof
+
+
+def cfg1_smem(torch, flush_buf):
+    """Config 1 batched in complex64: every state is one shared-memory tile
+    (2^10 amplitudes), so the passes are bound by shared memory or the FP32
+    pipe, not HBM.  Algorithmic work per gate and state (every gate acts on
+    every shot in batch mode): a k-qubit dense stage reads and writes each
+    of the 2^n amplitudes once in shared memory (2 x 8 B) and does 2^k
+    complex multiply-adds per amplitude (8 x 2^k flop).  Both are divided by
+    the pass kernels' event time of a profiled step."""
+    res, circ, n_shots, prof = leg(torch, flush_buf, "cfg1", steps=5, warmup=3, mode="batch", prec="c64")
+    from paper_2308_03399_gb300 import workloads as W
+    dim = 1 << circ.n_qubits
+    smem_b = sum(2 * 8 * dim for o in circ.ops if o.kind == W.GATE) * n_shots
+    flop = sum(8 * (1 << len(o.qubits)) * dim for o in circ.ops if o.kind == W.GATE) * n_shots
+    pk = sm_peaks()
+    t = res["pass_kernel_ms_per_step"] / 1e3
+    res.pop("roofline", None)
+    if t > 0:
+        smem_frac = smem_b / t / 1e9 / pk["smem_gbs"]
+        alu_frac = flop / t / 1e12 / pk["fp32_tflops"]
+        res["roofline"] = {
+            "bound": "smem" if smem_frac >= alu_frac else "alu", "kernel": "k_pass (whole-state tiles)",
+            "smem": {"achieved": smem_b / t / 1e9, "peak": pk["smem_gbs"], "unit": "GB/s", "frac": smem_frac,
+                     "algorithmic_bytes_per_step": smem_b},
+            "fp32": {"achieved": flop / t / 1e12, "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": alu_frac,
+                     "algorithmic_flop_per_step": flop},
+            "peak_derivation": pk["derivation"]}
+    return res
+
+
 def cpu_baseline(circ, seed, budget_s=15.0):
     """The oracle as it stands, on the host's cores, on a bounded sample of
     the workload's shots (shots are independent, so shots/s scales)."""
@@ -308,6 +404,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the config-1 plain-vs-batched comparison")
     ap.add_argument("--max-active", type=int, default=0, help="fusion width (qubits per pass), 0 = library default")
     ap.add_argument("--autotune", action="store_true", help="config 4: also run the autotuner's picks")
+    ap.add_argument("--no-legs", action="store_true", help="skip the config 1 / 3 / 5 legs of the default run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -452,6 +549,18 @@ def main():
     if rank == 0 and not args.no_plain and world == 1:
         line["plain_vs_batched"] = plain_vs_batched(torch, flush_buf)
     b.close()
+    if rank == 0 and world == 1 and not args.no_legs and args.workload == "cfg2":
+        # the metric's other sizes: 10 qubits (shared-memory bound), 20 and 28
+        # qubits (the HBM-roofline target), each with its own clocks
+        legs = {"cfg1_smem": lambda: cfg1_smem(torch, flush_buf),
+                "cfg3": lambda: leg(torch, flush_buf, "cfg3", steps=2, warmup=1)[0],
+                "cfg5": lambda: leg(torch, flush_buf, "cfg5", steps=2, warmup=1)[0]}
+        line["legs"] = {}
+        for k, fn in legs.items():
+            torch.cuda.empty_cache()
+            line["legs"][k] = fn()
+        c3 = line["legs"]["cfg3"]
+        c3["passes_per_round"] = c3["passes_per_step"] / 30
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -235,8 +235,8 @@ sv_status sv_get_outcomes(sv_batch b, uint32_t op, int32_t *per_shot_outcome, do
 /* With SV_OPT_LOG: fork events of the last run (sv_run_circuit, or the
  * per-op calls since the batch was last started), 5 int64 each: (op, parent
  * branch, child branch or -1 for the waiting list, outcome, shots).  A
- * parent's own continuing group is reported with child == parent.
- * Synchronises.                                                             */
+ * parent's own continuing group is reported with child == parent.  With
+ * events NULL the call only reports *n_out.  Synchronises.                  */
 sv_status sv_get_fork_events(sv_batch b, int64_t *events, uint64_t cap, uint64_t *n_out);
 
 /* Section IV-B-2: with SV_OPT_LOG in shot-branching modes, the branch tree

@@ -17,7 +17,7 @@ constexpr int PRE_WORDS = 8;                 // integer-pool words per pre-drawn
 constexpr uint64_t PRE_TABLE_BYTES = 1ull << 30;  // largest pre-drawn Pauli table
 constexpr int MAX_RED = 16;        // probabilities reduced by one pass (Kraus terms, 2^m outcomes)
 constexpr int MAX_CHUNKS = 1024;   // reduction partials per state
-constexpr int MAX_STAGE_Q = 4;     // qubits of one stage
+constexpr int MAX_STAGE_Q = 5;     // qubits of one stage (dense gates up to MAX_GATE_Q)
 constexpr int MAT_SMEM = 1024;     // complex matrix entries staged in shared memory per pass
 // fork log record: op, parent branch, child branch (-1: waiting list), outcome,
 // shots, first perm position of the group's shots at the fork, first perm

@@ -380,7 +380,7 @@ int local_pos(const int* tile_q, int tb, int q) {
 struct RedSpec {
     int kind = RED_NONE, k = 0, R = 0, off = 0;
     int diag_off = -1;  // RED_FORMS whose forms are all diagonal: weights here
-    int q[MAX_STAGE_Q] = {0, 0, 0, 0};
+    int q[MAX_STAGE_Q] = {};
 };
 
 // can a pass run in registers (k_pass_reg)?  its qubits plus qubit 0 <= 4,
@@ -1855,6 +1855,7 @@ sv_status sv_get_fork_events(sv_batch b, int64_t* ev, uint64_t cap, uint64_t* n_
     if (st) return st;
     const uint64_t n = std::min<uint64_t>(ctl[CTL_NFORK], b->dev.fork_log_cap);
     *n_out = n;
+    if (!ev) return SV_OK;  // size query
     if (n > cap) return fail(SV_EINVAL, "cap too small");
     if (n && ev) {
         std::vector<int64_t> raw(n * FORK_WORDS);

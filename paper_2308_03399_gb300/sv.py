@@ -207,7 +207,8 @@ class Batch:
 
     def get_fork_events(self):
         n = C.c_uint64()
-        cap = 4 * self.n_shots + 1024
+        _check(lib().sv_get_fork_events(self.h, None, 0, C.byref(n)))
+        cap = max(n.value, 1)
         ev = np.zeros(5 * cap, np.int64)
         _check(lib().sv_get_fork_events(self.h, _p(ev), cap, C.byref(n)))
         return ev[:5 * n.value].reshape(-1, 5)

@@ -47,10 +47,11 @@ def oracle_refs(circ, seed, shots, state_shots=(), base=0):
     """First oracle runs of several shots side by side (threads: the C
     oracle releases the interpreter lock), for sizes where one shot takes
     minutes.  Shots in state_shots also return their final state."""
+    import os
     from concurrent.futures import ThreadPoolExecutor
     oc = O.OracleCircuit(circ)
     shots = [int(s) for s in shots]
-    with ThreadPoolExecutor(max(1, len(shots))) as ex:
+    with ThreadPoolExecutor(max(1, min(len(shots), os.cpu_count() or 1))) as ex:
         futs = {s: ex.submit(O.run_shot, oc, seed, base + s, None, s in state_shots) for s in shots}
         return {s: f.result() for s, f in futs.items()}
 
