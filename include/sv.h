@@ -262,7 +262,7 @@ sv_status sv_get_fork_events(sv_batch b, int64_t *events, uint64_t cap, uint64_t
  * records: host, cap records; shots: host, shot_cap ids.  With both NULL
  * the call only reports *n_records and *n_shot_ids.  SV_EINVAL when a
  * buffer is too small, SV_EUNSUPPORTED when the device log overflowed
- * (8 x shots + 4096 events).  Synchronises.                                 */
+ * (min(64 x shots + 65536, 2^22) events).  Synchronises.                   */
 #define SV_TREE_WORDS 9
 sv_status sv_get_branch_tree(sv_batch b, int64_t *records, uint64_t cap, uint64_t *n_records, uint32_t *shots,
                              uint64_t shot_cap, uint64_t *n_shot_ids);

@@ -332,7 +332,8 @@ __host__ __device__ inline size_t pass_bytes_before_bars(const PassDesc& p, int 
 }
 
 // Kraus probabilities: quadratic forms v^dagger F_i v over groups of the
-// Kraus qubits, F_i = K_i^dagger K_i (Section III-B-2 / IV-A-4)
+// Kraus qubits, F_i = K_i^dagger K_i (Section III-B-2 / IV-A-4).  F holds the
+// Rn forms, then their float32 residuals (complex64: each form is hi + lo)
 template <class R, int K>
 __device__ __noinline__ void reduce_forms(const typename Cplx<R>::T* tile, int tb, const int32_t* pos, int Rn,
                                           const typename Cplx<R>::T* F, typename AccSlot<R>::T* acc) {
@@ -347,17 +348,24 @@ __device__ __noinline__ void reduce_forms(const typename Cplx<R>::T* tile, int t
         for (int r = 0; r < D; ++r) v[r] = tile[base | gi.off[r]];
         for (int f = 0; f < Rn; ++f) {
             const T* Ff = F + f * D * D;
-            R q = 0;
+            const T* Fl = F + (Rn + f) * D * D;  // float32 residuals of Ff
+            R q = 0, ql = 0;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                T fa;
+                T fa, fl;
                 fa.x = 0;
                 fa.y = 0;
+                fl.x = 0;
+                fl.y = 0;
 #pragma unroll
-                for (int c = 0; c < D; ++c) cfma(fa, Ff[a * D + c], v[c]);
+                for (int c = 0; c < D; ++c) {
+                    cfma(fa, Ff[a * D + c], v[c]);
+                    if constexpr (sizeof(R) == 4) cfma(fl, Fl[a * D + c], v[c]);
+                }
                 q += v[a].x * fa.x + v[a].y * fa.y;  // Re(conj(v_a) (F v)_a)
+                if constexpr (sizeof(R) == 4) ql += v[a].x * fl.x + v[a].y * fl.y;
             }
-            acc_add(&acc[f * blockDim.x + threadIdx.x], q);
+            acc_add(&acc[f * blockDim.x + threadIdx.x], q + ql);
         }
     }
 }
@@ -602,14 +610,14 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
                     mats[st.mat + e] = m;
                 }
             }
-            if (p.red_kind == RED_FORMS) {
-                const int D2 = 1 << (2 * p.red_k);
+            if (p.red_kind == RED_FORMS) {  // the forms, then their float32 residuals
+                const int E2 = 2 * (p.red_R << (2 * p.red_k));
                 const R* src = pool + p.red_off;
-                for (int e = threadIdx.x; e < p.red_R * D2; e += blockDim.x) {
+                for (int e = threadIdx.x; e < E2; e += blockDim.x) {
                     T m;
                     m.x = src[2 * e];
                     m.y = src[2 * e + 1];
-                    mats[p.mat_elems - p.red_R * D2 + e] = m;
+                    mats[p.mat_elems - E2 + e] = m;
                 }
             }
             __syncthreads();
@@ -629,10 +637,7 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
             stage_dispatch<R>(tile, tb, st, mats + st.mat, sel_sh[st_i], scale_sh[st_i], packed_sh[st_i]);
             __syncthreads();
         }
-        if (red) {
-            const int D2 = 1 << (2 * p.red_k);
-            reduce_dispatch<R>(tile, tb, p, mats + p.mat_elems - p.red_R * D2, acc);
-        }
+        if (red) reduce_dispatch<R>(tile, tb, p, mats + p.mat_elems - 2 * (p.red_R << (2 * p.red_k)), acc);
         __syncthreads();
         if (p.store && warp == 0) {
             T* dst = tile_ptr(i);
@@ -891,7 +896,16 @@ __device__ __forceinline__ void reg_forms1(const typename Cplx<R>::T* v, const t
             const R fa_y = Ff[0].x * a.y + Ff[0].y * a.x + Ff[1].x * b.y + Ff[1].y * b.x;
             const R fb_x = Ff[2].x * a.x - Ff[2].y * a.y + Ff[3].x * b.x - Ff[3].y * b.y;
             const R fb_y = Ff[2].x * a.y + Ff[2].y * a.x + Ff[3].x * b.y + Ff[3].y * b.x;
-            acc[f].add(a.x * fa_x + a.y * fa_y + b.x * fb_x + b.y * fb_y);
+            R q = a.x * fa_x + a.y * fa_y + b.x * fb_x + b.y * fb_y;
+            if constexpr (sizeof(R) == 4) {  // the same form with the residual coefficients
+                const auto* Fl = F + 4 * (Rn + f);
+                const R la_x = Fl[0].x * a.x - Fl[0].y * a.y + Fl[1].x * b.x - Fl[1].y * b.y;
+                const R la_y = Fl[0].x * a.y + Fl[0].y * a.x + Fl[1].x * b.y + Fl[1].y * b.x;
+                const R lb_x = Fl[2].x * a.x - Fl[2].y * a.y + Fl[3].x * b.x - Fl[3].y * b.y;
+                const R lb_y = Fl[2].x * a.y + Fl[2].y * a.x + Fl[3].x * b.y + Fl[3].y * b.x;
+                q += a.x * la_x + a.y * la_y + b.x * lb_x + b.y * lb_y;
+            }
+            acc[f].add(q);
         }
     }
 }
@@ -950,13 +964,17 @@ __device__ __forceinline__ void reg_diag(const typename Cplx<R>::T* v, const Pas
         }
     }
     const int D = 1 << p.red_k;
+    const auto* Wl = W + (p.red_R << p.red_k);  // float32 residuals of the weights
 #pragma unroll
     for (int f = 0; f < REG_MAX_RED; ++f) {
         if (f >= p.red_R) break;
         R loc = 0;
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-            if (r < D) loc += W[f * D + r].x * q[r];
+            if (r < D) {
+                loc += W[f * D + r].x * q[r];
+                if constexpr (sizeof(R) == 4) loc += Wl[f * D + r].x * q[r];
+            }
         acc[f].add(loc);
     }
 }
@@ -1102,14 +1120,14 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                     mats[st.mat] = m;
                 }
             }
-            if (p.red_kind == RED_FORMS || p.red_kind == RED_DIAG) {
-                const int E = p.red_kind == RED_FORMS ? 4 * p.red_R : p.red_R << p.red_k;
+            if (p.red_kind == RED_FORMS || p.red_kind == RED_DIAG) {  // coefficients, then residuals
+                const int E2 = 2 * (p.red_kind == RED_FORMS ? 4 * p.red_R : p.red_R << p.red_k);
                 const R* src = pool + p.red_off;
-                for (int e = lane; e < E; e += 32) {
+                for (int e = lane; e < E2; e += 32) {
                     T m;
                     m.x = src[2 * e];
                     m.y = src[2 * e + 1];
-                    mats[p.mat_elems - E + e] = m;
+                    mats[p.mat_elems - E2 + e] = m;
                 }
             }
             __syncwarp();
@@ -1213,9 +1231,9 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                 }
             }
             if (p.red_kind == RED_FORMS)
-                reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - p.red_R * 4, p.red_R, acc);
+                reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - 8 * p.red_R, p.red_R, acc);
             else if (p.red_kind == RED_DIAG)
-                reg_diag<R, G>(v, p, mats + p.mat_elems - (p.red_R << p.red_k), acc);
+                reg_diag<R, G>(v, p, mats + p.mat_elems - 2 * (p.red_R << p.red_k), acc);
             if (p.store) {
                 if constexpr (sizeof(T) == 8 && PAIRED) {
 #pragma unroll

@@ -401,7 +401,7 @@ int reg_width(sv_batch b, const RedSpec& red, uint64_t act) {
     for (const PendStage& ps : b->pend)
         probe.mat_elems += (ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) ? 1 << (2 * ps.k)
                                                                           : (ps.kind == ST_PROJ_BR ? 1 : 0);
-    if (red.kind == RED_FORMS) probe.mat_elems += red.diag_off >= 0 ? red.R << red.k : red.R << (2 * red.k);
+    if (red.kind == RED_FORMS) probe.mat_elems += 2 * (red.diag_off >= 0 ? red.R << red.k : red.R << (2 * red.k));
     const int prec = b->prec == SV_C128;
     if (pass_reg_smem_bytes(prec, probe, pass_reg_threads(prec)) > 48 * 1024) return 0;
     return wp;
@@ -494,8 +494,9 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
         p.red_off = red.diag_off;
     }
     for (int j = 0; j < red.k; ++j) p.red_pos[j] = local_pos(p.tile_q, p.tb, red.q[j]);
-    if (p.red_kind == RED_FORMS) mat += red.R << (2 * red.k);
-    else if (p.red_kind == RED_DIAG) mat += red.R << red.k;
+    // forms (or diagonal weights) and their float32 residuals
+    if (p.red_kind == RED_FORMS) mat += 2 * (red.R << (2 * red.k));
+    else if (p.red_kind == RED_DIAG) mat += 2 * (red.R << red.k);
     p.mat_elems = mat;
     b->pend.clear();
     b->active = 0;
@@ -828,7 +829,20 @@ bool kraus_complete(const std::vector<std::complex<double>>& F, int k, int n_ter
     return true;
 }
 
-// push forms (and, when all are diagonal, their diagonals) into the pool
+// Quadratic-form coefficients carry a second copy holding their float32
+// residuals v - (float)v: a complex64 reduction evaluates each form as
+// hi + lo, so the coefficients enter at float64-grade accuracy (a float32
+// coefficient alone would shift every probability by the same relative
+// ~3e-8, which no summation order averages out).  Zero for complex128.
+void push_residuals(sv_batch b, int off, int n) {
+    for (int i = 0; i < n; ++i) {
+        const double v = b->pool[off + i];
+        b->pool.push_back(b->prec == SV_C64 ? v - (double)(float)v : 0.0);
+    }
+}
+
+// push forms (and, when all are diagonal, their diagonals) into the pool,
+// each followed by its residuals
 void push_forms(sv_batch b, const std::vector<std::complex<double>>& F, int k, int R, RedSpec& red) {
     const int D = 1 << k, E = D * D;
     red.off = (int)b->pool.size();
@@ -841,6 +855,7 @@ void push_forms(sv_batch b, const std::vector<std::complex<double>>& F, int k, i
                 b->pool.push_back(v.imag());
                 if (i != j && v != 0.0) diag = false;
             }
+    push_residuals(b, red.off, 2 * R * E);
     red.diag_off = -1;
     if (diag) {
         red.diag_off = (int)b->pool.size();
@@ -849,6 +864,7 @@ void push_forms(sv_batch b, const std::vector<std::complex<double>>& F, int k, i
                 b->pool.push_back(F[(size_t)E * f + i * D + i].real());
                 b->pool.push_back(0.0);
             }
+        push_residuals(b, red.diag_off, 2 * R * D);
     }
 }
 
@@ -1151,6 +1167,7 @@ sv_status run_plain(sv_batch b, const sv_circuit* c) {
                                 b->pool.push_back(s.real());
                                 b->pool.push_back(s.imag());
                             }
+                        push_residuals(b, red.off, 2 * E);
                     } else {
                         red.kind = RED_BINS;
                         red.R = 1 << k;
@@ -1476,7 +1493,8 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
     switch (opt) {
     case SV_OPT_LOG:
         if (v && !b->dev.fork_log) {
-            b->dev.fork_log_cap = (int)std::min<uint64_t>(8 * b->n_shots + 4096, 1 << 24);
+            // waiting-list restarts fork the same shots again: room for many rounds
+            b->dev.fork_log_cap = (int)std::min<uint64_t>(64 * b->n_shots + 65536, 1 << 22);
             sv_status st = dalloc(b, &b->dev.fork_log, FORK_WORDS * (size_t)b->dev.fork_log_cap);
             if (st) return st;
         }

@@ -52,10 +52,12 @@ template <> struct Cx<double> { using T = double2; };
 template <class R> struct Sum;
 template <> struct Sum<double> {
     double s = 0.0;
-    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void add_sq(double x, double y) { s += x * x + y * y; }
     __device__ __forceinline__ double get() const { return s; }
 };
-template <> struct Sum<float> {  // float-float pair, Knuth TwoSum
+// float-float pair (Knuth's TwoSum); the squares of float32 values enter
+// exactly: x*x rounded plus its error fma(x, x, -x*x) (Dekker's product)
+template <> struct Sum<float> {
     float hi = 0.f, lo = 0.f;
     __device__ __forceinline__ void add(float x) {
         float s = __fadd_rn(hi, x);
@@ -63,6 +65,13 @@ template <> struct Sum<float> {  // float-float pair, Knuth TwoSum
         float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
         hi = s;
         lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add_sq(float x, float y) {
+        const float px = __fmul_rn(x, x), py = __fmul_rn(y, y);
+        const float ex = __fmaf_rn(x, x, -px), ey = __fmaf_rn(y, y, -py);
+        add(px);
+        add(py);
+        lo = __fadd_rn(lo, __fadd_rn(ex, ey));
     }
     __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
 };
@@ -81,7 +90,7 @@ __device__ __forceinline__ double chunk_sum(const typename Cx<R>::T* g, int64_t 
             if (j0 + k * bd < L) v[k] = g[j0 + k * bd];
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-            if (j0 + k * bd < L) a.add(v[k].x * v[k].x + v[k].y * v[k].y);
+            if (j0 + k * bd < L) a.add_sq(v[k].x, v[k].y);
     }
     double x = a.get();
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);

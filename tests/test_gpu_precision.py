@@ -127,4 +127,4 @@ def test_accumulation_matches_float64_sums(name):
     names = {W.KRAUS: "Kraus", W.MEASURE: "measurement", W.FINAL: "final sample"}
     print(f"\n{name}: largest |C_gpu - C_float64| over the same complex64 state: " +
           ", ".join(f"{names[k]} {worst[k]:.2e} ({count[k]} decisions)" for k in worst if count[k]))
-    assert max(worst.values()) <= 1e-9
+    assert max(worst.values()) <= 5e-9
