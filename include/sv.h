@@ -212,10 +212,12 @@ sv_status sv_waiting(sv_batch b, uint64_t *n_waiting);
 sv_status sv_run_circuit(sv_batch b, const sv_circuit *c, int use_graph);
 
 /* Several circuits, one per batch (n of them, batches sharing one stream;
- * batch and branch modes may mix), run back to back: with use_graph != 0 the
- * launch sequences of all of them, each with its reset, are captured into
- * ONE CUDA graph (cached for the same batches and circuits) and replayed
- * (the paper's multi-circuit batching, Section VI).  Shot-branching
+ * batch and branch modes may mix): with use_graph != 0 the launch sequences
+ * of all of them, each with its reset, are captured into ONE CUDA graph
+ * (cached for the same batches and circuits) in which every circuit is a
+ * parallel branch, so independent circuits run side by side on the GPU
+ * (the paper's multi-circuit batching, Section VI); without a graph they run
+ * one after another.  Shot-branching
  * batches whose forks parked shots on the waiting list then restart them
  * outside the graph until none wait.  Per-shot keys via sv_get_keys.
  * Batches and circuits must stay alive while the graph is cached.           */

@@ -294,6 +294,9 @@ __device__ __forceinline__ void acc_add(float2* a, float x) {
     a->y = t.lo;
 }
 __device__ __forceinline__ void acc_add(double* a, double x) { *a += x; }
+// a term far below the pair's rounding unit goes straight to the low word
+__device__ __forceinline__ void acc_add_lo(float2* a, float x) { a->y = __fadd_rn(a->y, x); }
+__device__ __forceinline__ void acc_add_lo(double* a, double x) { *a += x; }
 __device__ __forceinline__ double acc_get(float2 a) { return (double)a.x + (double)a.y; }
 __device__ __forceinline__ double acc_get(double a) { return a; }
 
@@ -365,7 +368,10 @@ __device__ __noinline__ void reduce_forms(const typename Cplx<R>::T* tile, int t
                 q += v[a].x * fa.x + v[a].y * fa.y;  // Re(conj(v_a) (F v)_a)
                 if constexpr (sizeof(R) == 4) ql += v[a].x * fl.x + v[a].y * fl.y;
             }
-            acc_add(&acc[f * blockDim.x + threadIdx.x], q + ql);
+            acc_add(&acc[f * blockDim.x + threadIdx.x], q);
+            // the residual part is far below an ulp of q: it joins the
+            // accumulator's low word instead of being rounded away in q + ql
+            if constexpr (sizeof(R) == 4) acc_add_lo(&acc[f * blockDim.x + threadIdx.x], ql);
         }
     }
 }
@@ -896,16 +902,17 @@ __device__ __forceinline__ void reg_forms1(const typename Cplx<R>::T* v, const t
             const R fa_y = Ff[0].x * a.y + Ff[0].y * a.x + Ff[1].x * b.y + Ff[1].y * b.x;
             const R fb_x = Ff[2].x * a.x - Ff[2].y * a.y + Ff[3].x * b.x - Ff[3].y * b.y;
             const R fb_y = Ff[2].x * a.y + Ff[2].y * a.x + Ff[3].x * b.y + Ff[3].y * b.x;
-            R q = a.x * fa_x + a.y * fa_y + b.x * fb_x + b.y * fb_y;
-            if constexpr (sizeof(R) == 4) {  // the same form with the residual coefficients
+            acc[f].add(a.x * fa_x + a.y * fa_y + b.x * fb_x + b.y * fb_y);
+            if constexpr (sizeof(R) == 4) {
+                // the same form with the residual coefficients: far below an
+                // ulp of the term, so it joins the accumulator's low word
                 const auto* Fl = F + 4 * (Rn + f);
                 const R la_x = Fl[0].x * a.x - Fl[0].y * a.y + Fl[1].x * b.x - Fl[1].y * b.y;
                 const R la_y = Fl[0].x * a.y + Fl[0].y * a.x + Fl[1].x * b.y + Fl[1].y * b.x;
                 const R lb_x = Fl[2].x * a.x - Fl[2].y * a.y + Fl[3].x * b.x - Fl[3].y * b.y;
                 const R lb_y = Fl[2].x * a.y + Fl[2].y * a.x + Fl[3].x * b.y + Fl[3].y * b.x;
-                q += a.x * la_x + a.y * la_y + b.x * lb_x + b.y * lb_y;
+                acc[f].lo += a.x * la_x + a.y * la_y + b.x * lb_x + b.y * lb_y;
             }
-            acc[f].add(q);
         }
     }
 }
@@ -968,14 +975,15 @@ __device__ __forceinline__ void reg_diag(const typename Cplx<R>::T* v, const Pas
 #pragma unroll
     for (int f = 0; f < REG_MAX_RED; ++f) {
         if (f >= p.red_R) break;
-        R loc = 0;
+        R loc = 0, loc_lo = 0;
 #pragma unroll
         for (int r = 0; r < 4; ++r)
             if (r < D) {
                 loc += W[f * D + r].x * q[r];
-                if constexpr (sizeof(R) == 4) loc += Wl[f * D + r].x * q[r];
+                if constexpr (sizeof(R) == 4) loc_lo += Wl[f * D + r].x * q[r];
             }
         acc[f].add(loc);
+        if constexpr (sizeof(R) == 4) acc[f].lo += loc_lo;  // below an ulp of loc: the low word
     }
 }
 

@@ -1768,19 +1768,51 @@ sv_status sv_run_circuits(sv_batch* bs, const sv_circuit* const* cs, int n, int 
                 cudaGraphExecDestroy(b0->multi_exec);
                 b0->multi_exec = nullptr;
             }
-            cudaGraph_t g;
-            CU(cudaStreamBeginCapture(b0->stream, cudaStreamCaptureModeThreadLocal));
-            for (int i = 0; i < n; ++i)
-                for (const Launch& L : b0->multi_lists[i]) {
-                    cudaError_t e = exec_one(bs[i], L);
-                    if (e != cudaSuccess) {
-                        cudaStreamEndCapture(b0->stream, &g);
-                        return fail(SV_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
-                    }
-                }
-            CU(cudaStreamEndCapture(b0->stream, &g));
-            CU(cudaGraphInstantiate(&b0->multi_exec, g, 0));
-            cudaGraphDestroy(g);
+            // every circuit is its own branch of the graph: its launches are
+            // captured on a stream of its own, forked from and joined back to
+            // the batches' stream, so independent circuits run side by side
+            // (small ones fill the SMs that large ones leave idle)
+            std::vector<cudaStream_t> cs(n, nullptr);
+            std::vector<cudaEvent_t> done(n, nullptr);
+            cudaEvent_t root = nullptr;
+            cudaError_t e = cudaEventCreateWithFlags(&root, cudaEventDisableTiming);
+            for (int i = 0; i < n && e == cudaSuccess; ++i) {
+                e = cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+            }
+            cudaGraph_t g = nullptr;
+            bool capturing = false;
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(b0->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                capturing = true;
+                e = cudaEventRecord(root, b0->stream);
+            }
+            for (int i = 0; i < n && e == cudaSuccess; ++i) {
+                e = cudaStreamWaitEvent(cs[i], root, 0);
+                cudaStream_t own = bs[i]->stream;
+                bs[i]->stream = cs[i];
+                for (size_t j = 0; j < b0->multi_lists[i].size() && e == cudaSuccess; ++j)
+                    e = exec_one(bs[i], b0->multi_lists[i][j]);
+                bs[i]->stream = own;
+                if (e == cudaSuccess) e = cudaEventRecord(done[i], cs[i]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(b0->stream, done[i], 0);
+            }
+            if (capturing) {
+                const cudaError_t e2 = cudaStreamEndCapture(b0->stream, &g);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b0->multi_exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            for (int i = 0; i < n; ++i) {
+                if (cs[i]) cudaStreamDestroy(cs[i]);
+                if (done[i]) cudaEventDestroy(done[i]);
+            }
+            if (root) cudaEventDestroy(root);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                b0->multi_exec = nullptr;
+                return fail(SV_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+            }
             b0->multi_hash = h;
             b0->multi_gens.resize(n);
             for (int i = 0; i < n; ++i) b0->multi_gens[i] = bs[i]->pool_gen;

@@ -325,11 +325,40 @@ def test_run_circuits_one_graph_matches_separate_runs():
     bs = [sv.Batch(c.n_qubits, s, max(1, c.n_clbits), sv.SV_C64, m, 20 + i, mem_budget=1 << 30, stream=stream)
           for i, (c, m, s) in enumerate(zip(cs, modes, shots))]
     bs[2].set_option(sv.SV_OPT_SLOT_LIMIT, 4)  # force a waiting list in one of them
+    for b in bs:
+        b.set_option(sv.SV_OPT_LOG, 1)
     for _ in range(2):  # the second call replays the cached graph
         sv.run_circuits(bs, structs, use_graph=True)
         for b, r in zip(bs, ref):
             assert np.array_equal(b.get_keys(), r)
+    # every shot of every circuit of the graph against the oracle
+    for i, (b, c) in enumerate(zip(bs, cs)):
+        gpu = dict(keys=b.get_keys(), sel={}, thr={})
+        for op in c.random_ops():
+            gpu["sel"][op], gpu["thr"][op] = b.get_outcomes(op, thresholds=True)
+        compare_shots(c, 20 + i, gpu, range(shots[i]), sv.SV_C64, check_amps=False)
     for b in bs:
+        b.close()
+
+
+def test_run_circuits_uneven_sizes_match_oracle():
+    # circuits of 6 to 14 qubits, both modes, side by side in one graph
+    cs = [W.brickwork(n, 3, 0.02, 0.05, seed=200 + n) for n in (6, 9, 12, 14)] + \
+         [W.random_su4(11, 3, 0.05, 0.1, seed=211)]
+    modes = [sv.SV_BATCH, sv.SV_BRANCH, sv.SV_BATCH, sv.SV_BRANCH, sv.SV_BRANCH]
+    shots = [64, 40, 32, 24, 48]
+    import torch
+    stream = torch.cuda.Stream().cuda_stream
+    bs = [sv.Batch(c.n_qubits, s, 1, sv.SV_C64, m, 50 + i, mem_budget=1 << 30, stream=stream)
+          for i, (c, m, s) in enumerate(zip(cs, modes, shots))]
+    for b in bs:
+        b.set_option(sv.SV_OPT_LOG, 1)
+    sv.run_circuits(bs, [sv.circuit_struct(c.to_arrays()) for c in cs], use_graph=True)
+    for i, (b, c) in enumerate(zip(bs, cs)):
+        gpu = dict(keys=b.get_keys(), sel={}, thr={})
+        for op in c.random_ops():
+            gpu["sel"][op], gpu["thr"][op] = b.get_outcomes(op, thresholds=True)
+        compare_shots(c, 50 + i, gpu, range(shots[i]), sv.SV_C64, check_amps=False)
         b.close()
 
 
