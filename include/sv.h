@@ -78,7 +78,7 @@ typedef enum { SV_PLAIN = 0, SV_BATCH = 1, SV_BRANCH = 2, SV_BATCH_BRANCH = 3 } 
 typedef enum { SV_NOISE_PAULI = 0, SV_NOISE_KRAUS = 1 } sv_noise_kind;
 
 /* Op kinds of a flattened circuit (sv_circuit.kind). */
-enum { SV_OP_GATE = 0, SV_OP_PAULI = 1, SV_OP_KRAUS = 2, SV_OP_MEASURE = 3, SV_OP_FINAL = 4 };
+enum { SV_OP_GATE = 0, SV_OP_PAULI = 1, SV_OP_KRAUS = 2, SV_OP_MEASURE = 3, SV_OP_FINAL = 4, SV_OP_PGATE = 5 };
 
 /* A flattened circuit as struct-of-arrays (all host pointers, n_ops long
  * unless stated).  Op i acts on qubits[q_off[i] .. q_off[i]+nq[i]).
@@ -90,7 +90,9 @@ enum { SV_OP_GATE = 0, SV_OP_PAULI = 1, SV_OP_KRAUS = 2, SV_OP_MEASURE = 3, SV_O
  *   KRAUS:   n_terms[i] matrices of 2^k x 2^k at data[d_off[i] ..].
  *   MEASURE: nq[i] qubits into classical bits clbits[cl_off[i] ..]; reset[i]
  *            != 0 returns the measured qubits to |0>.
- *   FINAL:   sample every qubit; the sampled index is the count key.      */
+ *   FINAL:   sample every qubit; the sampled index is the count key.
+ *   PGATE:   n_terms[i] matrices of 2^k x 2^k at data[d_off[i] ..], one per
+ *            parameter set (sv_set_param_sets); a shot applies its own. */
 typedef struct {
     int32_t n_qubits, n_clbits, n_ops;
     const int32_t *kind, *nq, *q_off, *cl_off, *n_terms, *s_off, *cond_clbit, *cond_val, *reset;
@@ -158,6 +160,23 @@ sv_status sv_set_option(sv_batch b, sv_option opt, int64_t value);
  * the tile (SV_OPT_TILE_BITS).                                              */
 sv_status sv_apply_gate_batch(sv_batch b, int k, const int *qubits, const double *mat, int cond_clbit,
                               int cond_value);
+
+/* Section VI (shots of one circuit with varied gate parameters): give every
+ * shot a parameter set.  set_of_shot: host, n_shots entries < n_sets
+ * (n_sets <= 1024; 0 removes the sweep).  Parameterized gates
+ * (sv_apply_param_gate_batch, SV_OP_PGATE) then apply to each shot the
+ * matrix of its set.  In shot-branching modes shots of different sets never
+ * share a state: a run starts with one root branch per set that has shots
+ * (each needs a slot: SV_ENOMEM if n_sets exceeds the batch's slots).  Call
+ * before the first op of a run; the device copy of the map is the
+ * library's.                                                                */
+sv_status sv_set_param_sets(sv_batch b, const uint32_t *set_of_shot, uint32_t n_sets);
+
+/* Section VI: a k-qubit gate (k = 1 or 2) whose matrix depends on the
+ * shot's parameter set: mats is host, n_sets matrices of 2^k x 2^k complex
+ * float64 (n_sets must equal the batch's).  SV_EINVAL for a non-unitary
+ * matrix or a batch without parameter sets.                                */
+sv_status sv_apply_param_gate_batch(sv_batch b, int k, const int *qubits, const double *mats, int n_sets);
 
 /* Sections III-B and IV-A-3/4: every shot samples one term of a noise model
  * with its own draw for ordinal `op`.

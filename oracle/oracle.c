@@ -26,6 +26,9 @@
  *            and renormalise, write the classical bits, optional reset.
  *   FINAL    Section IV-B-2 / Section I: one sample of all qubits from the
  *            final state; the sampled index is the count key.
+ *   PGATE    Section VI (shots of one circuit with varied gate parameters):
+ *            n_terms dense matrices, one per parameter set; the shot's own
+ *            parameter set picks the matrix it applies.
  *
  * Randomness: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), key = (seed lo, seed hi), counter =
@@ -47,7 +50,7 @@
 
 typedef double complex cplx;
 
-enum { O_GATE = 0, O_PAULI = 1, O_KRAUS = 2, O_MEASURE = 3, O_FINAL = 4 };
+enum { O_GATE = 0, O_PAULI = 1, O_KRAUS = 2, O_MEASURE = 3, O_FINAL = 4, O_PGATE = 5 };
 
 typedef struct {
     int32_t n_qubits, n_clbits, n_ops;
@@ -167,6 +170,7 @@ static int find_override(uint32_t op, int32_t n_ovr, const uint32_t *ovr_op, con
 /* one shot                                                            */
 /* ------------------------------------------------------------------ */
 /*
+ * pset: the shot's parameter set (the matrix PGATE ops apply).
  * Outputs (each nullable, each indexed by op ordinal):
  *   outcome[op]  chosen term / outcome / key for random ops, -1 otherwise
  *   u_log[op]    the draw
@@ -176,7 +180,7 @@ static int find_override(uint32_t op, int32_t n_ovr, const uint32_t *ovr_op, con
  * state_out: 2*2^n doubles, the state when FINAL is reached (or at the end).
  * Returns 0, or -1 on allocation failure / unsupported sizes.
  */
-int orc_run_shot(const orc_circuit *c, uint64_t seed, uint64_t shot,
+int orc_run_shot(const orc_circuit *c, uint64_t seed, uint64_t shot, int32_t pset,
                  int32_t n_ovr, const uint32_t *ovr_op, const int32_t *ovr_out,
                  int32_t *outcome, double *u_log, double *c_lo, double *c_hi, double *norms,
                  uint64_t *key_out, uint64_t *clbits_out, double *state_out)
@@ -205,6 +209,11 @@ int orc_run_shot(const orc_circuit *c, uint64_t seed, uint64_t shot,
             cplx m[1024];
             if (k > 5) { rc = -1; break; }
             load_matrix(d, k, m);
+            apply_matrix(psi, n, k, q, m);
+        } else if (kind == O_PGATE) {
+            cplx m[1024];
+            if (k > 5 || pset < 0 || pset >= c->n_terms[op]) { rc = -1; break; }
+            load_matrix(d + (int64_t)pset * (int64_t)(2ull << (2 * k)), k, m);
             apply_matrix(psi, n, k, q, m);
         } else if (kind == O_PAULI) {
             const int nt = c->n_terms[op];
@@ -360,12 +369,13 @@ int orc_run_shot(const orc_circuit *c, uint64_t seed, uint64_t shot,
 /*
  * Shots [shot0, shot0 + n_shots), spread over n_threads OpenMP threads (one
  * shot per thread at a time; threads share nothing but the read-only
- * circuit).  keys[s] gets shot shot0+s's final key; outcomes (nullable) is
+ * circuit).  psets (nullable: all 0) gives shot shot0+s's parameter set at
+ * psets[s].  keys[s] gets shot shot0+s's final key; outcomes (nullable) is
  * n_shots x n_ops; clbits (nullable) is n_shots.  Returns the number of
  * shots that failed (0 on success).
  */
-int orc_run_shots(const orc_circuit *c, uint64_t seed, uint64_t shot0, uint64_t n_shots, int n_threads,
-                  uint64_t *keys, int32_t *outcomes, uint64_t *clbits)
+int orc_run_shots(const orc_circuit *c, uint64_t seed, uint64_t shot0, uint64_t n_shots, const uint32_t *psets,
+                  int n_threads, uint64_t *keys, int32_t *outcomes, uint64_t *clbits)
 {
     int failed = 0;
 #ifdef _OPENMP
@@ -375,7 +385,8 @@ int orc_run_shots(const orc_circuit *c, uint64_t seed, uint64_t shot0, uint64_t 
     for (int64_t s = 0; s < (int64_t)n_shots; ++s) {
         int32_t *oc = outcomes ? outcomes + (uint64_t)s * (uint64_t)c->n_ops : NULL;
         uint64_t key = 0, cl = 0;
-        if (orc_run_shot(c, seed, shot0 + (uint64_t)s, 0, NULL, NULL, oc, NULL, NULL, NULL, NULL, &key, &cl, NULL))
+        const int32_t ps = psets ? (int32_t)psets[s] : 0;
+        if (orc_run_shot(c, seed, shot0 + (uint64_t)s, ps, 0, NULL, NULL, oc, NULL, NULL, NULL, NULL, &key, &cl, NULL))
             failed += 1;
         keys[s] = key;
         if (clbits) clbits[s] = cl;

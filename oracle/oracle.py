@@ -62,10 +62,11 @@ def lib():
             L.orc_philox4x32_10.argtypes = [P, P, P]
             L.orc_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32]
             L.orc_uniform.restype = C.c_double
-            L.orc_run_shot.argtypes = [C.POINTER(_Circ), C.c_uint64, C.c_uint64, C.c_int32, P, P,
+            L.orc_run_shot.argtypes = [C.POINTER(_Circ), C.c_uint64, C.c_uint64, C.c_int32, C.c_int32, P, P,
                                        P, P, P, P, P, P, P, P]
             L.orc_run_shot.restype = C.c_int
-            L.orc_run_shots.argtypes = [C.POINTER(_Circ), C.c_uint64, C.c_uint64, C.c_uint64, C.c_int, P, P, P]
+            L.orc_run_shots.argtypes = [C.POINTER(_Circ), C.c_uint64, C.c_uint64, C.c_uint64, P, C.c_int, P, P,
+                                        P]
             L.orc_run_shots.restype = C.c_int
             L.orc_max_threads.restype = C.c_int
             _lib = L
@@ -111,9 +112,11 @@ def uniform(seed: int, shot: int, op: int) -> float:
     return lib().orc_uniform(seed, shot, op)
 
 
-def run_shot(circuit, seed: int, shot: int, overrides: dict | None = None, want_state: bool = False):
+def run_shot(circuit, seed: int, shot: int, overrides: dict | None = None, want_state: bool = False,
+             pset: int = 0):
     """Simulate one shot.  overrides maps op ordinal -> forced outcome (used to
-    follow the GPU past a flagged draw)."""
+    follow the GPU past a flagged draw); pset is the shot's parameter set
+    (the matrix its parameterized gates apply)."""
     oc = _as_oc(circuit)
     n_ops = oc.n_ops
     outcome = np.full(n_ops, -1, np.int32)
@@ -127,7 +130,7 @@ def run_shot(circuit, seed: int, shot: int, overrides: dict | None = None, want_
     ov = overrides or {}
     ov_op = np.asarray(list(ov.keys()) or [0], np.uint32)
     ov_out = np.asarray(list(ov.values()) or [0], np.int32)
-    rc = lib().orc_run_shot(C.byref(oc.struct), seed, shot, len(ov), _ptr(ov_op), _ptr(ov_out),
+    rc = lib().orc_run_shot(C.byref(oc.struct), seed, shot, int(pset), len(ov), _ptr(ov_op), _ptr(ov_out),
                             _ptr(outcome), _ptr(u), _ptr(lo), _ptr(hi), _ptr(norms),
                             C.byref(key), C.byref(cl), _ptr(state))
     if rc != 0:
@@ -138,13 +141,17 @@ def run_shot(circuit, seed: int, shot: int, overrides: dict | None = None, want_
     return res
 
 
-def run_shots(circuit, seed: int, shot0: int, n_shots: int, threads: int = 0, want_outcomes: bool = True):
-    """Keys (and outcome logs) of shots [shot0, shot0+n_shots)."""
+def run_shots(circuit, seed: int, shot0: int, n_shots: int, threads: int = 0, want_outcomes: bool = True,
+              psets=None):
+    """Keys (and outcome logs) of shots [shot0, shot0+n_shots); psets[s]
+    (optional) is shot shot0+s's parameter set."""
     oc = _as_oc(circuit)
     keys = np.zeros(n_shots, np.uint64)
     outc = np.full((n_shots, oc.n_ops), -1, np.int32) if want_outcomes else None
     cl = np.zeros(n_shots, np.uint64)
-    bad = lib().orc_run_shots(C.byref(oc.struct), seed, shot0, n_shots, threads, _ptr(keys), _ptr(outc), _ptr(cl))
+    ps = None if psets is None else np.ascontiguousarray(psets, np.uint32)
+    bad = lib().orc_run_shots(C.byref(oc.struct), seed, shot0, n_shots, _ptr(ps), threads, _ptr(keys), _ptr(outc),
+                              _ptr(cl))
     if bad:
         raise RuntimeError(f"oracle: {bad} shots failed")
     return keys, outc, cl

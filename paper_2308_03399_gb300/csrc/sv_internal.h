@@ -32,6 +32,11 @@ enum : int32_t {
     ST_PAULI_BR = 2,  // per-branch Pauli string from its 4 parameters (Section IV-A-3)
     ST_PROJ_BR = 3    // per-branch projection onto the measured outcome, optional reset
 };
+// An ST_DENSE_BR stage whose pend is PEND_PSET takes the matrix of the
+// branch's parameter set (br_pset) instead of a sampled choice: a gate whose
+// parameters differ between shots (a parameter sweep)
+constexpr int32_t PEND_PSET = -1;
+constexpr int MAX_PSETS = 1024;  // parameter sets of one batch
 enum : int32_t { RED_NONE = 0, RED_FORMS = 1, RED_BINS = 2, RED_DIAG = 3 };
 // DEC_KRAUS_J1 / _J2: two one-qubit Kraus ops on different qubits decided
 // from one joint reduction p_ij = ||K2_j K1_i psi||^2 (partials indexed
@@ -138,6 +143,9 @@ struct DevBatch {
     uint64_t* br_clbits;
     int32_t* br_parent;
     int32_t* br_big;           // op whose big-branch decide changed the branch's count (-1: none)
+    int32_t* br_pset;          // parameter set of the branch's shots (parameter sweeps)
+    const uint32_t* pset_of_shot;  // parameter set of every shot id, nullable (no sweep)
+    int32_t n_psets;
     int32_t* br_sel;           // [MAX_PEND][cap_br]
     double* br_scale;          // [MAX_PEND][cap_br]
     uint32_t* perm;            // shot ids, grouped by branch

@@ -587,6 +587,8 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
                     sel = d.pre_sel[(int64_t)st.pend * d.cap_br + d.perm[d.br_start[b]]];
                     packed = d.ipool[st.off + sel];
                     if ((packed & 0xff) == 0) sk = 1;
+                } else if (st.pend == PEND_PSET) {  // the branch's parameter set
+                    sel = d.br_pset[b];
                 } else if (st.kind != ST_DENSE) {
                     sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
                     scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
@@ -1058,6 +1060,8 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                     sel = d.pre_sel[(int64_t)st.pend * d.cap_br + d.perm[d.br_start[b]]];
                     packed = d.ipool[st.off + sel];
                     if ((packed & 0xff) == 0) sk = 1;
+                } else if (st.pend == PEND_PSET) {  // the branch's parameter set
+                    sel = d.br_pset[b];
                 } else if (st.kind != ST_DENSE) {
                     sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
                     scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
@@ -1593,6 +1597,7 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
             d.br_clbits[child] = clbits_of(r);
             d.br_parent[child] = b;
             d.br_big[child] = -1;
+            d.br_pset[child] = d.br_pset[b];
             for (int q = 0; q < dd.pend; ++q) {  // earlier pending choices of the parent
                 d.br_sel[(int64_t)q * d.cap_br + child] = d.br_sel[(int64_t)q * d.cap_br + b];
                 d.br_scale[(int64_t)q * d.cap_br + child] = d.br_scale[(int64_t)q * d.cap_br + b];
@@ -1989,6 +1994,9 @@ __global__ void __launch_bounds__(256) k_reset(DevBatch d, int branch_mode, int 
         d.br_clbits[b] = 0;
         d.br_parent[b] = -1;
         d.br_big[b] = -1;
+        // batch mode: the shot's own parameter set (shot-branching with a
+        // sweep resets through k_reset_psets instead)
+        d.br_pset[b] = d.pset_of_shot ? (int32_t)d.pset_of_shot[from_wait ? d.wait_shots[b] : (uint32_t)b] : 0;
         for (int q = 0; q < MAX_PEND; ++q) {
             d.br_sel[(int64_t)q * d.cap_br + b] = 0;
             d.br_scale[(int64_t)q * d.cap_br + b] = 1.0;
@@ -1997,6 +2005,76 @@ __global__ void __launch_bounds__(256) k_reset(DevBatch d, int branch_mode, int 
     const int n_free = d.n_slots - nb;
     for (int64_t j = t0; j < n_free; j += stride) d.free_slots[j] = d.n_slots - 1 - (int)j;
     if (t0 == 0) {
+        d.ctl[CTL_NBR] = nb;
+        d.ctl[CTL_NFREE] = n_free;
+        d.ctl[CTL_NWAIT] = 0;
+        d.ctl[CTL_COPY_FIRST] = 0;
+        d.ctl[CTL_COPY_END] = 0;
+        d.ctl[CTL_NALLOC] = 0;
+        d.ctl[CTL_DONE] = 0;
+    }
+}
+
+// Shot-branching with a parameter sweep: shots with different parameters
+// never share a state, so a run starts with one root branch per parameter
+// set that has shots (each a copy of |0...0>).  One CTA counts the shots of
+// every set, lays the sets out one after another in perm (a counting sort;
+// the order of shots inside a set is not fixed, and no result depends on
+// it) and writes the root branches.
+constexpr int RESET_PSET_THREADS = 1024;
+
+__global__ void __launch_bounds__(RESET_PSET_THREADS) k_reset_psets(DevBatch d, int n_run, int from_wait) {
+    __shared__ int cnt[MAX_PSETS], base[MAX_PSETS], run[MAX_PSETS];
+    __shared__ int nb_sh;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int P = d.n_psets;
+    for (int q = tid; q < P; q += nth) {
+        cnt[q] = 0;
+        run[q] = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < n_run; i += nth) {
+        const uint32_t s = from_wait ? d.wait_shots[i] : (uint32_t)i;
+        atomicAdd(&cnt[d.pset_of_shot[s]], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0, nb = 0;
+        for (int q = 0; q < P; ++q) {
+            base[q] = acc;
+            if (cnt[q] == 0) continue;
+            d.br_slot[nb] = nb;
+            d.br_start[nb] = acc;
+            d.br_count[nb] = cnt[q];
+            d.br_pset[nb] = q;
+            acc += cnt[q];
+            ++nb;
+        }
+        if (nb > d.n_slots) {  // the host checks this; a later slot limit could break it
+            set_err(d, ERR_SLOT, nb);
+            nb = 0;
+        }
+        nb_sh = nb;
+    }
+    __syncthreads();
+    for (int i = tid; i < n_run; i += nth) {
+        const uint32_t s = from_wait ? d.wait_shots[i] : (uint32_t)i;
+        const int q = d.pset_of_shot[s];
+        d.perm[base[q] + atomicAdd(&run[q], 1)] = s;
+    }
+    const int nb = nb_sh;
+    for (int b = tid; b < nb; b += nth) {
+        d.br_clbits[b] = 0;
+        d.br_parent[b] = -1;
+        d.br_big[b] = -1;
+        for (int q = 0; q < MAX_PEND; ++q) {
+            d.br_sel[(int64_t)q * d.cap_br + b] = 0;
+            d.br_scale[(int64_t)q * d.cap_br + b] = 1.0;
+        }
+    }
+    const int n_free = d.n_slots - nb;
+    for (int j = tid; j < n_free; j += nth) d.free_slots[j] = d.n_slots - 1 - j;
+    if (tid == 0) {
         d.ctl[CTL_NBR] = nb;
         d.ctl[CTL_NFREE] = n_free;
         d.ctl[CTL_NWAIT] = 0;
@@ -2141,7 +2219,8 @@ cudaError_t launch_init(const DevBatch& d, int prec, int n_init_slots, int grid,
 
 cudaError_t launch_reset(const DevBatch& d, int mode_branch, int n_shots_run, int from_wait, int grid,
                          cudaStream_t s) {
-    k_reset<<<grid, 256, 0, s>>>(d, mode_branch, n_shots_run, from_wait);
+    if (mode_branch && d.pset_of_shot) k_reset_psets<<<1, RESET_PSET_THREADS, 0, s>>>(d, n_shots_run, from_wait);
+    else k_reset<<<grid, 256, 0, s>>>(d, mode_branch, n_shots_run, from_wait);
     return cudaGetLastError();
 }
 

@@ -188,6 +188,9 @@ struct sv_batch_s {
     int pre_cap = 0;               // rows the device table holds
     std::map<int, int> reg_occ;
     int slot_limit = 0;
+    // parameter sweep (sv_set_param_sets): every shot's parameter set
+    int n_psets = 0;
+    std::vector<uint32_t> h_pset;
     // branch tree of the last run (with SV_OPT_LOG in shot-branching modes):
     // per round (the first pass, then each waiting-list restart) the fork
     // events logged by its end and the shot permutation as it stood then
@@ -530,6 +533,14 @@ void add_stage(sv_batch b, const PendStage& s) {
 
 sv_status tree_begin(sv_batch b);
 
+// slots that hold |0...0> when a run (or a waiting-list restart) begins:
+// every shot's own in batch mode; in shot-branching mode one root, or one
+// per parameter set of a sweep
+int root_slots(sv_batch b, int n_run) {
+    if (!b->branch) return n_run;
+    return b->n_psets > 0 ? std::min(b->n_psets, b->dev.n_slots) : 1;
+}
+
 sv_status ensure_started(sv_batch b) {
     if (b->started) return SV_OK;
     if (!b->rec) {  // per-op calls: a new run, a new fork log
@@ -546,7 +557,7 @@ sv_status ensure_started(sv_batch b) {
     if (st) return st;
     Launch i;
     i.type = L_INIT;
-    i.a0 = branch ? 1 : (int)b->n_shots;
+    i.a0 = root_slots(b, (int)b->n_shots);
     st = emit(b, std::move(i));
     if (st) return st;
     b->started = true;
@@ -724,6 +735,34 @@ sv_status op_gate(sv_batch b, int k, const int* q, const double* mat, int cond_c
     s.cond_clbit = cond_clbit;
     s.cond_val = cond_val;
     s.off = pool_matrix(b, mat, k);
+    add_stage(b, s);
+    return SV_OK;
+}
+
+// Section VI: a gate whose parameters vary between shots.  The matrix of
+// every parameter set goes to the pool; the stage takes, per branch, the
+// matrix of the branch's parameter set (all shots of a branch share it).
+sv_status op_pgate(sv_batch b, int k, const int* q, const double* mats, int n_sets) {
+    sv_status st = check_qubits(b, k, q);
+    if (st) return st;
+    if (k < 1 || k > 2) return fail(SV_EUNSUPPORTED, "parameterized gates act on 1 or 2 qubits");
+    if (!mats) return fail(SV_EINVAL, "matrices are NULL");
+    if (b->n_psets == 0) return fail(SV_EINVAL, "no parameter sets (sv_set_param_sets) on this batch");
+    if (n_sets != b->n_psets) return fail(SV_EINVAL, "one matrix per parameter set of the batch is needed");
+    const int E = 1 << (2 * k);
+    for (int j = 0; j < n_sets; ++j)
+        if (!is_unitary(mats + 2 * (size_t)E * j, k, 1e-10)) return fail(SV_EINVAL, "a parameter set's matrix is not unitary");
+    if ((st = ensure_started(b))) return st;
+    if ((st = make_room(b, q, k, E, false))) return st;
+    PendStage s{};
+    s.kind = ST_DENSE_BR;
+    s.k = k;
+    for (int j = 0; j < k; ++j) s.q[j] = q[j];
+    s.cond_clbit = -1;
+    s.pend = PEND_PSET;
+    s.off = (int)b->pool.size();
+    s.stride = 2 * E;
+    for (size_t i = 0; i < 2 * (size_t)E * n_sets; ++i) b->pool.push_back(mats[i]);
     add_stage(b, s);
     return SV_OK;
 }
@@ -1067,6 +1106,7 @@ sv_status circuit_op(sv_batch b, const sv_circuit* c, int i) {
     case SV_OP_KRAUS: return op_kraus(b, (uint32_t)i, k, q, c->n_terms[i], d);
     case SV_OP_MEASURE: return op_measure(b, (uint32_t)i, k, q, c->clbits + c->cl_off[i], c->reset[i]);
     case SV_OP_FINAL: return op_final(b, (uint32_t)i);
+    case SV_OP_PGATE: return op_pgate(b, k, q, d, c->n_terms[i]);
     }
     return fail(SV_EINVAL, "unknown op kind");
 }
@@ -1096,7 +1136,7 @@ uint64_t circuit_hash(sv_batch b, const sv_circuit* c) {
         int64_t len = 0;
         if (c->kind[i] == SV_OP_GATE) len = 2ll << (2 * k);
         else if (c->kind[i] == SV_OP_PAULI) len = c->n_terms[i];
-        else if (c->kind[i] == SV_OP_KRAUS) len = (int64_t)c->n_terms[i] * (2ll << (2 * k));
+        else if (c->kind[i] == SV_OP_KRAUS || c->kind[i] == SV_OP_PGATE) len = (int64_t)c->n_terms[i] * (2ll << (2 * k));
         dmax = std::max<int64_t>(dmax, c->d_off[i] + len);
     }
     h = fnv(h, c->data, 8 * dmax);
@@ -1132,6 +1172,14 @@ sv_status run_plain(sv_batch b, const sv_circuit* c) {
             if (kind == SV_OP_GATE) {
                 if (c->cond_clbit[i] >= 0 && (int)((clreg >> c->cond_clbit[i]) & 1) != c->cond_val[i]) continue;
                 if ((st = op_gate(b, k, q, d, -1, 0))) return st;
+                if ((st = upload_pool(b))) return st;
+                if ((st = flush(b))) return st;
+            } else if (kind == SV_OP_PGATE) {
+                // the shot's own parameter set, chosen on the host
+                if (b->n_psets == 0 || c->n_terms[i] != b->n_psets)
+                    return fail(SV_EINVAL, "parameterized gate without matching parameter sets");
+                const uint32_t ps = b->h_pset[shot];
+                if ((st = op_gate(b, k, q, d + (size_t)ps * (2ull << (2 * k)), -1, 0))) return st;
                 if ((st = upload_pool(b))) return st;
                 if ((st = flush(b))) return st;
             } else if (kind == SV_OP_PAULI) {
@@ -1308,7 +1356,7 @@ sv_status drain_waiting(sv_batch b, const std::vector<Launch>& launches) {
         if ((st = exec(b, r))) return st;
         Launch in;
         in.type = L_INIT;
-        in.a0 = 1;
+        in.a0 = root_slots(b, n_run);
         if ((st = exec(b, in))) return st;
         for (const Launch& L : launches)
             if ((st = exec(b, L))) return st;
@@ -1420,7 +1468,7 @@ sv_status sv_alloc_batch(int n_qubits, uint64_t n_shots, int n_clbits, sv_prec p
     d.states = states;
     const uint64_t S = n_shots;
     if ((st = dalloc(b, &d.ctl, CTL_WORDS)) || (st = dalloc(b, &d.br_slot, S)) || (st = dalloc(b, &d.br_start, S)) ||
-        (st = dalloc(b, &d.br_count, S)) || (st = dalloc(b, &d.br_clbits, S)) || (st = dalloc(b, &d.br_parent, S)) || (st = dalloc(b, &d.br_big, S)) ||
+        (st = dalloc(b, &d.br_count, S)) || (st = dalloc(b, &d.br_clbits, S)) || (st = dalloc(b, &d.br_parent, S)) || (st = dalloc(b, &d.br_big, S)) || (st = dalloc(b, &d.br_pset, S)) ||
         (st = dalloc(b, &d.br_sel, S * MAX_PEND)) || (st = dalloc(b, &d.br_scale, S * MAX_PEND)) ||
         (st = dalloc(b, &d.perm, S)) || (st = dalloc(b, &d.perm_tmp, S)) || (st = dalloc(b, &d.shot_sel, S)) ||
         (st = dalloc(b, &d.free_slots, b->n_slots)) || (st = dalloc(b, &d.wait_shots, S)) ||
@@ -1532,6 +1580,7 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
     case SV_OPT_PREDRAW_PAULI: b->predraw = v != 0; return SV_OK;
     case SV_OPT_SLOT_LIMIT:
         if (v < 0) return fail(SV_EINVAL, "slot limit must be >= 0");
+        if (v && b->branch && v < b->n_psets) return fail(SV_EINVAL, "fewer slots than parameter sets");
         b->slot_limit = (int)v;
         if (v && b->branch) b->dev.n_slots = std::min<int>(b->n_slots, (int)v);
         else b->dev.n_slots = b->n_slots;
@@ -1545,6 +1594,46 @@ sv_status sv_apply_gate_batch(sv_batch b, int k, const int* qubits, const double
     if (sv_status cs = commit_forks(b)) return cs;
     if (b->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "plain mode runs whole circuits (sv_run_circuit)");
     sv_status st = op_gate(b, k, qubits, mat, cond_clbit, cond_value);
+    if (st) return st;
+    return upload_pool(b);
+}
+
+sv_status sv_set_param_sets(sv_batch b, const uint32_t* set_of_shot, uint32_t n_sets) {
+    if (!b) return fail(SV_EINVAL, "batch is NULL");
+    if (!b->pend.empty() || b->uncommitted || b->started)
+        return fail(SV_EINVAL, "set the parameter sets before the first op of a run");
+    if (n_sets == 0) {
+        b->n_psets = 0;
+        b->h_pset.clear();
+        b->dev.pset_of_shot = nullptr;
+        b->dev.n_psets = 0;
+        b->pool_gen += 1;
+        return SV_OK;
+    }
+    if (!set_of_shot) return fail(SV_EINVAL, "set_of_shot is NULL");
+    if (n_sets > (uint32_t)MAX_PSETS) return fail(SV_EUNSUPPORTED, "at most 1024 parameter sets per batch");
+    if (b->branch && n_sets > (uint32_t)b->dev.n_slots)
+        return fail(SV_ENOMEM, "shot-branching needs a state slot for every parameter set");
+    for (uint64_t s = 0; s < b->n_shots; ++s)
+        if (set_of_shot[s] >= n_sets) return fail(SV_EINVAL, "a shot's parameter set is out of range");
+    uint32_t* d = nullptr;
+    sv_status st = dalloc(b, &d, b->n_shots);
+    if (st) return st;
+    CU(cudaMemcpyAsync(d, set_of_shot, b->n_shots * 4, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    b->h_pset.assign(set_of_shot, set_of_shot + b->n_shots);
+    b->n_psets = (int)n_sets;
+    b->dev.pset_of_shot = d;
+    b->dev.n_psets = (int)n_sets;
+    b->pool_gen += 1;  // cached graphs hold the batch's device struct
+    return SV_OK;
+}
+
+sv_status sv_apply_param_gate_batch(sv_batch b, int k, const int* qubits, const double* mats, int n_sets) {
+    if (!b) return fail(SV_EINVAL, "batch is NULL");
+    if (sv_status cs = commit_forks(b)) return cs;
+    if (b->mode == SV_PLAIN) return fail(SV_EUNSUPPORTED, "plain mode runs whole circuits (sv_run_circuit)");
+    sv_status st = op_pgate(b, k, qubits, mats, n_sets);
     if (st) return st;
     return upload_pool(b);
 }
@@ -1667,7 +1756,7 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
         if ((st = exec(b, r))) return st;
         Launch in;
         in.type = L_INIT;
-        in.a0 = branch ? 1 : n_run;
+        in.a0 = root_slots(b, n_run);
         if ((st = exec(b, in))) return st;
         if (use_graph) {
             if (!cached && round == 0) {
@@ -1753,7 +1842,7 @@ sv_status sv_run_circuits(sv_batch* bs, const sv_circuit* const* cs, int n, int 
             L.push_back(r);
             Launch in;
             in.type = L_INIT;
-            in.a0 = bs[i]->branch ? 1 : (int)bs[i]->n_shots;
+            in.a0 = root_slots(bs[i], (int)bs[i]->n_shots);
             L.push_back(in);
             std::vector<Launch> ops;
             if ((st = record_circuit(bs[i], cs[i], ops))) return st;

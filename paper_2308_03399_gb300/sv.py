@@ -61,6 +61,8 @@ def lib():
                 "sv_set_option": [P, I, C.c_int64],
                 "sv_apply_gate_batch": [P, I, P, P, I, I],
                 "sv_sample_noise": [P, U32, I, I, P, I, P, P, P],
+                "sv_set_param_sets": [P, P, U32],
+                "sv_apply_param_gate_batch": [P, I, P, P, I],
                 "sv_measure_batch": [P, U32, I, P, P, I],
                 "sv_branch": [P, U32],
                 "sv_counts": [P, U32, P, P, U64, P],
@@ -153,6 +155,15 @@ class Batch:
         q = np.asarray(qubits, np.int32)
         m = np.ascontiguousarray(np.stack([np.real(mat), np.imag(mat)], -1).reshape(-1), np.float64)
         _check(lib().sv_apply_gate_batch(self.h, len(q), _p(q), _p(m), cond_clbit, cond_value))
+
+    def set_param_sets(self, set_of_shot, n_sets):
+        m = None if set_of_shot is None else np.ascontiguousarray(set_of_shot, np.uint32)
+        _check(lib().sv_set_param_sets(self.h, _p(m), int(n_sets)))
+
+    def apply_param_gate_batch(self, qubits, mats):
+        q = np.asarray(qubits, np.int32)
+        m = np.ascontiguousarray(np.stack([np.real(mats), np.imag(mats)], -1).reshape(-1), np.float64)
+        _check(lib().sv_apply_param_gate_batch(self.h, len(q), _p(q), _p(m), len(mats)))
 
     def sample_noise_pauli(self, op, qubits, cum, strings):
         q = np.asarray(qubits, np.int32)
@@ -308,5 +319,6 @@ def exported_symbols():
     return ["sv_alloc_batch", "sv_free_batch", "sv_set_option", "sv_apply_gate_batch", "sv_sample_noise",
             "sv_measure_batch", "sv_branch", "sv_counts", "sv_get_keys", "sv_waiting", "sv_run_circuit",
             "sv_get_amplitudes", "sv_get_outcomes", "sv_get_fork_events", "sv_get_branch_tree", "sv_stats", "sv_profile", "sv_sync",
-            "sv_last_error", "sv_run_circuits", "sv_final_sample_noalloc", "sv_mlp_create", "sv_mlp_free", "sv_mlp_num_params",
+            "sv_last_error", "sv_run_circuits", "sv_final_sample_noalloc", "sv_set_param_sets",
+            "sv_apply_param_gate_batch", "sv_mlp_create", "sv_mlp_free", "sv_mlp_num_params",
             "sv_mlp_set_params", "sv_mlp_get_params", "sv_mlp_forward", "sv_mlp_gradient", "sv_mlp_train"]

@@ -26,8 +26,9 @@ What it fixes (conventions the paper leaves open):
   their draws with it.
 
 Op kinds: GATE, PAULI, KRAUS, MEASURE (m qubits into m classical bits,
-optionally followed by a reset of the measured qubits) and FINAL (sample all
-qubits; the sampled n-bit index is the count key).
+optionally followed by a reset of the measured qubits), FINAL (sample all
+qubits; the sampled n-bit index is the count key) and PGATE (one matrix per
+parameter set; a shot applies the matrix of its own set).
 """
 from __future__ import annotations
 
@@ -36,8 +37,9 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-GATE, PAULI, KRAUS, MEASURE, FINAL = 0, 1, 2, 3, 4
-KIND_NAMES = {GATE: "gate", PAULI: "pauli", KRAUS: "kraus", MEASURE: "measure", FINAL: "final"}
+GATE, PAULI, KRAUS, MEASURE, FINAL, PGATE = 0, 1, 2, 3, 4, 5
+KIND_NAMES = {GATE: "gate", PAULI: "pauli", KRAUS: "kraus", MEASURE: "measure", FINAL: "final",
+              PGATE: "param_gate"}
 RANDOM_KINDS = (PAULI, KRAUS, MEASURE, FINAL)
 
 
@@ -131,7 +133,7 @@ class Op:
     mat: np.ndarray | None = None          # GATE
     cum: list | None = None                # PAULI
     strings: list | None = None            # PAULI
-    kraus: list | None = None              # KRAUS
+    kraus: list | None = None              # KRAUS; PGATE: one matrix per parameter set
     clbits: list | None = None             # MEASURE
     reset: int = 0                         # MEASURE
     cond_clbit: int = -1                   # GATE
@@ -164,6 +166,14 @@ class Circuit:
     def kraus(self, qubits, mats):
         mats = [np.asarray(m, dtype=np.complex128) for m in mats]
         self.ops.append(Op(KRAUS, list(qubits), kraus=mats))
+        return len(self.ops) - 1
+
+    def param_gate(self, qubits, mats):
+        """A gate whose matrix depends on the shot's parameter set: mats[j]
+        is the matrix of parameter set j (Section VI's parameter sweeps)."""
+        mats = [np.asarray(m, dtype=np.complex128) for m in mats]
+        assert all(m.shape == (1 << len(qubits),) * 2 for m in mats)
+        self.ops.append(Op(PGATE, list(qubits), kraus=mats))
         return len(self.ops) - 1
 
     def measure(self, qubits, clbits, reset=0):
@@ -221,7 +231,7 @@ class Circuit:
                 s_off[i] = len(paulis)
                 for s in o.strings:
                     paulis.extend(s.encode())
-            elif o.kind == KRAUS:
+            elif o.kind in (KRAUS, PGATE):
                 n_terms[i] = len(o.kraus)
                 for m in o.kraus:
                     data.extend(np.stack([m.real, m.imag], -1).reshape(-1).tolist())
@@ -398,3 +408,31 @@ def config5():
 
 
 CONFIG_SHOTS = {1: 1000, 2: 10_000, 3: 10_000, 5: 2000}
+
+
+def param_sweep(n, layers, n_sets, p, seed, name=None):
+    """A variational-style circuit run for several parameter settings at
+    once (Section VI): each layer is RY(theta_q) RZ(phi_q) on every qubit --
+    one parameterized gate per qubit, its angles drawn uniformly in [0, 2 pi)
+    independently for each of the n_sets parameter sets -- then CX on
+    (0,1),(2,3),... for even layers and (1,2),(3,4),... for odd ones, with
+    depolarizing p after every gate.  Final measurement of every qubit."""
+    rng = np.random.default_rng(seed)
+    c = Circuit(n, name=name or f"sweep{n}x{layers}p{n_sets}")
+    for layer in range(layers):
+        for q in range(n):
+            mats = []
+            for _ in range(n_sets):
+                th, ph = rng.uniform(0, 2 * math.pi, 2)
+                ry = np.array([[math.cos(th / 2), -math.sin(th / 2)], [math.sin(th / 2), math.cos(th / 2)]])
+                rz = np.diag([np.exp(-0.5j * ph), np.exp(0.5j * ph)])
+                mats.append(rz @ ry)
+            c.param_gate([q], mats)
+            if p > 0:
+                c.depolarizing([q], p)
+        for a in range(layer % 2, n - 1, 2):
+            c.gate([a, a + 1], cx())
+            if p > 0:
+                c.depolarizing([a, a + 1], p)
+    c.final()
+    return c

@@ -21,10 +21,13 @@ from paper_2308_03399_gb300 import workloads as W
 TOL = {sv.SV_C128: dict(c=1e-10, amp=1e-12), sv.SV_C64: dict(c=1e-5, amp=1e-5)}
 
 
-def run_gpu(circ, seed, n_shots, mode, prec, use_graph=True, opts=None, want_amps=(), log=True, mem_budget=0):
+def run_gpu(circ, seed, n_shots, mode, prec, use_graph=True, opts=None, want_amps=(), log=True, mem_budget=0,
+            psets=None):
     arrays = circ.to_arrays()
     cs = sv.circuit_struct(arrays)
     with sv.Batch(circ.n_qubits, n_shots, max(1, circ.n_clbits), prec, mode, seed, mem_budget=mem_budget) as b:
+        if psets is not None:
+            b.set_param_sets(psets, int(np.max(psets)) + 1)
         if log:
             b.set_option(sv.SV_OPT_LOG, 1)
         for k, v in (opts or {}).items():
@@ -43,7 +46,7 @@ def run_gpu(circ, seed, n_shots, mode, prec, use_graph=True, opts=None, want_amp
     return res
 
 
-def oracle_refs(circ, seed, shots, state_shots=(), base=0):
+def oracle_refs(circ, seed, shots, state_shots=(), base=0, psets=None):
     """First oracle runs of several shots side by side (threads: the C
     oracle releases the interpreter lock), for sizes where one shot takes
     minutes.  Shots in state_shots also return their final state."""
@@ -52,12 +55,13 @@ def oracle_refs(circ, seed, shots, state_shots=(), base=0):
     oc = O.OracleCircuit(circ)
     shots = [int(s) for s in shots]
     with ThreadPoolExecutor(max(1, min(len(shots), os.cpu_count() or 1))) as ex:
-        futs = {s: ex.submit(O.run_shot, oc, seed, base + s, None, s in state_shots) for s in shots}
+        futs = {s: ex.submit(O.run_shot, oc, seed, base + s, None, s in state_shots,
+                             0 if psets is None else int(psets[s])) for s in shots}
         return {s: f.result() for s, f in futs.items()}
 
 
 def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0, amp_errs=None, outcomes_out=None,
-                  refs=None):
+                  refs=None, psets=None):
     """Compare the GPU's logs of `shots` with the oracle.  Local shot s of the
     GPU batch is the oracle's global shot base + s.  Returns counts of
     checked draws and flagged draws; raises AssertionError on an unexplained
@@ -65,7 +69,8 @@ def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0, amp_err
     L2) amplitude error is appended to it.  With outcomes_out (a dict), the
     oracle's outcome log of each shot (after following flagged draws) is
     stored under the shot.  refs: first oracle runs (oracle_refs) to start
-    from instead of running each shot here."""
+    from instead of running each shot here.  psets[s]: local shot s's
+    parameter set (parameter sweeps)."""
     tol = TOL[prec]
     oc = O.OracleCircuit(circ)
     kinds = circ.to_arrays()["kind"]
@@ -74,7 +79,8 @@ def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0, amp_err
     fin_ops = {op for op in rops if kinds[op] == W.FINAL}
     for s in shots:
         overrides = {}
-        ref = refs[int(s)] if refs is not None else O.run_shot(oc, seed, base + int(s))
+        ps = 0 if psets is None else int(psets[s])
+        ref = refs[int(s)] if refs is not None else O.run_shot(oc, seed, base + int(s), pset=ps)
         for op in rops:
             g = int(gpu["sel"][op][s])
             c = int(ref["outcome"][op])
@@ -94,7 +100,7 @@ def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0, amp_err
             n_flag += 1
             overrides[op] = g
             if op not in fin_ops:  # the final draw changes nothing after it
-                ref = O.run_shot(oc, seed, base + int(s), overrides=overrides)
+                ref = O.run_shot(oc, seed, base + int(s), overrides=overrides, pset=ps)
         if outcomes_out is not None:
             outcomes_out[int(s)] = ref["outcome"].copy()
         fin = [op for op in rops if kinds[op] == W.FINAL]
@@ -104,7 +110,7 @@ def compare_shots(circ, seed, gpu, shots, prec, check_amps=True, base=0, amp_err
             if "state" in ref and not set(overrides) - fin_ops:
                 st = ref["state"]  # the state before the final draw
             else:
-                st = O.run_shot(oc, seed, base + int(s), overrides=overrides, want_state=True)["state"]
+                st = O.run_shot(oc, seed, base + int(s), overrides=overrides, want_state=True, pset=ps)["state"]
             err = np.abs(gpu["amps"][s] - st).max()
             if amp_errs is not None:
                 amp_errs.append((float(err), float(np.linalg.norm(gpu["amps"][s] - st) / np.linalg.norm(st))))

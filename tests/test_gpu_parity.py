@@ -441,3 +441,62 @@ def test_predrawn_pauli_choices_match_decides(name, prec):
     assert np.array_equal(a["keys"], b["keys"])
     assert a["stats"]["launches"] < b["stats"]["launches"]
     compare_shots(c, 13, a, range(0, 150, 7), prec)
+
+
+# ---------------------------------------------------------------------------
+# Parameter sweeps (Section VI: shots of one circuit with varied gate
+# parameters): each shot applies the matrices of its own parameter set
+# ---------------------------------------------------------------------------
+def _psets(n_shots, n_sets, seed):
+    return np.random.default_rng(seed).integers(0, n_sets, n_shots).astype(np.uint32)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("mode", MODES)
+def test_param_sweep_matches_oracle(mode, prec):
+    c = W.param_sweep(6, 4, 5, 0.05, seed=300)
+    n_shots = 200
+    ps = _psets(n_shots, 5, 1)
+    gpu = run_gpu(c, 3, n_shots, mode, prec, psets=ps, want_amps=[0, 1, 2, 199])
+    compare_shots(c, 3, gpu, range(n_shots), prec, psets=ps)
+    if mode == sv.SV_BRANCH:
+        # one root per parameter set: no state is shared across sets
+        assert gpu["stats"]["live_branches"] >= len(set(ps.tolist()))
+
+
+def test_param_sweep_waiting_list_and_per_op_calls():
+    c = W.param_sweep(5, 3, 4, 0.1, seed=301)
+    n_shots = 160
+    ps = _psets(n_shots, 4, 2)
+    gpu = run_gpu(c, 8, n_shots, sv.SV_BRANCH, sv.SV_C128, psets=ps, opts={sv.SV_OPT_SLOT_LIMIT: 6})
+    assert gpu["stats"]["restarts"] > 0
+    compare_shots(c, 8, gpu, range(n_shots), sv.SV_C128, check_amps=False, psets=ps)
+    # the same circuit through the per-op calls gives the same keys
+    with sv.Batch(5, n_shots, 1, sv.SV_C128, sv.SV_BRANCH, 8) as b:
+        b.set_param_sets(ps, 4)
+        for i, o in enumerate(c.ops):
+            if o.kind == W.PGATE:
+                b.apply_param_gate_batch(o.qubits, o.kraus)
+            elif o.kind == W.GATE:
+                b.apply_gate_batch(o.qubits, o.mat)
+            elif o.kind == W.PAULI:
+                b.sample_noise_pauli(i, o.qubits, o.cum, o.strings)
+            else:
+                b.counts(i)
+        keys = b.get_keys()
+    okeys, _, _ = O.run_shots(c, 8, 0, n_shots, want_outcomes=False, psets=ps)
+    assert np.array_equal(keys, okeys)
+    # plain per-shot form
+    gp = run_gpu(c, 8, 40, sv.SV_PLAIN, sv.SV_C128, log=False, psets=ps[:40])
+    assert np.array_equal(gp["keys"], okeys[:40])
+
+
+def test_param_sweep_rejects_bad_sets():
+    with sv.Batch(3, 8, 1, sv.SV_C64, sv.SV_BRANCH, 1) as b:
+        with pytest.raises(sv.SvError):
+            b.set_param_sets(np.full(8, 3, np.uint32), 3)  # set 3 of 3
+        with pytest.raises(sv.SvError):
+            b.apply_param_gate_batch([0], [np.eye(2)])  # no sets yet
+        b.set_param_sets(np.arange(8) % 2, 2)
+        with pytest.raises(sv.SvError):
+            b.apply_param_gate_batch([0], [np.eye(2)] * 3)  # 3 matrices for 2 sets

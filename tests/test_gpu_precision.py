@@ -97,6 +97,7 @@ def test_accumulation_matches_float64_sums(name):
         c = extra
     n, n_shots, watch = c.n_qubits, 32, (0, 9, 21, 31)
     worst = {W.KRAUS: 0.0, W.MEASURE: 0.0, W.FINAL: 0.0}
+    detail = []
     count = {W.KRAUS: 0, W.MEASURE: 0, W.FINAL: 0}
     with sv.Batch(n, n_shots, max(1, c.n_clbits), sv.SV_C64, sv.SV_BATCH, 17) as b:
         b.set_option(sv.SV_OPT_LOG, 1)
@@ -124,7 +125,10 @@ def test_accumulation_matches_float64_sums(name):
                 gap = max(abs(thr[s][0] - lo), abs(thr[s][1] - cum[k]))
                 worst[o.kind] = max(worst[o.kind], gap)
                 count[o.kind] += 1
+                detail.append((gap, i, o.kind, tuple(o.qubits[:2]), s, k, float(thr[s][1]), float(cum[k])))
     names = {W.KRAUS: "Kraus", W.MEASURE: "measurement", W.FINAL: "final sample"}
     print(f"\n{name}: largest |C_gpu - C_float64| over the same complex64 state: " +
           ", ".join(f"{names[k]} {worst[k]:.2e} ({count[k]} decisions)" for k in worst if count[k]))
+    for d in sorted(detail, reverse=True)[:6]:
+        print("  gap %.2e op %d kind %d qubits %s shot %d choice %d C_gpu %.17g C_f64 %.17g" % d)
     assert max(worst.values()) <= 5e-9

@@ -85,3 +85,27 @@ def test_final_sampling_follows_cumulative_rule():
         r = O.run_shot(c, 9, s)
         u = r["u"][op]
         assert r["key"] == int(np.searchsorted(cum, u, side="right")) or abs(u - cum[r["key"]]) < 1e-12
+
+
+@pytest.mark.parametrize("pset", [0, 1, 2])
+def test_param_gates_match_the_substituted_circuit(pset):
+    # a parameterized gate applies the matrix of the shot's parameter set
+    # (Section VI): the oracle's state equals the tensor contraction of the
+    # circuit with that set's matrices written in as plain gates
+    rng = np.random.default_rng(7)
+    c, plain = W.Circuit(5), W.Circuit(5)
+    for _ in range(12):
+        k = int(rng.integers(1, 3))
+        q = rng.choice(5, k, replace=False).tolist()
+        mats = [_random_unitary(rng, k) for _ in range(3)]
+        c.param_gate(q, mats)
+        plain.gate(q, mats[pset])
+        u = _random_unitary(rng, 1)
+        c.gate([int(rng.integers(5))], u)
+        plain.gate(c.ops[-1].qubits, u)
+    c.final()
+    plain.final()
+    got = O.run_shot(c, 1, 0, want_state=True, pset=pset)["state"]
+    assert np.abs(got - dm.final_state_unitary(plain)).max() < 1e-12
+    with pytest.raises(RuntimeError):
+        O.run_shot(c, 1, 0, pset=3)  # no such parameter set

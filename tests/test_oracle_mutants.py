@@ -35,6 +35,7 @@ MUTANTS = {
     "final_fallback_last_entry": ("if (chosen < 0) chosen = last_nonzero >= 0 ? last_nonzero : (int64_t)dim - 1;",
                                   "if (chosen < 0) chosen = (int64_t)dim - 1;"),
     "final_override_keeps_old_sums": ("if (ov >= 0 || u >= sum) {", "if (ov < 0 && u >= sum) {"),
+    "pgate_ignores_set": ("load_matrix(d + (int64_t)pset * (int64_t)(2ull << (2 * k)), k, m);", "load_matrix(d, k, m);"),
 }
 
 
