@@ -387,6 +387,88 @@ def run_config4(args):
     print(json.dumps(line), flush=True)
 
 
+def run_qft_sweep(args):
+    """The paper's own evaluation (Section V-B, V-D) restated on GB300: QFT
+    circuits with 1% depolarizing noise after every gate, as a Pauli model
+    and as the equivalent Kraus model, 4000 shots, complex64.  For each
+    qubit count: shots/s of batched shots (one state per shot, while they
+    fit), shot-branching, and the plain per-shot float64 form (timed on a
+    sample of shots, shots being independent); the pass kernels' fraction of
+    the measured HBM copy bandwidth.  Then the error-ratio sweep at one
+    size: Pauli and Kraus noise at p = 1e-3 .. 3e-2, batched and branched."""
+    import torch
+    from paper_2308_03399_gb300 import sv
+    from paper_2308_03399_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    hbm_peak, peak_kind = peaks()
+    shots = 4000
+    free = torch.cuda.mem_get_info()[0]
+
+    def timed(circ, mode, prec, n_shots, steps):
+        cs = sv.circuit_struct(circ.to_arrays())
+        b = sv.Batch(circ.n_qubits, n_shots, 1, prec, mode, 5, stream=stream.cuda_stream)
+        graph = mode != sv.SV_PLAIN
+        b.run_circuit(cs, use_graph=graph)
+        b.stats()
+        ms = []
+        for _ in range(steps):
+            flush_buf.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run_circuit(cs, use_graph=graph)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = b.stats()
+        out = {"shots_per_s": n_shots / (np.mean(ms) / 1e3), "ms_per_step": float(np.mean(ms)),
+               "passes_per_step": st["passes"] / steps, "restarts_per_step": st["restarts"] / steps}
+        if mode != sv.SV_PLAIN:
+            b.set_option(sv.SV_OPT_PROFILE, 1)
+            b.profile()
+            b.run_circuit(cs, use_graph=False)
+            pr = b.profile()
+            stp = b.stats()
+            if pr["pass"][0] > 0:
+                out["hbm_frac"] = stp["pass_bytes"] / (pr["pass"][0] / 1e3) / 1e9 / hbm_peak
+        b.close()
+        return out
+
+    rows = []
+    sizes = [int(x) for x in args.qft_sizes.split(",")]
+    for n in sizes:
+        for kind in ("pauli", "kraus"):
+            circ = W.qft(n, 0.01, seed=n, kraus=(kind == "kraus"))
+            row = {"n": n, "noise": kind, "ops": circ.n_ops}
+            if shots * (8 << n) < 0.6 * free:
+                row["batch"] = timed(circ, sv.SV_BATCH, sv.SV_C64, shots, 2)
+            row["branch"] = timed(circ, sv.SV_BRANCH, sv.SV_C64, shots, 2)
+            # the plain form pays a launch per op (per Kraus term and a host
+            # round trip for Kraus noise): a sample of the shots
+            plain_shots = max(2, min(40, int((4e4 if kind == "pauli" else 1e4) / circ.n_ops)))
+            row["plain_fp64"] = timed(circ, sv.SV_PLAIN, sv.SV_C128, plain_shots, 1)
+            row["plain_fp64"]["sample_shots"] = plain_shots
+            best = max(v["shots_per_s"] for k, v in row.items() if k in ("batch", "branch"))
+            row["best_over_plain"] = best / row["plain_fp64"]["shots_per_s"]
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    ratio = []
+    n_r = args.qft_ratio_n
+    for p in (1e-3, 3e-3, 1e-2, 3e-2):
+        for kind in ("pauli", "kraus"):
+            circ = W.qft(n_r, p, seed=n_r, kraus=(kind == "kraus"))
+            r = {"n": n_r, "p": p, "noise": kind, "batch": timed(circ, sv.SV_BATCH, sv.SV_C64, shots, 2),
+                 "branch": timed(circ, sv.SV_BRANCH, sv.SV_C64, shots, 2)}
+            ratio.append(r)
+            print(json.dumps(r), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": METRIC, "workload": "qft_sweep", "unit": "shots/s", "shots": shots,
+                      "precision": "c64 (plain form: c128)", "hbm_peak_gbs": hbm_peak, "peak_kind": peak_kind,
+                      "sizes": rows, "error_ratio": ratio}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -405,6 +487,8 @@ def main():
     ap.add_argument("--max-active", type=int, default=0, help="fusion width (qubits per pass), 0 = library default")
     ap.add_argument("--autotune", action="store_true", help="config 4: also run the autotuner's picks")
     ap.add_argument("--no-legs", action="store_true", help="skip the config 1 / 3 / 5 legs of the default run")
+    ap.add_argument("--qft-sizes", default="10,12,14,16,18,20", help="qubit counts of the QFT sweep")
+    ap.add_argument("--qft-ratio-n", type=int, default=14, help="qubit count of the error-ratio sweep")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -415,6 +499,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "cfg4":
         return run_config4(args)
+    if args.workload == "qft":
+        return run_qft_sweep(args)
 
     import torch
     if not torch.cuda.is_available():
