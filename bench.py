@@ -451,6 +451,17 @@ def run_qft_sweep(args):
             plain_shots = max(2, min(40, int((4e4 if kind == "pauli" else 1e4) / circ.n_ops)))
             row["plain_fp64"] = timed(circ, sv.SV_PLAIN, sv.SV_C128, plain_shots, 1)
             row["plain_fp64"]["sample_shots"] = plain_shots
+            if n <= 14:
+                # the density-matrix method (exact distribution, 4^n memory)
+                # for the same 4000 shots: the crossover against multi-shot
+                cs = sv.circuit_struct(circ.to_arrays())
+                sv.dm_run(cs, shots, sv.SV_C64, 5, stream=stream.cuda_stream)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sv.dm_run(cs, shots, sv.SV_C64, 5, stream=stream.cuda_stream)
+                dt = time.perf_counter() - t0
+                row["density_matrix"] = {"shots_per_s": shots / dt, "ms_per_run": 1e3 * dt,
+                                         "note": "host wall time of sv_dm_run, allocation included"}
             best = max(v["shots_per_s"] for k, v in row.items() if k in ("batch", "branch"))
             row["best_over_plain"] = best / row["plain_fp64"]["shots_per_s"]
             rows.append(row)

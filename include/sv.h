@@ -330,6 +330,25 @@ sv_status sv_final_sample_noalloc(const void *states, sv_prec prec, int n_qubits
                                   const uint64_t *shots, uint64_t seed, uint32_t op, uint64_t *keys,
                                   void *cuda_stream);
 
+/* Density-matrix method (Sections II and III-C: exact, but 4^n memory): the
+ * circuit's density matrix rho evolves on the GPU (gates U rho U^dagger,
+ * Pauli and Kraus channels sum_i K_i rho K_i^dagger, held as a state of 2n
+ * qubits vec(rho)[r + c 2^n] = rho[r][c]), then every shot is sampled from
+ * the exact final distribution p_j = rho[j][j]: shot s takes the first j
+ * with u < C_j, u its Philox draw for the final op (counter (s, op)) and C
+ * the running float64 sum in index order.
+ *   c           gates (unconditional), Pauli and Kraus noise on 1 or 2
+ *               qubits, and a last FINAL op; n_qubits <= 15
+ *   keys        host, n_shots sampled indices (n_shots may be 0)
+ *   probs       host, 2^n float64 (the distribution), nullable
+ *   thresholds  host, 2 x n_shots running sums just below and at each key,
+ *               nullable
+ * Allocates its own device memory for the call (4^n amplitudes) and frees
+ * it.  SV_EUNSUPPORTED for measurements, conditional or parameterized gates,
+ * or n_qubits > 15.  Synchronises.                                          */
+sv_status sv_dm_run(const sv_circuit *c, sv_prec prec, uint64_t seed, uint64_t n_shots, uint64_t *keys,
+                    double *probs, double *thresholds, void *cuda_stream);
+
 /* Learned cost model ------------------------------------------------------
  * A small MLP, n_in -> n_hidden -> n_hidden -> 1 with ReLU, that predicts the
  * log run time of a circuit under a candidate configuration (batch or

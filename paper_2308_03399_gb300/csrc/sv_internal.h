@@ -198,5 +198,9 @@ size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads);
 int pass_reg_blocks_per_sm(int prec, int wp, int paired, size_t smem);
 int pass_reg_threads(int prec);  // CTA size of the register path
 cudaError_t init_kernels();
+// density-matrix method (sv_dm.cu): diagonal, running sums, one key per shot
+cudaError_t launch_dm_final(const void* rho, int prec, int n, double* p, double* sums, double* cum, int chunks,
+                            uint64_t n_shots, uint64_t seed, uint32_t op, uint64_t* keys, double* thr, int n_sm,
+                            cudaStream_t s);
 
 }  // namespace sv

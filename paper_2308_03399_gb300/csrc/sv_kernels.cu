@@ -171,6 +171,62 @@ template <int K> struct GroupIdx {
     }
 };
 
+// the monomial structure of a 4x4 matrix m (row-major), or 0 when it is not
+// monomial; phases go to ph[0..3]
+template <class T>
+__device__ __forceinline__ int mono_info(const T* m, T* ph) {
+    int pi[4];
+    for (int q = 0; q < 4; ++q) {
+        pi[q] = -1;
+        for (int c = 0; c < 4; ++c)
+            if (m[q * 4 + c].x != 0 || m[q * 4 + c].y != 0) {
+                if (pi[q] >= 0) return 0;
+                pi[q] = c;
+            }
+        if (pi[q] < 0) return 0;
+    }
+    if ((pi[0] ^ pi[1] ^ pi[2] ^ pi[3]) != 0 || pi[0] == pi[1] || pi[0] == pi[2] || pi[0] == pi[3] ||
+        pi[1] == pi[2] || pi[1] == pi[3] || pi[2] == pi[3])
+        return 0;
+    const int b = pi[0], a1 = pi[1] ^ b, a2 = pi[2] ^ b;
+    if ((a1 ^ a2) != (pi[3] ^ b)) return 0;  // not affine (never for 4 points, kept as a guard)
+    int word = -1;
+    const int tab[6][2] = {{1, 2}, {3, 2}, {1, 3}, {3, 1}, {2, 3}, {2, 1}};
+    for (int w = 0; w < 6; ++w)
+        if (tab[w][0] == a1 && tab[w][1] == a2) word = w;
+    if (word < 0) return 0;
+    int unit = 1;
+    for (int q = 0; q < 4; ++q) {
+        ph[q] = m[q * 4 + pi[q]];
+        if (ph[q].x != 1 || ph[q].y != 0) unit = 0;
+    }
+    return 1 | (unit << 1) | (b << 2) | (word << 4) | (pi[0] << 8) | (pi[1] << 10) | (pi[2] << 12) | (pi[3] << 14);
+}
+
+// a monomial 4x4 matrix (see mono_info) on a tile: out[q] = ph[q] in[pi(q)]
+template <class R>
+__device__ __noinline__ void stage_mono(typename Cplx<R>::T* tile, int tb, const int32_t* pos, int info,
+                                        const typename Cplx<R>::T* ph) {
+    using T = typename Cplx<R>::T;
+    const GroupIdx<2> gi(pos);
+    int offp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int pq = (info >> (8 + 2 * q)) & 3;
+        offp[q] = (pq & 1 ? 1 << pos[0] : 0) | (pq & 2 ? 1 << pos[1] : 0);
+    }
+    const bool unit = (info >> 1) & 1;
+    const int groups = 1 << (tb - 2);
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+        const int base = insert_zeros<2>(g, gi.sp);
+        T a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = tile[base | offp[q]];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tile[base | gi.off[q]] = unit ? a[q] : cmul(ph[q], a[q]);
+    }
+}
+
 // dense 2^K x 2^K matrix (staged in shared memory, already scaled)
 template <class R, int K>
 __device__ __noinline__ void stage_dense(typename Cplx<R>::T* tile, int tb, const int32_t* pos,
@@ -259,8 +315,11 @@ __device__ __noinline__ void stage_proj(typename Cplx<R>::T* tile, int tb, const
 
 template <class R>
 __device__ __forceinline__ void stage_dispatch(typename Cplx<R>::T* tile, int tb, const Stage& st,
-                                               const typename Cplx<R>::T* M, int sel, double scale, int packed) {
-    if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
+                                               const typename Cplx<R>::T* M, int sel, double scale, int packed,
+                                               int mono) {
+    if (mono) {
+        stage_mono<R>(tile, tb, st.pos, mono, M);
+    } else if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
         if (st.k == 1) stage_dense<R, 1>(tile, tb, st.pos, M);
         else if (st.k == 2) stage_dense<R, 2>(tile, tb, st.pos, M);
         else if (st.k == 3) stage_dense<R, 3>(tile, tb, st.pos, M);
@@ -404,10 +463,18 @@ __device__ __noinline__ void reduce_bins(const typename Cplx<R>::T* tile, int tb
     }
 }
 
+// the weight of diagonal form f on bin r in float64: the pool's value
+// (float32 for complex64) plus its float32 residual
+template <class T>
+__device__ __forceinline__ double diag_weight(const T* W, int R, int k, int f, int r) {
+    const double w = (double)W[(f << k) + r].x;
+    return sizeof(T) == 8 ? w + (double)W[(R << k) + (f << k) + r].x : w;
+}
+
 template <class R>
 __device__ __forceinline__ void reduce_dispatch(const typename Cplx<R>::T* tile, int tb, const PassDesc& p,
                                                 const typename Cplx<R>::T* F, typename AccSlot<R>::T* acc) {
-    if (p.red_kind == RED_BINS) {
+    if (p.red_kind == RED_BINS || p.red_kind == RED_DIAG) {  // diagonal forms: the bins of |psi|^2
         if (p.red_k == 1) reduce_bins<R, 1>(tile, tb, p.red_pos, acc);
         else if (p.red_k == 2) reduce_bins<R, 2>(tile, tb, p.red_pos, acc);
         else if (p.red_k == 3) reduce_bins<R, 3>(tile, tb, p.red_pos, acc);
@@ -499,7 +566,7 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
     A* acc = reinterpret_cast<A*>(mats + p.mat_elems);
     int* hi_tab = reinterpret_cast<int*>(acc + (red ? p.red_R * (int)blockDim.x : 0));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + ((pass_bytes_before_bars(p, blockDim.x, sizeof(T)) + 7) & ~7ull));
-    __shared__ int skip[MAX_STAGES], sel_sh[MAX_STAGES], packed_sh[MAX_STAGES];
+    __shared__ int skip[MAX_STAGES], sel_sh[MAX_STAGES], packed_sh[MAX_STAGES], mono_sh[MAX_STAGES];
     __shared__ double scale_sh[MAX_STAGES];
     __shared__ double wsum[8][MAX_RED];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -618,8 +685,8 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
                     mats[st.mat + e] = m;
                 }
             }
-            if (p.red_kind == RED_FORMS) {  // the forms, then their float32 residuals
-                const int E2 = 2 * (p.red_R << (2 * p.red_k));
+            if (p.red_kind == RED_FORMS || p.red_kind == RED_DIAG) {  // coefficients, then residuals
+                const int E2 = 2 * (p.red_R << ((p.red_kind == RED_FORMS ? 2 : 1) * p.red_k));
                 const R* src = pool + p.red_off;
                 for (int e = threadIdx.x; e < E2; e += blockDim.x) {
                     T m;
@@ -629,11 +696,27 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
                 }
             }
             __syncthreads();
+            // monomial two-qubit matrices (CX, CZ, SWAP, controlled phases)
+            // move amplitudes instead of multiplying: structure and phases
+            for (int st_i = threadIdx.x; st_i < p.n_stages; st_i += blockDim.x) {
+                const Stage& st = p.st[st_i];
+                int mi = 0;
+                if (!skip[st_i] && st.k == 2 && (st.kind == ST_DENSE || st.kind == ST_DENSE_BR)) {
+                    T m[16], ph[4];
+                    for (int e = 0; e < 16; ++e) m[e] = mats[st.mat + e];
+                    mi = mono_info(m, ph);
+                    if (mi)
+                        for (int q = 0; q < 4; ++q) mats[st.mat + q] = ph[q];  // this stage's own entries
+                }
+                mono_sh[st_i] = mi;
+            }
+            __syncthreads();
             cur_b = b;
         }
+        const int n_bins = p.red_kind == RED_DIAG ? 1 << p.red_k : p.red_R;  // warp-owned bins
         if (red && i % tpc == 0) {
-            if (p.red_kind == RED_BINS)
-                for (int r = warp; r < p.red_R; r += (int)(blockDim.x >> 5)) acc[r * 32 + lane] = A{};
+            if (p.red_kind == RED_BINS || p.red_kind == RED_DIAG)
+                for (int r = warp; r < n_bins; r += (int)(blockDim.x >> 5)) acc[r * 32 + lane] = A{};
             else
                 for (int r = 0; r < p.red_R; ++r) acc[r * blockDim.x + threadIdx.x] = A{};
         }
@@ -642,7 +725,7 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
         for (int st_i = 0; st_i < p.n_stages; ++st_i) {
             if (skip[st_i]) continue;
             const Stage& st = p.st[st_i];
-            stage_dispatch<R>(tile, tb, st, mats + st.mat, sel_sh[st_i], scale_sh[st_i], packed_sh[st_i]);
+            stage_dispatch<R>(tile, tb, st, mats + st.mat, sel_sh[st_i], scale_sh[st_i], packed_sh[st_i], mono_sh[st_i]);
             __syncthreads();
         }
         if (red) reduce_dispatch<R>(tile, tb, p, mats + p.mat_elems - 2 * (p.red_R << (2 * p.red_k)), acc);
@@ -663,6 +746,21 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
                 for (int r = warp; r < p.red_R; r += (int)(blockDim.x >> 5)) {
                     const double v = warp_combine(acc[r * 32 + lane]);
                     if (lane == 0 && slot_ok) part[r] = v;
+                }
+            } else if (p.red_kind == RED_DIAG) {
+                // the bins as for a measurement, then every diagonal form
+                // from them with float64 weights (thread f: form f)
+                for (int r = warp; r < n_bins; r += (int)(blockDim.x >> 5)) {
+                    const double v = warp_combine(acc[r * 32 + lane]);
+                    if (lane == 0) wsum[0][r] = v;
+                }
+                __syncthreads();
+                if (threadIdx.x < p.red_R && slot_ok) {
+                    const T* W = mats + p.mat_elems - 2 * (p.red_R << p.red_k);
+                    double v = 0.0;
+                    for (int r = 0; r < n_bins; ++r)
+                        v += diag_weight(W, p.red_R, p.red_k, (int)threadIdx.x, r) * wsum[0][r];
+                    part[threadIdx.x] = v;
                 }
             } else {
                 // fixed-order combination: lanes by shuffles, warps in order
@@ -825,6 +923,76 @@ __device__ __forceinline__ void reg_apply2x_dyn(float2* v, int j0, int j1, const
     }
 }
 
+// A monomial 2-qubit matrix (one nonzero per row and column: CX, SWAP, CZ,
+// controlled phases, ...) is applied as a gather plus phases:
+// out[q] = M[q][pi(q)] in[pi(q)].  Every permutation pi of the 4 indices is
+// affine over GF(2), pi(q) = A q xor b, and A is a word of at most three
+// elementary maps E01: (q0, q1) -> (q0, q1 xor q0) and E10: (q0, q1) ->
+// (q0 xor q1, q1), each a swap of register pairs.  Words of A by index:
+// I, E01, E10, E01.E10, E10.E01, E01.E10.E01 (the swap of the two bits).
+template <class T, int G, int J>
+__device__ __forceinline__ void reg_flip_t(T* v) {
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+        if (r & (1 << J)) continue;
+        const T t = v[r];
+        v[r] = v[r | (1 << J)];
+        v[r | (1 << J)] = t;
+    }
+}
+
+// v[r] <-> v[r | T] for every r with bit C set and bit T clear: the gather
+// of an elementary map with control bit C and target bit T
+template <class T, int G, int C, int TB>
+__device__ __forceinline__ void reg_cswap(T* v) {
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+        if (!(r & (1 << C)) || (r & (1 << TB))) continue;
+        const T t = v[r];
+        v[r] = v[r | (1 << TB)];
+        v[r | (1 << TB)] = t;
+    }
+}
+
+// info: bit 1 unit phases, bits 2-3 b, bits 4-6 the word of A; ph[q] the
+// phase of output q (matrix bit 0 on group bit J0, bit 1 on J1)
+template <class T, int G, int J0, int J1>
+__device__ __forceinline__ void reg_mono(T* v, int info, const T* ph) {
+    const int b = (info >> 2) & 3, word = (info >> 4) & 7;
+    if (b & 1) reg_flip_t<T, G, J0>(v);
+    if (b & 2) reg_flip_t<T, G, J1>(v);
+    switch (word) {  // E01 = reg_cswap<J0, J1>, E10 = reg_cswap<J1, J0>, applied left to right
+    case 1: reg_cswap<T, G, J0, J1>(v); break;
+    case 2: reg_cswap<T, G, J1, J0>(v); break;
+    case 3: reg_cswap<T, G, J0, J1>(v); reg_cswap<T, G, J1, J0>(v); break;
+    case 4: reg_cswap<T, G, J1, J0>(v); reg_cswap<T, G, J0, J1>(v); break;
+    case 5: reg_cswap<T, G, J0, J1>(v); reg_cswap<T, G, J1, J0>(v); reg_cswap<T, G, J0, J1>(v); break;
+    default: break;
+    }
+    if (!(info & 2)) {
+#pragma unroll
+        for (int e = 0; e < G; ++e) v[e] = cmul(ph[((e >> J0) & 1) | (((e >> J1) & 1) << 1)], v[e]);
+    }
+}
+
+template <class T, int G>
+__device__ __forceinline__ void reg_mono_dyn(T* v, int j0, int j1, int info, const T* ph) {
+    switch (j0 * 4 + j1) {
+    case 1: if constexpr (G > 2) reg_mono<T, G, 0, 1>(v, info, ph); break;
+    case 4: if constexpr (G > 2) reg_mono<T, G, 1, 0>(v, info, ph); break;
+    case 2: if constexpr (G > 4) reg_mono<T, G, 0, 2>(v, info, ph); break;
+    case 8: if constexpr (G > 4) reg_mono<T, G, 2, 0>(v, info, ph); break;
+    case 6: if constexpr (G > 4) reg_mono<T, G, 1, 2>(v, info, ph); break;
+    case 9: if constexpr (G > 4) reg_mono<T, G, 2, 1>(v, info, ph); break;
+    case 3: if constexpr (G > 8) reg_mono<T, G, 0, 3>(v, info, ph); break;
+    case 12: if constexpr (G > 8) reg_mono<T, G, 3, 0>(v, info, ph); break;
+    case 7: if constexpr (G > 8) reg_mono<T, G, 1, 3>(v, info, ph); break;
+    case 13: if constexpr (G > 8) reg_mono<T, G, 3, 1>(v, info, ph); break;
+    case 11: if constexpr (G > 8) reg_mono<T, G, 2, 3>(v, info, ph); break;
+    default: if constexpr (G > 8) reg_mono<T, G, 3, 2>(v, info, ph); break;
+    }
+}
+
 template <class T, int G, int J>
 __device__ __forceinline__ void reg_flip(T* v) {
 #pragma unroll
@@ -932,10 +1100,13 @@ __device__ __forceinline__ void reg_forms1_dyn(const typename Cplx<R>::T* v, int
 
 constexpr int REG_MAX_RED = 4;
 
-// diagonal forms (sum_r w_f[r] |v_r|^2 over the 2^k amplitudes of the
-// reduced qubits): every group first collects |v|^2 into the 2^k bins of the
-// reduced qubits (compile-time bin of each amplitude), then weights the
-// bins (float32) and adds the group totals to the float-float accumulators
+// Diagonal forms (sum_r w_f[r] |v_r|^2 over the 2^k amplitudes of the
+// reduced qubits) are linear in the 2^k bins of |v|^2, so a unit only
+// accumulates the bins: every group collects |v|^2 into the bins of the
+// reduced qubits (compile-time bin of each amplitude, float32 within the
+// group) and adds them to the float-float bin accumulators.  The weights
+// are applied once per unit, in float64 (any number of forms, weights at
+// full precision).
 template <class R, int G, int J0, int J1>
 __device__ __forceinline__ void reg_diag_bins(const typename Cplx<R>::T* v, R* q) {
 #pragma unroll
@@ -946,8 +1117,7 @@ __device__ __forceinline__ void reg_diag_bins(const typename Cplx<R>::T* v, R* q
 }
 
 template <class R, int G>
-__device__ __forceinline__ void reg_diag(const typename Cplx<R>::T* v, const PassDesc& p,
-                                         const typename Cplx<R>::T* W, Acc<R>* acc) {
+__device__ __forceinline__ void reg_diag(const typename Cplx<R>::T* v, const PassDesc& p, Acc<R>* acc) {
     R q[4] = {0, 0, 0, 0};
     if (p.red_k == 1) {
         switch (p.red_pos[0]) {
@@ -972,21 +1142,9 @@ __device__ __forceinline__ void reg_diag(const typename Cplx<R>::T* v, const Pas
         default: if constexpr (G > 8) reg_diag_bins<R, G, 3, 2>(v, q); break;
         }
     }
-    const int D = 1 << p.red_k;
-    const auto* Wl = W + (p.red_R << p.red_k);  // float32 residuals of the weights
 #pragma unroll
-    for (int f = 0; f < REG_MAX_RED; ++f) {
-        if (f >= p.red_R) break;
-        R loc = 0, loc_lo = 0;
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (r < D) {
-                loc += W[f * D + r].x * q[r];
-                if constexpr (sizeof(R) == 4) loc_lo += Wl[f * D + r].x * q[r];
-            }
-        acc[f].add(loc);
-        if constexpr (sizeof(R) == 4) acc[f].lo += loc_lo;  // below an ulp of loc: the low word
-    }
+    for (int r = 0; r < 4; ++r)
+        if (r < (1 << p.red_k)) acc[r].add(q[r]);
 }
 
 // CTA shape of the register path: complex64 at 128 threads and up to 96
@@ -1116,6 +1274,20 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                         if constexpr (sizeof(T) == 8)
                             matx[st.mat + e] = make_ulonglong2(pk2((float)m.x, (float)m.x), pk2(-(float)m.y, (float)m.y));
                     }
+                    if (st.k == 2) {
+                        // a monomial matrix (permutation times phases) moves
+                        // registers instead of multiplying: its structure to
+                        // w_packed, its phases over the matrix's first entries
+                        __syncwarp();
+                        if (lane == 0) {
+                            T m[16], ph[4];
+                            for (int e = 0; e < 16; ++e) m[e] = mats[st.mat + e];
+                            const int mi = mono_info(m, ph);
+                            if (mi)
+                                for (int q = 0; q < 4; ++q) mats[st.mat + q] = ph[q];
+                            w_packed[s] = mi;
+                        }
+                    }
                     if (st.k == 1 && lane == 0) {
                         // structure of a one-qubit matrix: 1 diagonal, 2 anti-diagonal, +4 real
                         const bool off0 = src[2] == 0 && src[3] == 0 && src[4] == 0 && src[5] == 0;
@@ -1200,6 +1372,8 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                         const int shape = w_packed[s];
                         if (shape) reg_apply1s_dyn<T, G>(v, st.pos[0], mats + st.mat, shape);
                         else reg_apply1_dyn<T, G>(v, st.pos[0], mats + st.mat);
+                    } else if (const int mi = w_packed[s]) {
+                        reg_mono_dyn<T, G>(v, st.pos[0], st.pos[1], mi, mats + st.mat);
                     } else {
                         if constexpr (sizeof(T) == 8)
                             reg_apply2x_dyn<G>(reinterpret_cast<float2*>(v), st.pos[0], st.pos[1], matx + st.mat);
@@ -1245,7 +1419,7 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
             if (p.red_kind == RED_FORMS)
                 reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - 8 * p.red_R, p.red_R, acc);
             else if (p.red_kind == RED_DIAG)
-                reg_diag<R, G>(v, p, mats + p.mat_elems - 2 * (p.red_R << p.red_k), acc);
+                reg_diag<R, G>(v, p, acc);
             if (p.store) {
                 if constexpr (sizeof(T) == 8 && PAIRED) {
 #pragma unroll
@@ -1257,7 +1431,27 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                 }
             }
         }
-        if (red) {
+        if (red && p.red_kind == RED_DIAG) {
+            // the unit's bins (fixed shuffle tree, float64), then every form
+            // from them: lane f writes form f
+            const int D = 1 << p.red_k;
+            double bin[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                double x = r < D ? acc[r].get() : 0.0;
+                if (r < D)
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                bin[r] = x;
+            }
+            if (lane < p.red_R) {
+                const T* W = mats + p.mat_elems - 2 * (p.red_R << p.red_k);
+                double part = 0.0;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (r < D) part += diag_weight(W, p.red_R, p.red_k, lane, r) * bin[r];
+                d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED + lane] = part;
+            }
+        } else if (red) {
 #pragma unroll
             for (int r = 0; r < REG_MAX_RED; ++r) {
                 if (r >= p.red_R) break;

@@ -395,8 +395,9 @@ int reg_width(sv_batch b, const RedSpec& red, uint64_t act) {
     for (const PendStage& ps : b->pend)
         if ((ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) && ps.k > 2) return 0;
     if (red.kind == RED_BINS) return 0;
-    if (red.kind == RED_FORMS && red.R > 4) return 0;
-    if (red.kind == RED_FORMS && red.k != 1 && red.diag_off < 0) return 0;
+    // diagonal forms reduce to 2^k bins (any number of forms); general
+    // forms take one accumulator each (at most 4, one qubit)
+    if (red.kind == RED_FORMS && red.diag_off < 0 && (red.R > 4 || red.k != 1)) return 0;
     // the per-warp matrix copies must fit the default 48 KB of dynamic
     // shared memory of the register kernels; longer stage lists take tiles
     PassDesc probe;
@@ -492,7 +493,7 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
     p.red_k = red.k;
     p.red_R = red.R;
     p.red_off = red.off;
-    if (wp > 0 && red.kind == RED_FORMS && red.diag_off >= 0) {
+    if (red.kind == RED_FORMS && red.diag_off >= 0) {  // diagonal forms: bins, weights per chunk
         p.red_kind = RED_DIAG;
         p.red_off = red.diag_off;
     }
@@ -734,6 +735,24 @@ sv_status op_gate(sv_batch b, int k, const int* q, const double* mat, int cond_c
     for (int j = 0; j < k; ++j) s.q[j] = q[j];
     s.cond_clbit = cond_clbit;
     s.cond_val = cond_val;
+    s.off = pool_matrix(b, mat, k);
+    add_stage(b, s);
+    return SV_OK;
+}
+
+// A dense matrix on k <= MAX_GATE_Q qubits that need not be unitary: the
+// density-matrix method's superoperators (vec(rho) is a state of 2n qubits)
+sv_status op_superop(sv_batch b, int k, const int* q, const double* mat) {
+    sv_status st = check_qubits(b, k, q);
+    if (st) return st;
+    if (k < 1 || k > MAX_GATE_Q) return fail(SV_EUNSUPPORTED, "superoperators act on 1 to 5 qubits");
+    if ((st = ensure_started(b))) return st;
+    if ((st = make_room(b, q, k, 1 << (2 * k), false))) return st;
+    PendStage s{};
+    s.kind = ST_DENSE;
+    s.k = k;
+    for (int j = 0; j < k; ++j) s.q[j] = q[j];
+    s.cond_clbit = -1;
     s.off = pool_matrix(b, mat, k);
     add_stage(b, s);
     return SV_OK;
@@ -1933,6 +1952,144 @@ sv_status sv_run_circuits(sv_batch* bs, const sv_circuit* const* cs, int n, int 
         if ((st = check_device_error(bs[i]))) return st;
     }
     return SV_OK;
+}
+
+// ---- density-matrix method -------------------------------------------------
+// the superoperator sum_t K_t (x) conj(K_t) of a k-qubit channel as a
+// 2k-qubit matrix: index bits 0..k-1 are the row qubits, k..2k-1 the column
+// qubits (row-major complex, re/im interleaved)
+static std::vector<double> superop(const std::vector<std::vector<std::complex<double>>>& K, int k) {
+    const int D = 1 << k, D2 = D * D;
+    std::vector<double> S(2 * (size_t)D2 * D2, 0.0);
+    for (const auto& Kt : K)
+        for (int r = 0; r < D; ++r)
+            for (int c = 0; c < D; ++c)
+                for (int r2 = 0; r2 < D; ++r2)
+                    for (int c2 = 0; c2 < D; ++c2) {
+                        const std::complex<double> v = Kt[r * D + r2] * std::conj(Kt[c * D + c2]);
+                        const size_t e = (size_t)(r + D * c) * D2 + (r2 + D * c2);
+                        S[2 * e] += v.real();
+                        S[2 * e + 1] += v.imag();
+                    }
+    return S;
+}
+
+static std::vector<std::complex<double>> host_matrix(const double* d, int k) {
+    const int E = 1 << (2 * k);
+    std::vector<std::complex<double>> m(E);
+    for (int e = 0; e < E; ++e) m[e] = {d[2 * e], d[2 * e + 1]};
+    return m;
+}
+
+// the Pauli string of characters s[0..k-1] (s[j] on qubit j of the op) as a
+// 2^k x 2^k matrix, scaled by sqrt(p)
+static std::vector<std::complex<double>> pauli_matrix_k(const char* s, int k, double p) {
+    const int D = 1 << k;
+    std::vector<std::complex<double>> m((size_t)D * D, 0.0);
+    const std::complex<double> I1(0, 1);
+    for (int c = 0; c < D; ++c) {
+        int r = c;
+        std::complex<double> ph = std::sqrt(p);
+        for (int j = 0; j < k; ++j) {
+            const int bit = (c >> j) & 1;
+            switch (s[j]) {
+            case 'X': r ^= 1 << j; break;
+            case 'Y': r ^= 1 << j; ph *= bit ? -I1 : I1; break;
+            case 'Z': if (bit) ph = -ph; break;
+            default: break;
+            }
+        }
+        m[(size_t)r * D + c] = ph;
+    }
+    return m;
+}
+
+extern "C" sv_status sv_dm_run(const sv_circuit* c, sv_prec prec, uint64_t seed, uint64_t n_shots, uint64_t* keys,
+                               double* probs, double* thresholds, void* cuda_stream) {
+    if (!c) return fail(SV_EINVAL, "circuit is NULL");
+    const int n = c->n_qubits;
+    if (n < 1 || n > 15) return fail(SV_EUNSUPPORTED, "the density matrix of n qubits is a state of 2n <= 30 qubits");
+    if (n_shots && !keys) return fail(SV_EINVAL, "keys is NULL");
+    int final_op = -1;
+    for (int i = 0; i < c->n_ops; ++i) {
+        const int kind = c->kind[i];
+        if (kind == SV_OP_MEASURE || kind == SV_OP_PGATE || (kind == SV_OP_GATE && c->cond_clbit[i] >= 0))
+            return fail(SV_EUNSUPPORTED, "the density-matrix method takes gates, Pauli and Kraus noise and a final sample");
+        if (kind == SV_OP_FINAL) {
+            if (i != c->n_ops - 1) return fail(SV_EUNSUPPORTED, "the final sample must be the last op");
+            final_op = i;
+        }
+    }
+    if (n_shots && final_op < 0) return fail(SV_EINVAL, "sampling shots needs a final op");
+    sv_batch b = nullptr;
+    sv_status st = sv_alloc_batch(2 * n, 1, 0, prec, SV_BATCH, seed, 0, cuda_stream, &b);
+    if (st) return st;
+    // the first call that fails frees the batch through this guard
+    struct Guard {
+        sv_batch b;
+        ~Guard() { sv_free_batch(b); }
+    } guard{b};
+    for (int i = 0; i < c->n_ops && !st; ++i) {
+        const int kind = c->kind[i], k = c->nq[i];
+        const int* q = c->qubits + c->q_off[i];
+        const double* d = c->data + c->d_off[i];
+        std::vector<int> qq(2 * k);
+        for (int j = 0; j < k; ++j) {
+            qq[j] = q[j];
+            qq[k + j] = q[j] + n;
+        }
+        if (kind == SV_OP_GATE) {
+            // U rho U^dagger: U on the row qubits, conj(U) on the column qubits
+            if ((st = check_qubits(b, k, q))) break;
+            if (!is_unitary(d, k, 1e-10)) {
+                st = fail(SV_EINVAL, "gate matrix is not unitary");
+                break;
+            }
+            std::vector<double> conj_u(d, d + (2 << (2 * k)));
+            for (size_t e = 1; e < conj_u.size(); e += 2) conj_u[e] = -conj_u[e];
+            if ((st = op_superop(b, k, qq.data(), d))) break;
+            st = op_superop(b, k, qq.data() + k, conj_u.data());
+        } else if (kind == SV_OP_PAULI || kind == SV_OP_KRAUS) {
+            if (2 * k > MAX_GATE_Q) {
+                st = fail(SV_EUNSUPPORTED, "channels of the density-matrix method act on 1 or 2 qubits");
+                break;
+            }
+            std::vector<std::vector<std::complex<double>>> K;
+            if (kind == SV_OP_PAULI) {
+                const char* strs = (const char*)c->paulis + c->s_off[i];
+                double prev = 0.0;
+                for (int t = 0; t < c->n_terms[i]; ++t) {
+                    const double pt = d[t] - prev;
+                    prev = d[t];
+                    if (pt > 0.0) K.push_back(pauli_matrix_k(strs + t * k, k, pt));
+                }
+            } else {
+                for (int t = 0; t < c->n_terms[i]; ++t) K.push_back(host_matrix(d + (size_t)t * (2 << (2 * k)), k));
+            }
+            const std::vector<double> S = superop(K, k);
+            st = op_superop(b, 2 * k, qq.data(), S.data());
+        }
+    }
+    if (st) return st;
+    if ((st = upload_pool(b))) return st;
+    if ((st = flush(b))) return st;
+    // final distribution and the shots' keys
+    const int64_t dim = 1ll << n;
+    const int chunks = (int)std::min<int64_t>(std::max<int64_t>(dim / 1024, 1), 1024);
+    double *p = nullptr, *sums = nullptr, *cum = nullptr, *thr = nullptr;
+    uint64_t* dkeys = nullptr;
+    if ((st = dalloc(b, &p, dim)) || (st = dalloc(b, &sums, chunks)) || (st = dalloc(b, &cum, chunks)) ||
+        (st = dalloc(b, &dkeys, std::max<uint64_t>(n_shots, 1))) ||
+        (thresholds && (st = dalloc(b, &thr, 2 * std::max<uint64_t>(n_shots, 1)))))
+        return st;
+    CU(launch_dm_final(b->dev.states, prec == SV_C128, n, p, sums, cum, chunks, n_shots, seed,
+                       (uint32_t)std::max(final_op, 0), dkeys, thr, b->n_sm, b->stream));
+    if (probs) CU(cudaMemcpyAsync(probs, p, dim * 8, cudaMemcpyDeviceToHost, b->stream));
+    if (n_shots) CU(cudaMemcpyAsync(keys, dkeys, n_shots * 8, cudaMemcpyDeviceToHost, b->stream));
+    if (thresholds && n_shots)
+        CU(cudaMemcpyAsync(thresholds, thr, n_shots * 16, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return check_device_error(b);
 }
 
 sv_status sv_get_amplitudes(sv_batch b, uint64_t shot, double* out, uint64_t len) {

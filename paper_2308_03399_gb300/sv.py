@@ -62,6 +62,7 @@ def lib():
                 "sv_apply_gate_batch": [P, I, P, P, I, I],
                 "sv_sample_noise": [P, U32, I, I, P, I, P, P, P],
                 "sv_set_param_sets": [P, P, U32],
+                "sv_dm_run": [P, I, U64, U64, P, P, P, P],
                 "sv_apply_param_gate_batch": [P, I, P, P, I],
                 "sv_measure_batch": [P, U32, I, P, P, I],
                 "sv_branch": [P, U32],
@@ -306,6 +307,18 @@ class MLP:
         return float(loss.value)
 
 
+def dm_run(circ_struct, n_shots, prec=SV_C64, seed=0, stream=None, thresholds=False):
+    """sv_dm_run: the density-matrix method.  Returns (keys, probs) or, with
+    thresholds, (keys, probs, thresholds as (n_shots, 2))."""
+    keys = np.zeros(max(n_shots, 1), np.uint64)
+    probs = np.zeros(1 << circ_struct.n_qubits, np.float64)
+    thr = np.zeros(2 * max(n_shots, 1), np.float64) if thresholds else None
+    _check(lib().sv_dm_run(C.byref(circ_struct), prec, seed, n_shots, _p(keys), _p(probs), _p(thr), stream))
+    if thresholds:
+        return keys[:n_shots], probs, thr[:2 * n_shots].reshape(-1, 2)
+    return keys[:n_shots], probs
+
+
 def run_circuits(batches, circ_structs, use_graph=True):
     """sv_run_circuits: several (batch, circuit) pairs in one CUDA graph."""
     n = len(batches)
@@ -320,5 +333,5 @@ def exported_symbols():
             "sv_measure_batch", "sv_branch", "sv_counts", "sv_get_keys", "sv_waiting", "sv_run_circuit",
             "sv_get_amplitudes", "sv_get_outcomes", "sv_get_fork_events", "sv_get_branch_tree", "sv_stats", "sv_profile", "sv_sync",
             "sv_last_error", "sv_run_circuits", "sv_final_sample_noalloc", "sv_set_param_sets",
-            "sv_apply_param_gate_batch", "sv_mlp_create", "sv_mlp_free", "sv_mlp_num_params",
+            "sv_apply_param_gate_batch", "sv_dm_run", "sv_mlp_create", "sv_mlp_free", "sv_mlp_num_params",
             "sv_mlp_set_params", "sv_mlp_get_params", "sv_mlp_forward", "sv_mlp_gradient", "sv_mlp_train"]
