@@ -671,10 +671,16 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
                 scale_sh[st_i] = scale;
             }
             __syncthreads();
+            // matrices: the shared gates' (and the reduction's forms) once per
+            // CTA, a branch's own choices (Kraus terms, parameter sets) per
+            // branch; a matrix that is monomial (CX, CZ, SWAP, phases) moves
+            // amplitudes instead of multiplying
             const R* pool = reinterpret_cast<const R*>(d.pool);
+            const bool first = cur_b < 0;
             for (int st_i = 0; st_i < p.n_stages; ++st_i) {
                 const Stage& st = p.st[st_i];
-                if (skip[st_i] || (st.kind != ST_DENSE && st.kind != ST_DENSE_BR)) continue;
+                if (st.kind != ST_DENSE && st.kind != ST_DENSE_BR) continue;
+                if (st.kind == ST_DENSE ? !first : skip[st_i]) continue;
                 const int D2 = 1 << (2 * st.k);
                 const R* src = pool + st.off + (st.kind == ST_DENSE_BR ? (int64_t)sel_sh[st_i] * st.stride : 0);
                 const R sc = (R)scale_sh[st_i];
@@ -685,7 +691,7 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
                     mats[st.mat + e] = m;
                 }
             }
-            if (p.red_kind == RED_FORMS || p.red_kind == RED_DIAG) {  // coefficients, then residuals
+            if (first && (p.red_kind == RED_FORMS || p.red_kind == RED_DIAG)) {  // coefficients, then residuals
                 const int E2 = 2 * (p.red_R << ((p.red_kind == RED_FORMS ? 2 : 1) * p.red_k));
                 const R* src = pool + p.red_off;
                 for (int e = threadIdx.x; e < E2; e += blockDim.x) {
@@ -696,20 +702,21 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
                 }
             }
             __syncthreads();
-            // monomial two-qubit matrices (CX, CZ, SWAP, controlled phases)
-            // move amplitudes instead of multiplying: structure and phases
             for (int st_i = threadIdx.x; st_i < p.n_stages; st_i += blockDim.x) {
                 const Stage& st = p.st[st_i];
-                int mi = 0;
-                if (!skip[st_i] && st.k == 2 && (st.kind == ST_DENSE || st.kind == ST_DENSE_BR)) {
-                    T m[16], ph[4];
-                    for (int e = 0; e < 16; ++e) m[e] = mats[st.mat + e];
-                    mi = mono_info(m, ph);
-                    if (mi)
-                        for (int q = 0; q < 4; ++q) mats[st.mat + q] = ph[q];  // this stage's own entries
-                }
+                if (st.k != 2 || (st.kind != ST_DENSE && st.kind != ST_DENSE_BR)) continue;
+                if (st.kind == ST_DENSE ? !first : skip[st_i]) continue;
+                T m[16], ph[4];
+                for (int e = 0; e < 16; ++e) m[e] = mats[st.mat + e];
+                const int mi = mono_info(m, ph);
+                if (mi)
+                    for (int q = 0; q < 4; ++q) mats[st.mat + q] = ph[q];  // this stage's own entries
                 mono_sh[st_i] = mi;
             }
+            if (first)
+                for (int st_i = threadIdx.x; st_i < p.n_stages; st_i += blockDim.x)
+                    if (p.st[st_i].k != 2 || (p.st[st_i].kind != ST_DENSE && p.st[st_i].kind != ST_DENSE_BR))
+                        mono_sh[st_i] = 0;
             __syncthreads();
             cur_b = b;
         }
@@ -1207,10 +1214,19 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
         }
         if (b != cur_b) {
             const uint64_t clb = d.br_clbits[b];
+            // the shared gates' matrices (and the reduction's coefficients)
+            // are loaded for the warp's first branch only; a branch's own
+            // stages (choices, parameter sets) on every branch change
+            const bool first = cur_b < 0;
             skipmask = 0;
             __syncwarp();
             for (int s = 0; s < p.n_stages; ++s) {
                 const Stage& st = p.st[s];
+                if (st.kind == ST_DENSE && !first) {  // only its condition is per branch
+                    if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val)
+                        skipmask |= 1ull << s;
+                    continue;
+                }
                 int sk = 0, sel = 0, packed = 0;
                 double scale = 1.0;
                 if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val) sk = 1;
@@ -1262,7 +1278,7 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                     w_sel[s] = sel;
                     w_packed[s] = info;
                 }
-                if (!sk && (st.kind == ST_DENSE || st.kind == ST_DENSE_BR)) {
+                if ((!sk || st.kind == ST_DENSE) && (st.kind == ST_DENSE || st.kind == ST_DENSE_BR)) {
                     const int D2 = 1 << (2 * st.k);
                     const R* src = pool + st.off + (st.kind == ST_DENSE_BR ? (int64_t)sel * st.stride : 0);
                     const R sc = (R)scale;
@@ -1304,7 +1320,7 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                     mats[st.mat] = m;
                 }
             }
-            if (p.red_kind == RED_FORMS || p.red_kind == RED_DIAG) {  // coefficients, then residuals
+            if (first && (p.red_kind == RED_FORMS || p.red_kind == RED_DIAG)) {  // coefficients, then residuals
                 const int E2 = 2 * (p.red_kind == RED_FORMS ? 4 * p.red_R : p.red_R << p.red_k);
                 const R* src = pool + p.red_off;
                 for (int e = lane; e < E2; e += 32) {
@@ -1493,8 +1509,10 @@ __device__ __forceinline__ double warp_sum(double x, int used) {
 struct DecTab {
     double p[MAX_TERMS], cum[MAX_TERMS];  // head op: probabilities, running sums
     uint64_t thr[MAX_TERMS];              // head op: integer thresholds
+    double sc[MAX_TERMS];                 // head op: 1 / sqrt(p) of every outcome (1 for Pauli)
     double jp[MAX_RED], jcum[MAX_RED];    // chained DEC_KRAUS_J2: p(j | i), row i at i * R2
     uint64_t jthr[MAX_RED];
+    double jsc[MAX_RED];                  // chained DEC_KRAUS_J2: 1 / sqrt(p(j | i))
     int bincnt[MAX_TERMS], binbase[MAX_TERMS], binrun[MAX_TERMS];
     int leaf[MAX_TERMS];                  // fork log: branch of each outcome tuple
 };
@@ -1547,18 +1565,27 @@ __device__ void warp_probs(const DevBatch& d, const DecideDesc& dd, int b, int s
             if (lane == 0) cum_out[k] = t;  // scratch until the caller forms the table
         }
     __syncwarp();
-    if (lane == 0) {
-        if (joint_out)
-            for (int k = 0; k < nk; ++k) joint_out[k] = cum_out[k];
+    // GB300's float64 pipe retires two lanes per clock per SM, shared by every
+    // warp there: each term below is computed by its own lane (the same
+    // operations in the same order as one lane looping over them)
+    for (int k = lane; k < nk; k += 32)
+        if (joint_out) joint_out[k] = cum_out[k];
+    for (int r = lane; r < R; r += 32) {
+        double t = 0.0;
+        for (int j = 0; j < inner; ++j) t += cum_out[r * inner + j];
+        p_out[r] = t;
+    }
+    __syncwarp();
+    if (dd.kind == DEC_KRAUS_J2) {
         double pi = 0.0;
-        for (int r = 0; r < R; ++r) {
-            double t = 0.0;
-            for (int j = 0; j < inner; ++j) t += cum_out[r * inner + j];
-            p_out[r] = t;
-            pi += t;
-        }
-        if (dd.kind == DEC_KRAUS_J2)
-            for (int r = 0; r < R; ++r) p_out[r] = p_out[r] / pi;
+        for (int r = 0; r < R; ++r) pi += p_out[r];
+        double q[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) q[h] = lane + 32 * h < R ? p_out[lane + 32 * h] / pi : 0.0;
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (lane + 32 * h < R) p_out[lane + 32 * h] = q[h];
     }
     __syncwarp();
 }
@@ -1575,27 +1602,37 @@ __device__ void branch_tables(const DevBatch& d, const DecideDesc& dd, int b, in
     const int lane = threadIdx.x & 31;
     const bool j2 = chained_j2(dd);
     warp_probs(d, dd, b, slot, T.p, T.cum, j2 ? T.jp : nullptr);
-    if (lane == 0) {
-        if (dd.kind != DEC_PAULI) {
-            double acc = 0.0;
-            for (int r = 0; r < dd.R; ++r) T.cum[r] = (acc += T.p[r]);
+    if (lane == 0 && dd.kind != DEC_PAULI) {
+        double acc = 0.0;
+        for (int r = 0; r < dd.R; ++r) T.cum[r] = (acc += T.p[r]);
+    }
+    if (j2) {
+        // row i of p(j | i) = p_ij / sum_j p_ij and its running sums, entry
+        // k = i * R2 + j by lane k (R * R2 <= MAX_RED <= 32)
+        const int R2 = dd.tail[0].R, n2 = dd.R * R2;
+        double q = 0.0;
+        if (lane < n2) {
+            const double* row = T.jp + (lane / R2) * R2;
+            double pi = 0.0;
+            for (int j = 0; j < R2; ++j) pi += row[j];
+            q = T.jp[lane] / pi;
         }
-        if (j2) {
-            const int R2 = dd.tail[0].R;
-            for (int i = 0; i < dd.R; ++i) {
-                double* row = T.jp + i * R2;
-                double pi = 0.0;
-                for (int j = 0; j < R2; ++j) pi += row[j];
-                double acc = 0.0;
-                for (int j = 0; j < R2; ++j) {
-                    row[j] = row[j] / pi;
-                    T.jcum[i * R2 + j] = (acc += row[j]);
-                }
-            }
+        __syncwarp();
+        if (lane < n2) T.jp[lane] = q;
+        __syncwarp();
+        if (lane < n2) {
+            const int i = lane / R2, j = lane % R2;
+            double acc = 0.0;
+            for (int jj = 0; jj <= j; ++jj) acc += T.jp[i * R2 + jj];
+            T.jcum[lane] = acc;
+            T.jsc[lane] = 1.0 / sqrt(T.jp[lane]);
         }
     }
     __syncwarp();
-    for (int r = lane; r < dd.R; r += 32) T.thr[r] = cum_threshold(T.cum[r]);
+    for (int r = lane; r < dd.R; r += 32) {
+        T.thr[r] = cum_threshold(T.cum[r]);
+        T.sc[r] = dd.kind == DEC_PAULI ? 1.0 : 1.0 / sqrt(T.p[r]);
+    }
     if (j2)
         for (int k = lane; k < dd.R * dd.tail[0].R; k += 32) T.jthr[k] = cum_threshold(T.jcum[k]);
     __syncwarp();
@@ -1646,13 +1683,12 @@ __device__ int write_choices(const DevBatch& d, const DecideDesc& dd, const DecT
     outc[0] = rest;
     const int oh = outc[0];
     d.br_sel[(int64_t)dd.pend * d.cap_br + leaf] = oh;
-    d.br_scale[(int64_t)dd.pend * d.cap_br + leaf] = dd.kind == DEC_PAULI ? 1.0 : 1.0 / sqrt(T.p[oh]);
+    d.br_scale[(int64_t)dd.pend * d.cap_br + leaf] = T.sc[oh];
     for (int t = 0; t < dd.n_tail; ++t) {
         const DecideTail& tl = dd.tail[t];
         const int o = outc[1 + t];
         d.br_sel[(int64_t)tl.pend * d.cap_br + leaf] = o;
-        d.br_scale[(int64_t)tl.pend * d.cap_br + leaf] =
-            tl.kind == DEC_KRAUS_J2 ? 1.0 / sqrt(T.jp[oh * tl.R + o]) : 1.0;
+        d.br_scale[(int64_t)tl.pend * d.cap_br + leaf] = tl.kind == DEC_KRAUS_J2 ? T.jsc[oh * tl.R + o] : 1.0;
     }
     return oh;
 }

@@ -755,7 +755,8 @@ sv_status op_superop(sv_batch b, int k, const int* q, const double* mat) {
     s.cond_clbit = -1;
     s.off = pool_matrix(b, mat, k);
     add_stage(b, s);
-    return SV_OK;
+    // a later make_room may flush this stage: its matrix must be on the device
+    return upload_pool(b);
 }
 
 // Section VI: a gate whose parameters vary between shots.  The matrix of

@@ -131,4 +131,9 @@ def test_accumulation_matches_float64_sums(name):
           ", ".join(f"{names[k]} {worst[k]:.2e} ({count[k]} decisions)" for k in worst if count[k]))
     for d in sorted(detail, reverse=True)[:6]:
         print("  gap %.2e op %d kind %d qubits %s shot %d choice %d C_gpu %.17g C_f64 %.17g" % d)
-    assert max(worst.values()) <= 5e-9
+    # each |psi_j|^2 is formed in float32 (relative error 2^-24 per term);
+    # in the sparse states of a circuit's first gates a few terms carry the
+    # whole sum, so the gap reaches a few 1e-8 there and falls to ~1e-10 as
+    # the state spreads -- in every case below the float32 amplitudes' own
+    # distance from the float64 oracle (~1e-7) and the flag window (1e-5)
+    assert max(worst.values()) <= 5e-8
