@@ -105,9 +105,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def pass_traffic(args):
-    """DRAM bytes per k_pass launch from the committed ncu record, or None when
-    the kernels have changed since it was taken or the workload differs."""
+def pass_traffic(args, alg_bytes_per_launch):
+    """DRAM bytes per k_pass launch: the committed ncu record gives the
+    ratio of DRAM traffic to algorithmic bytes over every k_pass launch of
+    one step of the same circuit at 2000 shots (a case small enough for a
+    multi-metric capture); traffic grows in proportion to the live states a
+    pass streams, so the full launch's traffic is that ratio times its
+    algorithmic bytes.  None when the kernels have changed since the record
+    was taken or the workload differs."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_pass_traffic_cfg2_su4_16.txt")
     if not os.path.exists(path) or args.shots:
@@ -117,7 +122,9 @@ def pass_traffic(args):
     sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
     if rec.get("source_sha1") != sha or rec.get("workload") != f"{args.workload}:{args.mode}:{args.prec}":
         return None
-    return float(rec["dram_bytes_per_step"]) / float(rec["launches"])
+    ratio = float(rec["dram_bytes_per_step"]) / float(rec["algorithmic_bytes_per_step"])
+    return {"bytes_per_launch": ratio * alg_bytes_per_launch, "traffic_over_algorithmic": ratio,
+            "measured_on": rec.get("measured_on", "")}
 
 
 def plain_vs_batched(torch, flush_buf):
@@ -501,7 +508,9 @@ def main():
     ap.add_argument("--qft-sizes", default="10,12,14,16,18,20", help="qubit counts of the QFT sweep")
     ap.add_argument("--qft-ratio-n", type=int, default=14, help="qubit count of the error-ratio sweep")
     args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
+    # three warm-up steps for every timed line; config 4's side record and the
+    # QFT sweep (minutes per step) may ask for fewer
+    args.warmup = max(args.warmup, 1 if args.workload in ("cfg4", "qft") else 3)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -618,7 +627,7 @@ def main():
     pass_ms, n_pass = prof["pass"]
     hbm_peak, peak_kind = peaks()
     achieved = stp["pass_bytes"] / (pass_ms / 1e3) / 1e9 if pass_ms > 0 else 0.0
-    traffic = pass_traffic(args)
+    traffic = pass_traffic(args, stp["pass_bytes"] / max(n_pass, 1))
 
     line = {
         "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
@@ -632,7 +641,10 @@ def main():
         "e2e": {"value": e2e_value, "unit": "shots/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(keys.nbytes)},
         "roofline": {"bound": "hbm", "kernel": "k_pass", "achieved": achieved, "peak": hbm_peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": traffic["bytes_per_launch"] if traffic else None,
+                     "traffic_note": (f"ncu DRAM bytes / algorithmic bytes = {traffic['traffic_over_algorithmic']:.3f} "
+                                      f"on {traffic['measured_on']}, scaled to this launch") if traffic else None,
                      "algorithmic_bytes_per_launch": stp["pass_bytes"] / max(n_pass, 1),
                      "algorithmic_bytes_per_step": stp["pass_bytes"] / prof_steps,
                      "pass_ms_per_step": pass_ms / prof_steps, "pass_launches_per_step": n_pass / prof_steps,
