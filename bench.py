@@ -144,6 +144,7 @@ def plain_vs_batched(torch, flush_buf):
         graph = mode != sv.SV_PLAIN
         for _ in range(warm):
             b.run_circuit(cs, use_graph=graph)
+        b.stats()  # counters from here on cover the timed steps
         ms = 0.0
         for _ in range(steps):
             flush_buf.fill_(1)
@@ -154,8 +155,16 @@ def plain_vs_batched(torch, flush_buf):
             e1.record(stream)
             e1.synchronize()
             ms += e0.elapsed_time(e1)
+        st = b.stats()
         b.close()
         out[key + "_shots_per_s"] = shots * steps / (ms / 1e3)
+        if mode == sv.SV_PLAIN:
+            # the conventional form's cost is launches: one pass per gate and
+            # per non-identity Pauli string, and for a Kraus op or a
+            # measurement one reduction per term with a host read of it
+            launches = st["launches"] / steps
+            out["plain_launches_per_shot"] = launches / shots
+            out["plain_us_per_launch"] = 1e3 * ms / steps / max(launches, 1)
     out["ratio_fp32_over_plain"] = out["batched_fp32_shots_per_s"] / out["plain_fp64_shots_per_s"]
     out["ratio_fp64_over_plain"] = out["batched_fp64_shots_per_s"] / out["plain_fp64_shots_per_s"]
     return out
@@ -257,12 +266,34 @@ def cfg1_smem(torch, flush_buf):
     return res
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(circ, seed, budget_s=15.0):
     """The oracle as it stands, on the host's cores, on a bounded sample of
-    the workload's shots (shots are independent, so shots/s scales)."""
+    the workload's shots (shots are independent, so shots/s scales); also
+    one core on a few shots."""
     from oracle import oracle as O
     oc = O.OracleCircuit(circ)
     threads = O.max_threads()
+    t0 = time.perf_counter()
+    O.run_shots(oc, seed, 0, 4, 1, want_outcomes=False)
+    single = 4 / (time.perf_counter() - t0)
     n = max(threads, 8)
     t0 = time.perf_counter()
     O.run_shots(oc, seed, 0, n, threads, want_outcomes=False)
@@ -274,8 +305,10 @@ def cpu_baseline(circ, seed, budget_s=15.0):
         O.run_shots(oc, seed, 0, n2, threads, want_outcomes=False)
         dt = time.perf_counter() - t0
         n = n2
-    return {"value": n / dt, "unit": "shots/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n} shots of the same circuit (oracle float64, OpenMP over shots), {dt:.1f} s"}
+    return {"value": n / dt, "unit": "shots/s", "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
+            "single_core_shots_per_s": single,
+            "sample": f"{n} shots of the same circuit (oracle float64, OpenMP over shots), {dt:.1f} s; "
+                      f"single core: 4 shots"}
 
 
 def run_reference(args, rank, world):
@@ -384,13 +417,17 @@ def run_config4(args):
                        "graph": "one CUDA graph for all 64 circuits", "l2": "flushed between steps (512 MB)"},
             "gpu_launches": int(res["gpu_launches_per_step"] * args.steps), "cost_model_pick_s": t_pick,
             "cost_model": res}
+    if args.compare or args.autotune:
+        # the fixed policies the model has to beat
+        line["fixed_branch"] = run([dict(T.DEFAULT) for _ in circs], "fixed: branch, default fusion")
+        fits = [dict(T.DEFAULT, mode="batch") if nd <= pool // 8 else dict(T.DEFAULT) for nd in need]
+        line["fixed_batch_where_it_fits"] = run(fits, "fixed: batch where a state per shot fits, else branch")
     if args.autotune:
         t0 = time.perf_counter()
         small = [c for c in cands if c["joint"] == 1 and c["path"] == 0 and c["tile"] == 0 and c["max_active"] in (0, 3, 8)]
         tuned = picks_by(lambda c, s, ok: T.autotune(c, s, cands=[x for x in small if x in ok], reps=1)[0])
         line["autotune_search_s"] = time.perf_counter() - t0
         line["autotuned"] = run(tuned, "autotuner")
-        line["fixed_branch"] = run([dict(T.DEFAULT) for _ in circs], "fixed: branch, default fusion")
     print(json.dumps(line), flush=True)
 
 
@@ -504,6 +541,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the config-1 plain-vs-batched comparison")
     ap.add_argument("--max-active", type=int, default=0, help="fusion width (qubits per pass), 0 = library default")
     ap.add_argument("--autotune", action="store_true", help="config 4: also run the autotuner's picks")
+    ap.add_argument("--compare", action="store_true", help="config 4: also run the fixed policies")
     ap.add_argument("--no-legs", action="store_true", help="skip the config 1 / 3 / 5 legs of the default run")
     ap.add_argument("--qft-sizes", default="10,12,14,16,18,20", help="qubit counts of the QFT sweep")
     ap.add_argument("--qft-ratio-n", type=int, default=14, help="qubit count of the error-ratio sweep")

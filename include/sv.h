@@ -129,10 +129,15 @@ typedef enum {
     SV_OPT_CHAIN_DECIDES = 12, /* 1 (default): sv_run_circuit decides, in one launch,
                                an op and the ops after it that need no new pass
                                (the second op of a joint Kraus pair, Pauli ops) */
-    SV_OPT_PREDRAW_PAULI = 13 /* 1 (default): in batch mode, sv_run_circuit draws the
+    SV_OPT_PREDRAW_PAULI = 13, /* 1 (default): in batch mode, sv_run_circuit draws the
                                Pauli choices of every shot in one launch before the
                                first gate (up to 1 GiB of one-byte choices)
                                instead of one decide per Pauli op */
+    SV_OPT_COMMUTE = 14       /* 1 (default): sv_run_circuit lets a pass take a subset
+                               of the queued ops: ops on other qubits commute with it
+                               and wait for a later pass (a reduction waits only for
+                               what it does not commute with), so passes fill up to
+                               the fusion width; 0: every pass takes the whole queue */
 } sv_option;
 
 /* Allocate a batch of n_shots shots of an n_qubits register.

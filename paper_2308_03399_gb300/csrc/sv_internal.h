@@ -10,7 +10,7 @@ namespace sv {
 
 constexpr int MAX_TILE_BITS = 12;  // amplitudes of one CTA tile <= 2^12
 constexpr int MAX_STAGES = 40;     // ops fused into one pass
-constexpr int MAX_PEND = 16;       // random ops whose per-branch choice is applied in one pass
+constexpr int MAX_PEND = 64;       // per-branch choice columns of random ops whose stages are pending
 constexpr int MAX_TERMS = 64;      // terms of one random op (Pauli strings)
 constexpr int64_t REG_UNIT_MIN_AMPS = 8192;  // smallest register-path unit
 constexpr int PRE_WORDS = 8;                 // integer-pool words per pre-drawn Pauli row
@@ -108,6 +108,7 @@ struct DecideDesc {
     int32_t clbit[MAX_STAGE_Q];
     int32_t r2;                // joint Kraus: terms of the second op (partials stride)
     int32_t pend_prev;         // DEC_KRAUS_J2: pending column of the first op's choice
+    uint64_t live_cols;        // choice columns whose stages are still pending (forks copy them)
     int32_t* log_sel;          // per shot id, nullable
     double* log_thr;           // 2 per shot id, nullable
     double cum[MAX_TERMS];     // Pauli cumulative table
@@ -180,6 +181,7 @@ enum : int32_t {
     CTL_NCOPIED = 9,    // branches created by forks (each one state copy)
     CTL_NALLOC = 10,    // new-branch ids handed out by the current decide
     CTL_DONE = 11,      // finished CTAs of k_copy (last one folds the counts)
+    CTL_NRUN = 12,      // shots of a restart whose count is read on the device
     CTL_WORDS = 16
 };
 

@@ -1828,7 +1828,8 @@ __device__ void decide_groups(const DevBatch& d, const DecideDesc& dd, int b, in
             d.br_parent[child] = b;
             d.br_big[child] = -1;
             d.br_pset[child] = d.br_pset[b];
-            for (int q = 0; q < dd.pend; ++q) {  // earlier pending choices of the parent
+            for (uint64_t cols = dd.live_cols; cols; cols &= cols - 1) {  // the parent's pending choices
+                const int q = __ffsll((long long)cols) - 1;
                 d.br_sel[(int64_t)q * d.cap_br + child] = d.br_sel[(int64_t)q * d.cap_br + b];
                 d.br_scale[(int64_t)q * d.cap_br + child] = d.br_scale[(int64_t)q * d.cap_br + b];
             }
@@ -2202,7 +2203,10 @@ __global__ void __launch_bounds__(256) k_final_sample(DevBatch d, FinalDesc f) {
 template <class R>
 __global__ void __launch_bounds__(256) k_init(DevBatch d, int n_init) {
     using T = typename Cplx<R>::T;
-    const int64_t total = (int64_t)n_init * d.dim;
+    // the root slots the reset created (none when a restart finds no
+    // waiting shots)
+    const int roots = d.ctl[CTL_NBR];
+    const int64_t total = (int64_t)(n_init < roots ? n_init : roots) * d.dim;
     T* s = reinterpret_cast<T*>(d.states);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         T v;
@@ -2212,11 +2216,18 @@ __global__ void __launch_bounds__(256) k_init(DevBatch d, int n_init) {
     }
 }
 
+// a restart whose shot count is read on the device (inside a captured
+// graph): the waiting count as the previous round left it
+__global__ void k_wait_snapshot(DevBatch d) { d.ctl[CTL_NRUN] = d.ctl[CTL_NWAIT]; }
+
+// from_wait: 0 shots 0 .. n_run-1; 1 the first n_run waiting shots; 2 every
+// waiting shot (count from the device)
 __global__ void __launch_bounds__(256) k_reset(DevBatch d, int branch_mode, int n_run, int from_wait) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (from_wait == 2) n_run = d.ctl[CTL_NRUN];
     for (int64_t i = t0; i < n_run; i += stride) d.perm[i] = from_wait ? d.wait_shots[i] : (uint32_t)i;
-    const int nb = branch_mode ? 1 : n_run;
+    const int nb = branch_mode ? (n_run > 0 ? 1 : 0) : n_run;
     for (int64_t b = t0; b < nb; b += stride) {
         d.br_slot[b] = (int)b;
         d.br_start[b] = branch_mode ? 0 : (int)b;
@@ -2257,6 +2268,7 @@ __global__ void __launch_bounds__(RESET_PSET_THREADS) k_reset_psets(DevBatch d, 
     __shared__ int cnt[MAX_PSETS], base[MAX_PSETS], run[MAX_PSETS];
     __shared__ int nb_sh;
     const int tid = threadIdx.x, nth = blockDim.x;
+    if (from_wait == 2) n_run = d.ctl[CTL_NRUN];
     const int P = d.n_psets;
     for (int q = tid; q < P; q += nth) {
         cnt[q] = 0;
@@ -2449,6 +2461,7 @@ cudaError_t launch_init(const DevBatch& d, int prec, int n_init_slots, int grid,
 
 cudaError_t launch_reset(const DevBatch& d, int mode_branch, int n_shots_run, int from_wait, int grid,
                          cudaStream_t s) {
+    if (from_wait == 2) k_wait_snapshot<<<1, 1, 0, s>>>(d);
     if (mode_branch && d.pset_of_shot) k_reset_psets<<<1, RESET_PSET_THREADS, 0, s>>>(d, n_shots_run, from_wait);
     else k_reset<<<grid, 256, 0, s>>>(d, mode_branch, n_shots_run, from_wait);
     return cudaGetLastError();

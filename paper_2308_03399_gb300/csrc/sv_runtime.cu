@@ -144,8 +144,11 @@ struct sv_batch_s {
     // scheduler
     std::vector<PendStage> pend;
     uint64_t active = 0;
-    int n_pend = 0;
+    uint64_t col_used = 0;  // per-branch choice columns held by pending stages
     int mat_used = 0;
+    // recorded circuits: a pass takes a dependency-closed subset of the
+    // pending stages, so stages on other qubits can wait for a later pass
+    bool commute = true;
     std::vector<Launch>* rec = nullptr;
     bool started = false;
     uint32_t last_random = 0xffffffffu;
@@ -175,6 +178,7 @@ struct sv_batch_s {
     // sv_run_circuits: one graph over several batches (kept by the first)
     uint64_t multi_hash = 0;
     cudaGraphExec_t multi_exec = nullptr;
+    cudaGraphExec_t multi_restart_exec = nullptr;  // waiting-list restarts of the same batches
     std::vector<std::vector<Launch>> multi_lists;
     std::vector<uint64_t> multi_gens;
     // the constant pool holds one recorded circuit at a time; every recording
@@ -388,12 +392,12 @@ struct RedSpec {
 
 // can a pass run in registers (k_pass_reg)?  its qubits plus qubit 0 <= 4,
 // dense stages <= 2 qubits, and no reduction or <= 4 one-qubit forms
-int reg_width(sv_batch b, const RedSpec& red, uint64_t act) {
+int reg_width(sv_batch b, const RedSpec& red, uint64_t act, const std::vector<const PendStage*>& ss) {
     if (b->pass_path == 1) return 0;
     const int wp = __builtin_popcountll(act);
     if (wp > 4 || wp < 1) return 0;
-    for (const PendStage& ps : b->pend)
-        if ((ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) && ps.k > 2) return 0;
+    for (const PendStage* ps : ss)
+        if ((ps->kind == ST_DENSE || ps->kind == ST_DENSE_BR) && ps->k > 2) return 0;
     if (red.kind == RED_BINS) return 0;
     // diagonal forms reduce to 2^k bins (any number of forms); general
     // forms take one accumulator each (at most 4, one qubit)
@@ -402,26 +406,57 @@ int reg_width(sv_batch b, const RedSpec& red, uint64_t act) {
     // shared memory of the register kernels; longer stage lists take tiles
     PassDesc probe;
     probe.mat_elems = 0;
-    for (const PendStage& ps : b->pend)
-        probe.mat_elems += (ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) ? 1 << (2 * ps.k)
-                                                                          : (ps.kind == ST_PROJ_BR ? 1 : 0);
+    for (const PendStage* ps : ss)
+        probe.mat_elems += (ps->kind == ST_DENSE || ps->kind == ST_DENSE_BR) ? 1 << (2 * ps->k)
+                                                                            : (ps->kind == ST_PROJ_BR ? 1 : 0);
     if (red.kind == RED_FORMS) probe.mat_elems += 2 * (red.diag_off >= 0 ? red.R << red.k : red.R << (2 * red.k));
     const int prec = b->prec == SV_C128;
     if (pass_reg_smem_bytes(prec, probe, pass_reg_threads(prec)) > 48 * 1024) return 0;
     return wp;
 }
 
-sv_status emit_pass(sv_batch b, const RedSpec& red) {
-    if (b->pend.empty() && red.kind == RED_NONE) return SV_OK;
+uint64_t stage_mask(const PendStage& s) {
+    uint64_t m = 0;
+    for (int j = 0; j < s.k; ++j) m |= 1ull << s.q[j];
+    return m;
+}
+
+int stage_mats(const PendStage& s) {
+    return (s.kind == ST_DENSE || s.kind == ST_DENSE_BR) ? 1 << (2 * s.k) : (s.kind == ST_PROJ_BR ? 1 : 0);
+}
+
+// the stage holds a per-branch choice column (a sampled op's choice)
+bool stage_has_col(const PendStage& s) { return s.kind != ST_DENSE && !s.pre && s.pend >= 0; }
+
+// Stages that may wait past a reduction on other qubits: unconditional
+// unitaries (gates, Pauli strings, a parameter set's matrix).  The
+// probabilities of a Kraus op or a measurement on qubits R do not change
+// under a unitary on qubits outside R (it commutes with the forms / the
+// projectors and keeps norms); a chosen Kraus matrix or a projection does
+// not keep norms, and a conditional gate reads classical bits a later
+// measurement may rewrite.
+bool stage_deferrable(const PendStage& s) {
+    if (s.cond_clbit >= 0) return false;
+    return s.kind == ST_DENSE || s.kind == ST_PAULI_BR || (s.kind == ST_DENSE_BR && s.pend == PEND_PSET);
+}
+
+// one pass: the pending stages idx (ascending, a dependency-closed subset in
+// op order) and an optional reduction; the stages leave the queue and their
+// choice columns are free again
+sv_status emit_stages(sv_batch b, const std::vector<int>& idx, const RedSpec& red) {
+    if (idx.empty() && red.kind == RED_NONE) return SV_OK;
+    std::vector<const PendStage*> ss;
+    for (int i : idx) ss.push_back(&b->pend[i]);
     Launch L;
     L.type = L_PASS;
     PassDesc& p = L.pass;
     memset(&p, 0, sizeof(p));
     p.n = b->n;
     p.tb = b->tb;
-    uint64_t act = b->active;
+    uint64_t act = 0;
+    for (const PendStage* ps : ss) act |= stage_mask(*ps);
     for (int j = 0; j < red.k; ++j) act |= 1ull << red.q[j];
-    const int wp = reg_width(b, red, act);
+    const int wp = reg_width(b, red, act, ss);
     if (wp > 0) {
         // register group: exactly the pass's qubits; with qubit 0 among them
         // complex64 amplitudes move as 128-bit pairs
@@ -465,9 +500,10 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
     }
     if (red.kind != RED_NONE) b->red_chunks = p.chunks;
     int mat = 0;
-    p.n_stages = (int)b->pend.size();
+    if ((int)ss.size() > MAX_STAGES) return fail(SV_EINTERNAL, "pass holds more stages than a pass descriptor");
+    p.n_stages = (int)ss.size();
     for (int s = 0; s < p.n_stages; ++s) {
-        const PendStage& ps = b->pend[s];
+        const PendStage& ps = *ss[s];
         Stage& st = p.st[s];
         st.kind = ps.kind;
         st.k = ps.k;
@@ -502,14 +538,181 @@ sv_status emit_pass(sv_batch b, const RedSpec& red) {
     if (p.red_kind == RED_FORMS) mat += 2 * (red.R << (2 * red.k));
     else if (p.red_kind == RED_DIAG) mat += 2 * (red.R << red.k);
     p.mat_elems = mat;
-    b->pend.clear();
+    // the rest of the queue stays pending
+    std::vector<PendStage> rest;
+    std::vector<char> taken(b->pend.size(), 0);
+    for (int i : idx) taken[i] = 1;
+    for (size_t i = 0; i < b->pend.size(); ++i) {
+        if (taken[i]) {
+            if (stage_has_col(b->pend[i])) b->col_used &= ~(1ull << b->pend[i].pend);
+        } else {
+            rest.push_back(b->pend[i]);
+        }
+    }
+    b->pend.swap(rest);
     b->active = 0;
-    b->n_pend = 0;
     b->mat_used = 0;
+    for (const PendStage& ps : b->pend) {
+        b->active |= stage_mask(ps);
+        b->mat_used += stage_mats(ps);
+    }
     return emit(b, std::move(L));
 }
 
-sv_status flush(sv_batch b) { return emit_pass(b, RedSpec()); }
+// every pending stage in one pass
+sv_status emit_pass(sv_batch b, const RedSpec& red) {
+    std::vector<int> all(b->pend.size());
+    for (size_t i = 0; i < all.size(); ++i) all[i] = (int)i;
+    return emit_stages(b, all, red);
+}
+
+bool fits(sv_batch b, uint64_t act);
+
+bool commute_on(sv_batch b) { return b->commute && b->rec; }
+
+constexpr int POOL_MAX = 2 * MAX_STAGES;  // pending stages that may wait for a later pass
+
+// The stages of the next pass, chosen from the pending queue.  A stage can
+// join when every earlier pending stage on one of its qubits has joined
+// (stages on disjoint qubits commute), so the pass is a dependency-closed
+// subset and runs its stages in op order.  Without a reduction the pass
+// grows from the oldest stage; with one (qubits red_q) it starts from the
+// stages the reduction must see: those on red_q, every non-deferrable stage,
+// and everything earlier on their qubits.  It then takes every stage that
+// adds no qubit, and, while the width allows, the stage adding the fewest
+// new qubits (ties: the one touching the most of the pass's qubits, then the
+// earliest).  Returns false when the required stages do not fit one pass.
+bool select_pass(sv_batch b, uint64_t red_q, bool for_red, int red_mats, std::vector<int>& out) {
+    const int n = (int)b->pend.size();
+    const int budget = MAT_SMEM - 256;
+    std::vector<char> in(n, 0);
+    uint64_t pq = red_q;
+    int cnt = 0, mats = red_mats;
+    if (for_red) {
+        uint64_t later = 0;
+        for (int t = n - 1; t >= 0; --t) {
+            const PendStage& s = b->pend[t];
+            const uint64_t m = stage_mask(s);
+            if ((m & red_q) || !stage_deferrable(s) || (m & later)) {
+                in[t] = 1;
+                later |= m;
+                pq |= m;
+                ++cnt;
+                mats += stage_mats(s);
+            }
+        }
+        if (!fits(b, pq) || cnt > b->max_stages || (cnt > 0 && mats > budget)) return false;
+    } else if (n > 0) {
+        in[0] = 1;
+        pq |= stage_mask(b->pend[0]);
+        cnt = 1;
+        mats += stage_mats(b->pend[0]);
+    }
+    for (;;) {
+        bool changed = true;
+        while (changed) {  // stages adding no qubit
+            changed = false;
+            uint64_t blocked = 0;
+            for (int t = 0; t < n; ++t) {
+                if (in[t]) continue;
+                const PendStage& s = b->pend[t];
+                const uint64_t m = stage_mask(s);
+                if (!(m & blocked) && !(m & ~pq) && cnt < b->max_stages && mats + stage_mats(s) <= budget) {
+                    in[t] = 1;
+                    ++cnt;
+                    mats += stage_mats(s);
+                    changed = true;
+                } else {
+                    blocked |= m;
+                }
+            }
+        }
+        int best = -1, best_new = 99, best_touch = -1;
+        uint64_t blocked = 0;
+        for (int t = 0; t < n; ++t) {
+            if (in[t]) continue;
+            const PendStage& s = b->pend[t];
+            const uint64_t m = stage_mask(s);
+            if (!(m & blocked) && fits(b, pq | m) && cnt < b->max_stages && mats + stage_mats(s) <= budget) {
+                const int nw = __builtin_popcountll(m & ~pq), touch = __builtin_popcountll(m & pq);
+                if (nw < best_new || (nw == best_new && touch > best_touch)) {
+                    best = t;
+                    best_new = nw;
+                    best_touch = touch;
+                }
+            }
+            blocked |= m;
+        }
+        if (best < 0) break;
+        in[best] = 1;
+        pq |= stage_mask(b->pend[best]);
+        ++cnt;
+        mats += stage_mats(b->pend[best]);
+    }
+    out.clear();
+    for (int t = 0; t < n; ++t)
+        if (in[t]) out.push_back(t);
+    return true;
+}
+
+// one pass grown from the oldest pending stage
+sv_status emit_oldest(sv_batch b) {
+    std::vector<int> idx;
+    select_pass(b, 0, false, 0, idx);
+    return emit_stages(b, idx, RedSpec());
+}
+
+sv_status flush(sv_batch b) {
+    if (!commute_on(b)) return emit_pass(b, RedSpec());
+    while (!b->pend.empty()) {
+        sv_status st = emit_oldest(b);
+        if (st) return st;
+    }
+    return SV_OK;
+}
+
+// the pass of a reduction on red.q (forms or bins holding red_mats matrix
+// entries), after whatever passes the pending stages need first
+sv_status emit_reduction(sv_batch b, const RedSpec& red, int red_mats) {
+    uint64_t rq = 0;
+    for (int j = 0; j < red.k; ++j) rq |= 1ull << red.q[j];
+    if (!commute_on(b)) {
+        if (!fits(b, b->active | rq) || b->mat_used + red_mats > MAT_SMEM - 256) {
+            sv_status st = flush(b);
+            if (st) return st;
+        }
+        return emit_pass(b, red);
+    }
+    for (;;) {
+        std::vector<int> idx;
+        if (select_pass(b, rq, true, red_mats, idx)) return emit_stages(b, idx, red);
+        if (b->pend.empty()) return fail(SV_EINTERNAL, "a reduction does not fit one pass");
+        sv_status st = emit_oldest(b);
+        if (st) return st;
+    }
+}
+
+int alloc_col(sv_batch b);
+
+// a free per-branch choice column, emitting passes until one is free
+sv_status get_col(sv_batch b, int* col) {
+    while ((*col = alloc_col(b)) < 0) {
+        if (b->pend.empty()) return fail(SV_EINTERNAL, "no free choice column");
+        sv_status st = commute_on(b) ? emit_oldest(b) : flush(b);
+        if (st) return st;
+    }
+    return SV_OK;
+}
+
+// a free per-branch choice column (-1: none)
+int alloc_col(sv_batch b) {
+    for (int c = 0; c < MAX_PEND; ++c)
+        if (!((b->col_used >> c) & 1)) {
+            b->col_used |= 1ull << c;
+            return c;
+        }
+    return -1;
+}
 
 // qubits of a pass fit one tile (which always holds qubit 0)
 bool fits(sv_batch b, uint64_t act) {
@@ -518,10 +721,18 @@ bool fits(sv_batch b, uint64_t act) {
 
 // make room for a stage on qubits q[0..k-1] with `mats` matrix entries
 sv_status make_room(sv_batch b, const int* q, int k, int mats, bool needs_pend) {
+    if (commute_on(b)) {
+        // the queue may span more qubits than a pass; passes leave it when
+        // it is long or holds every choice column
+        sv_status st = SV_OK;
+        while (!st && ((int)b->pend.size() >= POOL_MAX || (needs_pend && b->col_used == ~0ull)))
+            st = emit_oldest(b);
+        return st;
+    }
     uint64_t act = b->active;
     for (int j = 0; j < k; ++j) act |= 1ull << q[j];
     if (!fits(b, act) || (int)b->pend.size() >= b->max_stages ||
-        b->mat_used + mats > MAT_SMEM - 256 || (needs_pend && b->n_pend >= MAX_PEND))
+        b->mat_used + mats > MAT_SMEM - 256 || (needs_pend && b->col_used == ~0ull))
         return flush(b);
     return SV_OK;
 }
@@ -660,6 +871,7 @@ sv_status emit_decide(sv_batch b, uint32_t op, int kind, int R, const double* cu
     d.r2 = r2;
     d.pend_prev = pend_prev;
     d.nk = R;
+    d.live_cols = b->col_used;
     for (int j = 0; j < m; ++j) d.clbit[j] = clbits[j];
     if (cum)
         for (int t = 0; t < R; ++t) d.cum[t] = cum[t];
@@ -843,7 +1055,7 @@ sv_status op_pauli(sv_batch b, uint32_t op, int k, const int* q, int n_terms, co
         b->pre_rows.push_back(r);
         b->last_random = op;
     } else {
-        pend = b->n_pend++;
+        if ((st = get_col(b, &pend))) return st;
         if ((st = upload_pool(b))) return st;
         if ((st = emit_decide(b, op, DEC_PAULI, n_terms, cum, pend, 0, nullptr))) return st;
     }
@@ -937,11 +1149,7 @@ sv_status op_kraus(sv_batch b, uint32_t op, int k, const int* q, int n_terms, co
     const std::vector<std::complex<double>> F = kraus_forms(kraus, k, n_terms);
     if (!kraus_complete(F, k, n_terms)) return fail(SV_EINVAL, "Kraus matrices are not complete (sum K^dagger K != I)");
     if ((st = ensure_started(b))) return st;
-    // the reduction must see every earlier op: queued stages + forms in one pass
-    uint64_t act = b->active;
-    for (int j = 0; j < k; ++j) act |= 1ull << q[j];
-    if (!fits(b, act) || b->mat_used + n_terms * E > MAT_SMEM - 256)
-        if ((st = flush(b))) return st;
+    // the reduction must see every earlier op that does not commute with it
     RedSpec red;
     red.kind = RED_FORMS;
     red.k = k;
@@ -951,8 +1159,9 @@ sv_status op_kraus(sv_batch b, uint32_t op, int k, const int* q, int n_terms, co
     const int mat_off = (int)b->pool.size();
     for (int i = 0; i < 2 * E * n_terms; ++i) b->pool.push_back(kraus[i]);
     if ((st = upload_pool(b))) return st;
-    if ((st = emit_pass(b, red))) return st;
-    const int pend = b->n_pend++;
+    if ((st = emit_reduction(b, red, 2 * n_terms * E))) return st;
+    int pend;
+    if ((st = get_col(b, &pend))) return st;
     if ((st = emit_decide(b, op, DEC_KRAUS, n_terms, nullptr, pend, 0, nullptr))) return st;
     PendStage s{};
     s.kind = ST_DENSE_BR;
@@ -982,9 +1191,6 @@ sv_status op_kraus_pair(sv_batch b, uint32_t op1, int qa, int n1, const double* 
     if (!kraus_complete(F1, 1, n1) || !kraus_complete(F2, 1, n2))
         return fail(SV_EINVAL, "Kraus matrices are not complete (sum K^dagger K != I)");
     if ((st = ensure_started(b))) return st;
-    uint64_t act = b->active | (1ull << qa) | (1ull << qb);
-    if (!fits(b, act) || b->mat_used + n1 * n2 * 16 + 4 * (n1 + n2) > MAT_SMEM - 256)
-        if ((st = flush(b))) return st;
     // joint forms on [qa, qb]: matrix index bit 0 <-> qa, bit 1 <-> qb
     std::vector<std::complex<double>> F((size_t)16 * n1 * n2);
     for (int i = 0; i < n1; ++i)
@@ -1005,10 +1211,11 @@ sv_status op_kraus_pair(sv_batch b, uint32_t op1, int qa, int n1, const double* 
     const int m2 = (int)b->pool.size();
     for (int i = 0; i < 8 * n2; ++i) b->pool.push_back(k2[i]);
     if ((st = upload_pool(b))) return st;
-    if ((st = emit_pass(b, red))) return st;
-    const int pend1 = b->n_pend++;
+    if ((st = emit_reduction(b, red, 2 * n1 * n2 * 16))) return st;
+    int pend1, pend2;
+    if ((st = get_col(b, &pend1))) return st;
     if ((st = emit_decide(b, op1, DEC_KRAUS_J1, n1, nullptr, pend1, 0, nullptr, n2, -1))) return st;
-    const int pend2 = b->n_pend++;
+    if ((st = get_col(b, &pend2))) return st;
     if ((st = emit_decide(b, op2, DEC_KRAUS_J2, n2, nullptr, pend2, 0, nullptr, n2, pend1))) return st;
     PendStage s{};
     s.kind = ST_DENSE_BR;
@@ -1034,18 +1241,15 @@ sv_status op_measure(sv_batch b, uint32_t op, int m, const int* q, const int* cl
     for (int j = 0; j < m; ++j)
         if (clbits[j] < 0 || clbits[j] >= b->n_clbits) return fail(SV_EINVAL, "classical bit out of range");
     if ((st = ensure_started(b))) return st;
-    uint64_t act = b->active;
-    for (int j = 0; j < m; ++j) act |= 1ull << q[j];
-    if (!fits(b, act))
-        if ((st = flush(b))) return st;
     RedSpec red;
     red.kind = RED_BINS;
     red.k = m;
     red.R = 1 << m;
     for (int j = 0; j < m; ++j) red.q[j] = q[j];
     if ((st = upload_pool(b))) return st;
-    if ((st = emit_pass(b, red))) return st;
-    const int pend = b->n_pend++;
+    if ((st = emit_reduction(b, red, 0))) return st;
+    int pend;
+    if ((st = get_col(b, &pend))) return st;
     if ((st = emit_decide(b, op, DEC_MEASURE, 1 << m, nullptr, pend, m, clbits))) return st;
     PendStage s{};
     s.kind = ST_PROJ_BR;
@@ -1336,7 +1540,7 @@ sv_status record_circuit(sv_batch b, const sv_circuit* c, std::vector<Launch>& l
     b->pool_gen += 1;
     b->started = true;  // reset / init are issued by the caller, per run
     b->rec = &launches;
-    b->n_pend = 0;
+    b->col_used = 0;
     b->pre_rows.clear();
     for (int i = 0; i < c->n_ops && !st; ++i) {
         if (b->joint && i + 1 < c->n_ops && c->kind[i] == SV_OP_KRAUS && c->kind[i + 1] == SV_OP_KRAUS &&
@@ -1526,6 +1730,7 @@ sv_status sv_free_batch(sv_batch b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
     if (b->multi_exec) cudaGraphExecDestroy(b->multi_exec);
+    if (b->multi_restart_exec) cudaGraphExecDestroy(b->multi_restart_exec);
     for (auto& e : b->prof_ev) {
         cudaEventDestroy(e.second.first);
         cudaEventDestroy(e.second.second);
@@ -1598,6 +1803,7 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
         return SV_OK;
     case SV_OPT_CHAIN_DECIDES: b->chain = v != 0; return SV_OK;
     case SV_OPT_PREDRAW_PAULI: b->predraw = v != 0; return SV_OK;
+    case SV_OPT_COMMUTE: b->commute = v != 0; return SV_OK;
     case SV_OPT_SLOT_LIMIT:
         if (v < 0) return fail(SV_EINVAL, "slot limit must be >= 0");
         if (v && b->branch && v < b->n_psets) return fail(SV_EINVAL, "fewer slots than parameter sets");
@@ -1829,6 +2035,65 @@ sv_status sv_run_circuit(sv_batch b, const sv_circuit* c, int use_graph) {
     return check_device_error(b);
 }
 
+// One CUDA graph in which batch bs[i] runs lists[i] on a branch of its own
+// (forked from and joined back to the batches' shared stream), so the
+// batches' kernels run side by side.
+static sv_status capture_branches(sv_batch* bs, const std::vector<std::vector<Launch>>& lists, cudaGraphExec_t* out) {
+    const int n = (int)lists.size();
+    sv_batch b0 = bs[0];
+    std::vector<cudaStream_t> cs(n, nullptr);
+    std::vector<cudaEvent_t> done(n, nullptr);
+    cudaEvent_t root = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&root, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+    }
+    cudaGraph_t g = nullptr;
+    bool capturing = false;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(b0->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        capturing = true;
+        e = cudaEventRecord(root, b0->stream);
+    }
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamWaitEvent(cs[i], root, 0);
+        cudaStream_t own = bs[i]->stream;
+        bs[i]->stream = cs[i];
+        for (size_t j = 0; j < lists[i].size() && e == cudaSuccess; ++j) e = exec_one(bs[i], lists[i][j]);
+        bs[i]->stream = own;
+        if (e == cudaSuccess) e = cudaEventRecord(done[i], cs[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b0->stream, done[i], 0);
+    }
+    if (capturing) {
+        const cudaError_t e2 = cudaStreamEndCapture(b0->stream, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    for (int i = 0; i < n; ++i) {
+        if (cs[i]) cudaStreamDestroy(cs[i]);
+        if (done[i]) cudaEventDestroy(done[i]);
+    }
+    if (root) cudaEventDestroy(root);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return fail(SV_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    }
+    return SV_OK;
+}
+
+static void count_launches(sv_batch b, const std::vector<Launch>& list) {
+    for (const Launch& L : list) {
+        b->n_launch += L.type == L_FINAL ? 3 : (L.type == L_DECIDE ? 2 : 1);
+        if (L.type == L_PASS) {
+            b->n_passes += 1;
+            b->pass_store.push_back(L.pass.store ? 1 : 0);
+        }
+    }
+}
+
 sv_status sv_run_circuits(sv_batch* bs, const sv_circuit* const* cs, int n, int use_graph) {
     if (!bs || !cs || n < 1) return fail(SV_EINVAL, "sv_run_circuits: NULL or empty arguments");
     sv_status st;
@@ -1871,82 +2136,79 @@ sv_status sv_run_circuits(sv_batch* bs, const sv_circuit* const* cs, int n, int 
     }
     for (int i = 0; i < n; ++i)
         if ((st = tree_begin(bs[i]))) return st;
-    if (use_graph) {
+    if (!use_graph) {
+        for (int i = 0; i < n; ++i)
+            for (const Launch& L : b0->multi_lists[i])
+                if ((st = exec(bs[i], L))) return st;
+        // shot-branching batches whose forks found no slot: restart their
+        // waiting lists one by one
+        for (int i = 0; i < n; ++i) {
+            if (!bs[i]->branch) continue;
+            std::vector<Launch> ops(b0->multi_lists[i].begin() + 2, b0->multi_lists[i].end());
+            if ((st = drain_waiting(bs[i], ops))) return st;
+        }
+    } else {
         if (!cached) {
-            if (b0->multi_exec) {
-                cudaGraphExecDestroy(b0->multi_exec);
-                b0->multi_exec = nullptr;
-            }
-            // every circuit is its own branch of the graph: its launches are
-            // captured on a stream of its own, forked from and joined back to
-            // the batches' stream, so independent circuits run side by side
-            // (small ones fill the SMs that large ones leave idle)
-            std::vector<cudaStream_t> cs(n, nullptr);
-            std::vector<cudaEvent_t> done(n, nullptr);
-            cudaEvent_t root = nullptr;
-            cudaError_t e = cudaEventCreateWithFlags(&root, cudaEventDisableTiming);
-            for (int i = 0; i < n && e == cudaSuccess; ++i) {
-                e = cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking);
-                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
-            }
-            cudaGraph_t g = nullptr;
-            bool capturing = false;
-            if (e == cudaSuccess) e = cudaStreamBeginCapture(b0->stream, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                capturing = true;
-                e = cudaEventRecord(root, b0->stream);
-            }
-            for (int i = 0; i < n && e == cudaSuccess; ++i) {
-                e = cudaStreamWaitEvent(cs[i], root, 0);
-                cudaStream_t own = bs[i]->stream;
-                bs[i]->stream = cs[i];
-                for (size_t j = 0; j < b0->multi_lists[i].size() && e == cudaSuccess; ++j)
-                    e = exec_one(bs[i], b0->multi_lists[i][j]);
-                bs[i]->stream = own;
-                if (e == cudaSuccess) e = cudaEventRecord(done[i], cs[i]);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(b0->stream, done[i], 0);
-            }
-            if (capturing) {
-                const cudaError_t e2 = cudaStreamEndCapture(b0->stream, &g);
-                if (e == cudaSuccess) e = e2;
-            }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&b0->multi_exec, g, 0);
-            if (g) cudaGraphDestroy(g);
-            for (int i = 0; i < n; ++i) {
-                if (cs[i]) cudaStreamDestroy(cs[i]);
-                if (done[i]) cudaEventDestroy(done[i]);
-            }
-            if (root) cudaEventDestroy(root);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                b0->multi_exec = nullptr;
-                return fail(SV_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
-            }
+            if (b0->multi_exec) cudaGraphExecDestroy(b0->multi_exec);
+            if (b0->multi_restart_exec) cudaGraphExecDestroy(b0->multi_restart_exec);
+            b0->multi_exec = b0->multi_restart_exec = nullptr;
+            if ((st = capture_branches(bs, b0->multi_lists, &b0->multi_exec))) return st;
             b0->multi_hash = h;
             b0->multi_gens.resize(n);
             for (int i = 0; i < n; ++i) b0->multi_gens[i] = bs[i]->pool_gen;
         }
         CU(cudaGraphLaunch(b0->multi_exec, b0->stream));
-        for (int i = 0; i < n; ++i)
-            for (const Launch& L : b0->multi_lists[i]) {
-                bs[i]->n_launch += L.type == L_FINAL ? 3 : (L.type == L_DECIDE ? 2 : 1);
-                if (L.type == L_PASS) {
-                    bs[i]->n_passes += 1;
-                    bs[i]->pass_store.push_back(L.pass.store ? 1 : 0);
+        for (int i = 0; i < n; ++i) count_launches(bs[i], b0->multi_lists[i]);
+        // Waiting lists (Section IV-B-2): every shot-branching batch restarts
+        // the shots that found no slot, as a new root, in a second cached
+        // graph with one branch per batch whose reset reads the waiting
+        // count on the device; a batch with none left does no work there.
+        // It is replayed until no batch has shots waiting.
+        std::vector<int> wait(n, 0);
+        bool any = false;
+        for (int i = 0; i < n; ++i) {
+            if (!bs[i]->branch) continue;
+            int32_t ctl[CTL_WORDS];
+            if ((st = read_ctl(bs[i], ctl))) return st;
+            if ((st = tree_snapshot(bs[i], ctl, (int)bs[i]->n_shots))) return st;
+            wait[i] = ctl[CTL_ERR] ? 0 : ctl[CTL_NWAIT];
+            any = any || wait[i] > 0;
+        }
+        std::vector<std::vector<Launch>> rl;
+        while (any) {
+            if (rl.empty())
+                for (int i = 0; i < n; ++i) {
+                    std::vector<Launch> L;
+                    if (bs[i]->branch) {
+                        Launch r;
+                        r.type = L_RESET;
+                        r.a0 = 1;
+                        r.a1 = 0;
+                        r.a2 = 2;
+                        L.push_back(r);
+                        Launch in;
+                        in.type = L_INIT;
+                        in.a0 = root_slots(bs[i], (int)bs[i]->n_shots);
+                        L.push_back(in);
+                        L.insert(L.end(), b0->multi_lists[i].begin() + 2, b0->multi_lists[i].end());
+                    }
+                    rl.push_back(std::move(L));
                 }
+            if (!b0->multi_restart_exec && (st = capture_branches(bs, rl, &b0->multi_restart_exec))) return st;
+            CU(cudaGraphLaunch(b0->multi_restart_exec, b0->stream));
+            any = false;
+            for (int i = 0; i < n; ++i) {
+                if (!bs[i]->branch) continue;
+                count_launches(bs[i], rl[i]);
+                if (wait[i] == 0) continue;
+                bs[i]->restarts += 1;
+                int32_t ctl[CTL_WORDS];
+                if ((st = read_ctl(bs[i], ctl))) return st;
+                if ((st = tree_snapshot(bs[i], ctl, wait[i]))) return st;
+                wait[i] = ctl[CTL_ERR] ? 0 : ctl[CTL_NWAIT];
+                any = any || wait[i] > 0;
             }
-    } else {
-        for (int i = 0; i < n; ++i)
-            for (const Launch& L : b0->multi_lists[i])
-                if ((st = exec(bs[i], L))) return st;
-    }
-    // shot-branching batches whose forks found no slot: restart their
-    // waiting lists one by one (the graph covered the first round)
-    for (int i = 0; i < n; ++i) {
-        if (!bs[i]->branch) continue;
-        std::vector<Launch> ops(b0->multi_lists[i].begin() + 2, b0->multi_lists[i].end());
-        if ((st = drain_waiting(bs[i], ops))) return st;
-        bs[i]->started = false;
+        }
     }
     for (int i = 0; i < n; ++i) {
         bs[i]->started = false;

@@ -500,3 +500,32 @@ def test_param_sweep_rejects_bad_sets():
         b.set_param_sets(np.arange(8) % 2, 2)
         with pytest.raises(sv.SvError):
             b.apply_param_gate_batch([0], [np.eye(2)] * 3)  # 3 matrices for 2 sets
+
+
+# ---------------------------------------------------------------------------
+# Passes that take a subset of the queued ops (SV_OPT_COMMUTE): ops on
+# other qubits commute with the pass and wait for a later one; a reduction
+# waits only for what it does not commute with
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("mode", MODES)
+def test_commuting_passes_match_oracle(mode, prec):
+    # config 3's round structure (U3 layer, CX ladder, mid-circuit
+    # measurement, conditional resets) on 14 qubits: more qubits than a tile
+    c = W.midcircuit_measure(14, 3, 0.01, [0, 5, 10], seed=140)
+    a = run_gpu(c, 3, 200, mode, prec, want_amps=[0, 199])
+    b = run_gpu(c, 3, 200, mode, prec, opts={sv.SV_OPT_COMMUTE: 0})
+    assert a["stats"]["passes"] < b["stats"]["passes"]
+    compare_shots(c, 3, a, range(200), prec)
+    compare_shots(c, 3, b, range(0, 200, 5), prec, check_amps=False)
+
+
+@pytest.mark.parametrize("kraus", [False, True])
+def test_commuting_passes_qft_match_oracle(kraus):
+    c = W.qft(13, 0.02, seed=131, kraus=kraus)
+    a = run_gpu(c, 4, 120, sv.SV_BRANCH, sv.SV_C64, want_amps=[0, 119])
+    b = run_gpu(c, 4, 120, sv.SV_BRANCH, sv.SV_C64, opts={sv.SV_OPT_COMMUTE: 0}, log=False)
+    assert a["stats"]["passes"] <= b["stats"]["passes"]
+    compare_shots(c, 4, a, range(120), sv.SV_C64)
+    rops = [op for op in c.random_ops() if c.ops[op].kind != W.FINAL]
+    check_branch_tree(a["tree"], _oracle_outcomes(c, 4, a, 120, sv.SV_C64), rops)
