@@ -358,10 +358,15 @@ def run_config4(args):
     model = T.CostModel.load()
     cands = T.candidates()
 
+    # the circuits share one memory pool: a circuit may take a state per shot
+    # (batch mode) only within its even share of it, so that batch-mode
+    # circuits do not push the wide circuits into extra waiting-list rounds
+    share = pool // len(circs)
+
     def picks_by(fn):
         out = []
         for c, s, nd in zip(circs, shots, need):
-            ok = [cfg for cfg in cands if cfg["mode"] == "branch" or nd <= pool // 8]
+            ok = [cfg for cfg in cands if cfg["mode"] == "branch" or nd <= share]
             out.append(fn(c, s, ok))
         return out
 
@@ -399,12 +404,21 @@ def run_config4(args):
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        launches = sum(b.stats()["launches"] for b in bs)
+        sts = [b.stats() for b in bs]
+        launches = sum(x["launches"] for x in sts)
+        pass_bytes = sum(x["pass_bytes"] for x in sts) / args.steps
         for b in bs:
             b.close()
-        return {"label": label, "ms_per_step": float(np.mean(ms)), "shots_per_s": sum(shots) / (np.mean(ms) / 1e3),
+        ms_step = float(np.mean(ms))
+        return {"label": label, "ms_per_step": ms_step, "shots_per_s": sum(shots) / (ms_step / 1e3),
                 "gpu_launches_per_step": launches / args.steps,
-                "batch_mode_circuits": sum(p["mode"] == "batch" for p in picks)}
+                "batch_mode_circuits": sum(p["mode"] == "batch" for p in picks),
+                "restarts_per_step": sum(x["restarts"] for x in sts) / args.steps,
+                "algorithmic_pass_bytes_per_step": pass_bytes,
+                # every circuit's passes over the whole step: how busy HBM was
+                "step_average_hbm_gbs": pass_bytes / (ms_step / 1e3) / 1e9,
+                "per_circuit": [[c.n_qubits, s, p["mode"], x["restarts"] / args.steps, x["pass_bytes"] / args.steps / 1e9]
+                                for c, s, p, x in zip(circs, shots, picks, sts)] if args.compare else None}
 
     t0 = time.perf_counter()
     mlp_picks = picks_by(lambda c, s, ok: model.pick(c, s, ok))
@@ -420,8 +434,9 @@ def run_config4(args):
     if args.compare or args.autotune:
         # the fixed policies the model has to beat
         line["fixed_branch"] = run([dict(T.DEFAULT) for _ in circs], "fixed: branch, default fusion")
-        fits = [dict(T.DEFAULT, mode="batch") if nd <= pool // 8 else dict(T.DEFAULT) for nd in need]
-        line["fixed_batch_where_it_fits"] = run(fits, "fixed: batch where a state per shot fits, else branch")
+        fits = [dict(T.DEFAULT, mode="batch") if nd <= share else dict(T.DEFAULT) for nd in need]
+        line["fixed_batch_where_it_fits"] = run(fits, "fixed: batch where a state per shot fits the circuit's "
+                                                      "even share of the pool, else branch")
     if args.autotune:
         t0 = time.perf_counter()
         small = [c for c in cands if c["joint"] == 1 and c["path"] == 0 and c["tile"] == 0 and c["max_active"] in (0, 3, 8)]

@@ -107,7 +107,8 @@ typedef enum {
     SV_OPT_LOG = 0,         /* 1: record per-shot outcomes, thresholds and fork events */
     SV_OPT_TILE_BITS = 1,   /* amplitudes per CTA tile = 2^value (0 = default)          */
     SV_OPT_MAX_ACTIVE = 2,  /* most distinct qubits fused into one pass (0 = default:
-                               all when the state fits one tile, else 4)             */
+                               all when the state fits one tile, else 4; a later
+                               SV_OPT_TILE_BITS recomputes the default)             */
     SV_OPT_MAX_STAGES = 3,  /* most ops fused into one pass (0 = default)               */
     SV_OPT_THREADS = 4,     /* threads per CTA of the pass kernel (0 = default)         */
     SV_OPT_GRID = 5,        /* CTAs of the persistent kernels (0 = default)             */

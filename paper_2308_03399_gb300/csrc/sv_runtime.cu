@@ -128,6 +128,7 @@ struct sv_batch_s {
     int red_chunks = 1;  // chunk records written by the last pass with a reduction
     int threads = 256, grid_pass = 0, grid_small = 0, n_sm = 0;
     int max_active = 8, max_stages = MAX_STAGES;  // max_active is set in sv_alloc_batch
+    bool max_active_set = false;  // SV_OPT_MAX_ACTIVE given explicitly (a new tile size keeps it)
     bool branch = false;
     // device memory
     std::vector<void*> allocs;
@@ -1779,9 +1780,11 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
         if (b->started) return fail(SV_EINVAL, "set the tile size before the first op");
         b->tb = std::min<int>(b->n, v ? (int)v : (b->prec == SV_C128 ? 10 : 11));
         b->chunks = (int)std::min<int64_t>(1ll << (b->n - b->tb), b->dev.max_chunks);
+        if (!b->max_active_set) b->max_active = b->n <= b->tb ? b->n : 4;
         return SV_OK;
     case SV_OPT_MAX_ACTIVE:
         b->max_active = v ? (int)std::max<int64_t>(2, v) : (b->n <= b->tb ? b->n : 4);
+        b->max_active_set = v != 0;
         return SV_OK;
     case SV_OPT_MAX_STAGES: b->max_stages = v ? (int)std::min<int64_t>(std::max<int64_t>(v, 1), MAX_STAGES) : MAX_STAGES; return SV_OK;
     case SV_OPT_THREADS:

@@ -153,10 +153,12 @@ class CostModel:
             params = np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), w3, [0.0]])
         self.mlp.set_params(params)
         self.mu = np.zeros(1, np.float32)
+        self.n_max = 0  # largest qubit count in the training records (0: no limit)
 
     def fit(self, records, epochs=400, batch=32, lr=3e-3, seed=0):
         X, y = dataset(records)
         self.mu = np.array([y.mean()], np.float32)  # predict deviations from the mean log time
+        self.n_max = max(int(r["n"]) for r in records if r["ms"] is not None)
         return self.mlp.train(X, y - self.mu[0], epochs=epochs, batch=min(batch, len(y)), lr=lr, seed=seed)
 
     def predict(self, circ, shots, cands=None):
@@ -167,8 +169,13 @@ class CostModel:
 
     def pick(self, circ, shots, cands=None, verify=0, seed=1):
         """argmin of the predicted time; with verify=k the k best predictions
-        are timed on the GPU and the fastest is kept (autotuner fallback)."""
+        are timed on the GPU and the fastest is kept (autotuner fallback).
+        A circuit wider than any the model was trained on gets the library's
+        defaults: past its training range the model extrapolates from
+        smaller states, where passes are cheap and nothing restarts."""
         cands = cands or candidates()
+        if self.n_max and circ.n_qubits > self.n_max:
+            return dict(DEFAULT)
         pred = self.predict(circ, shots, cands)
         order = np.argsort(pred)
         if verify <= 0:
@@ -179,7 +186,7 @@ class CostModel:
 
     def save(self, path):
         with open(path, "w") as f:
-            json.dump({"hidden": self.hidden, "mu": float(self.mu[0]),
+            json.dump({"hidden": self.hidden, "mu": float(self.mu[0]), "n_max": int(self.n_max),
                        "params": [float(x) for x in self.mlp.get_params()]}, f)
 
     @classmethod
@@ -190,6 +197,7 @@ class CostModel:
         d = json.load(open(path))
         m = cls(hidden=int(d["hidden"]), params=np.asarray(d["params"], np.float32))
         m.mu = np.array([d["mu"]], np.float32)
+        m.n_max = int(d.get("n_max", 0))
         return m
 
 

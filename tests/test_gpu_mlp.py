@@ -49,18 +49,18 @@ def test_training_reduces_loss():
 
 def test_trained_cost_model_gains_over_fixed_configuration():
     """Trained on the committed GB300 timing log (the simulator's own
-    measurements), the model picks a configuration per held-out circuit;
-    every candidate is also timed live.  The model must stay close to the
-    per-circuit best and clearly beat the worse of the two fixed methods
-    (always batch, always branch); its ratio to the best fixed choice is
-    printed."""
+    measurements), the model picks a configuration per held-out circuit
+    (drawn from the training distribution with another seed); every
+    candidate is also timed live.  The model's total must be no worse than
+    the best fixed configuration (one configuration for every circuit,
+    chosen with hindsight) within 5% timing noise, and stay close to the
+    per-circuit best; the ratios are printed."""
     import json
     import os
     log = os.path.join(os.path.dirname(T.__file__), "data", "tuner_log_gb300.jsonl")
     recs = [json.loads(ln) for ln in open(log)]
     cands = [c for c in T.candidates() if c["joint"] == 1 and c["path"] == 0 and c["max_active"] in (0, 3, 8)]
-    held = T.training_circuits(seed=21, count=8, max_n=18)
-    held = [(c, s) for c, s in held if c.n_qubits >= 10]
+    held = T.training_circuits(seed=21, count=12, max_n=18)
     model = T.CostModel(seed=0)
     model.fit(recs, epochs=300)
     t_model = t_best = 0.0
@@ -73,11 +73,12 @@ def test_trained_cost_model_gains_over_fixed_configuration():
         for k in fixed:
             fixed[k] += times[k]
     by_mode = {m: min(v for k, v in fixed.items() if k[0] == m) for m in ("batch", "branch")}
+    best_fixed = min(fixed.values())
     print(f"held-out ({len(held)} circuits) total ms: model {t_model:.1f}, per-circuit best {t_best:.1f}, "
-          f"best fixed {min(fixed.values()):.1f}, always-batch {by_mode['batch']:.1f}, "
-          f"always-branch {by_mode['branch']:.1f}")
+          f"best fixed {best_fixed:.1f}, always-batch {by_mode['batch']:.1f}, "
+          f"always-branch {by_mode['branch']:.1f}; model / best fixed {t_model / best_fixed:.3f}")
+    assert t_model <= 1.05 * best_fixed
     assert t_model <= 1.3 * t_best
-    assert t_model < max(by_mode.values())
 
 
 def json_key(cfg):
