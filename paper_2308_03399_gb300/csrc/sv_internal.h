@@ -76,6 +76,8 @@ struct PassDesc {
     int32_t red_pos[MAX_STAGE_Q];
     int32_t reg_wp;            // > 0: register path (k_pass_reg), group of 2^reg_wp amplitudes
     int32_t reg_paired;        // register path: qubit 0 is group bit 0 (128-bit pairs)
+    int32_t fold;              // register path, complex64: the stages composed into one
+                               // 2^reg_wp x 2^reg_wp matrix per branch, applied once per group
     Stage st[MAX_STAGES];
 };
 

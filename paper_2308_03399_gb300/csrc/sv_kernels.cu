@@ -1177,13 +1177,74 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
     const int mat_stride = (p.mat_elems + 1) & ~1;
     T* mats = reinterpret_cast<T*>(smem_raw) + (size_t)warp * mat_stride;
     int* w_sel = reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) + (size_t)nwarps * mat_stride) +
-                 warp * 2 * MAX_STAGES;
+                 warp * 4 * MAX_STAGES;
     int* w_packed = w_sel + MAX_STAGES;
+    double* w_scale = reinterpret_cast<double*>(w_sel + 2 * MAX_STAGES);
     // complex64 only: expanded copies of the stages' matrices for packed FMAs
     ulonglong2* matx = reinterpret_cast<ulonglong2*>(reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) +
                                                                             (size_t)nwarps * mat_stride) +
-                                                     nwarps * 2 * MAX_STAGES) +
+                                                     nwarps * 4 * MAX_STAGES) +
                        (size_t)warp * mat_stride;
+
+    // complex64 passes with many stages: the stages folded into one matrix
+    // per branch, after the expanded matrices
+    ulonglong2* fold_m = matx + (size_t)nwarps * mat_stride + (size_t)warp * G * G;
+    uint64_t skipmask = 0;
+    // every stage of the pass, in op order, on one group of G amplitudes
+    auto apply_stages = [&](T (&v)[G]) {
+        for (int s = 0; s < p.n_stages; ++s) {
+            if ((skipmask >> s) & 1) continue;
+            const Stage& st = p.st[s];
+            if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
+                if (st.k == 1) {
+                    const int shape = w_packed[s];
+                    if (shape) reg_apply1s_dyn<T, G>(v, st.pos[0], mats + st.mat, shape);
+                    else reg_apply1_dyn<T, G>(v, st.pos[0], mats + st.mat);
+                } else if (const int mi = w_packed[s]) {
+                    reg_mono_dyn<T, G>(v, st.pos[0], st.pos[1], mi, mats + st.mat);
+                } else {
+                    if constexpr (sizeof(T) == 8)
+                        reg_apply2x_dyn<G>(reinterpret_cast<float2*>(v), st.pos[0], st.pos[1], matx + st.mat);
+                    else
+                        reg_apply2_dyn<T, G>(v, st.pos[0], st.pos[1], mats + st.mat);
+                }
+            } else if (st.kind == ST_PAULI_BR) {
+                // out[e] = (-i)^ny (-1)^popcount(z & e) in[e ^ x]
+                const int info = w_packed[s];
+                reg_xor_mask<T, G>(v, info & 15);
+                const bool rot = (info >> 4) & 1;
+                const int sign = info >> 8;
+#pragma unroll
+                for (int e = 0; e < G; ++e) {
+                    T t = v[e];
+                    if (rot) {
+                        const R x = t.x;
+                        t.x = t.y;
+                        t.y = -x;
+                    }
+                    if ((sign >> e) & 1) {
+                        t.x = -t.x;
+                        t.y = -t.y;
+                    }
+                    v[e] = t;
+                }
+            } else {  // ST_PROJ_BR
+                const int info = w_packed[s];
+                const R sc = mats[st.mat].x;
+#pragma unroll
+                for (int e = 0; e < G; ++e) {
+                    if ((info >> e) & 1) {
+                        v[e].x *= sc;
+                        v[e].y *= sc;
+                    } else {
+                        v[e].x = 0;
+                        v[e].y = 0;
+                    }
+                }
+                reg_xor_mask<T, G>(v, (info >> 16) & 15);
+            }
+        }
+    };
 
     const int n_br = d.ctl[CTL_NBR];
     if (blockIdx.x == 0 && threadIdx.x == 0 && d.pass_log) {
@@ -1203,7 +1264,6 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
     T* const states = reinterpret_cast<T*>(d.states);
     const R* pool = reinterpret_cast<const R*>(d.pool);
     int cur_b = -1;
-    uint64_t skipmask = 0;
     for (int64_t u = u0; u < u1; ++u) {
         const int b = (int)(u / p.chunks);
         const int c = (int)(u % p.chunks);
@@ -1218,70 +1278,77 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
             // are loaded for the warp's first branch only; a branch's own
             // stages (choices, parameter sets) on every branch change
             const bool first = cur_b < 0;
-            skipmask = 0;
             __syncwarp();
-            for (int s = 0; s < p.n_stages; ++s) {
-                const Stage& st = p.st[s];
-                if (st.kind == ST_DENSE && !first) {  // only its condition is per branch
-                    if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val)
-                        skipmask |= 1ull << s;
-                    continue;
-                }
-                int sk = 0, sel = 0, packed = 0;
-                double scale = 1.0;
-                if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val) sk = 1;
-                if (st.pre) {  // batch mode: the branch's one shot, pre-drawn
-                    sel = d.pre_sel[(int64_t)st.pend * d.cap_br + d.perm[d.br_start[b]]];
-                    packed = d.ipool[st.off + sel];
-                    if ((packed & 0xff) == 0) sk = 1;
-                } else if (st.pend == PEND_PSET) {  // the branch's parameter set
-                    sel = d.br_pset[b];
-                } else if (st.kind != ST_DENSE) {
-                    sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
-                    scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
-                    if (sel < 0) sk = 1;
-                    if (st.kind == ST_PAULI_BR && !sk) {
+            // each lane takes its stages' choices: the loads of different
+            // stages overlap instead of forming one chain per stage
+            skipmask = 0;
+            for (int s0 = 0; s0 < p.n_stages; s0 += 32) {
+                const int s = s0 + lane;
+                int sk = 0;
+                if (s < p.n_stages) {
+                    const Stage& st = p.st[s];
+                    int sel = 0, packed = 0;
+                    double scale = 1.0;
+                    if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val) sk = 1;
+                    if (st.kind == ST_DENSE) {
+                        // only its condition is per branch
+                    } else if (st.pre) {  // batch mode: the branch's one shot, pre-drawn
+                        sel = d.pre_sel[(int64_t)st.pend * d.cap_br + d.perm[d.br_start[b]]];
                         packed = d.ipool[st.off + sel];
                         if ((packed & 0xff) == 0) sk = 1;
+                    } else if (st.pend == PEND_PSET) {  // the branch's parameter set
+                        sel = d.br_pset[b];
+                    } else {
+                        sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
+                        scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
+                        if (sel < 0) sk = 1;
+                        if (st.kind == ST_PAULI_BR && !sk) {
+                            packed = d.ipool[st.off + sel];
+                            if ((packed & 0xff) == 0) sk = 1;
+                        }
                     }
-                }
-                if (sk) skipmask |= 1ull << s;
-                // Pauli and projection stages in group form, once per branch:
-                // Pauli: bits 0-3 flip mask, bit 4 the (-i) factor, bits 8+
-                // the sign of each group element; projection: bits 0-15 the
-                // kept elements, bits 16-19 the flips of a reset
-                int info = packed;
-                if (!sk && st.kind == ST_PAULI_BR) {
-                    const int xm = packed & 15, zm = (packed >> 4) & 15, ny = (packed >> 8) & 3;
-                    int xg = 0, zg = 0;
-                    for (int j = 0; j < st.k; ++j) {
-                        if ((xm >> j) & 1) xg |= 1 << st.pos[j];
-                        if ((zm >> j) & 1) zg |= 1 << st.pos[j];
+                    // Pauli and projection stages in group form, once per
+                    // branch: Pauli: bits 0-3 flip mask, bit 4 the (-i)
+                    // factor, bits 8+ the sign of each group element;
+                    // projection: bits 0-15 the kept elements, bits 16-19 the
+                    // flips of a reset
+                    if (!sk && st.kind == ST_PAULI_BR) {
+                        const int xm = packed & 15, zm = (packed >> 4) & 15, ny = (packed >> 8) & 3;
+                        int xg = 0, zg = 0;
+                        for (int j = 0; j < st.k; ++j) {
+                            if ((xm >> j) & 1) xg |= 1 << st.pos[j];
+                            if ((zm >> j) & 1) zg |= 1 << st.pos[j];
+                        }
+                        int sign = 0;
+                        for (int e = 0; e < G; ++e)
+                            if ((((ny >> 1) & 1) ^ (__popc(zg & e) & 1)) != 0) sign |= 1 << e;
+                        w_packed[s] = xg | ((ny & 1) << 4) | (sign << 8);
+                    } else if (!sk && st.kind == ST_PROJ_BR) {
+                        int keep = 0, xr = 0;
+                        for (int e = 0; e < G; ++e) {
+                            int o = 0;
+                            for (int j = 0; j < st.k; ++j) o |= ((e >> st.pos[j]) & 1) << j;
+                            if (o == sel) keep |= 1 << e;
+                        }
+                        if (st.reset)
+                            for (int j = 0; j < st.k; ++j)
+                                if ((sel >> j) & 1) xr |= 1 << st.pos[j];
+                        w_packed[s] = keep | (xr << 16);
                     }
-                    int sign = 0;
-                    for (int e = 0; e < G; ++e)
-                        if ((((ny >> 1) & 1) ^ (__popc(zg & e) & 1)) != 0) sign |= 1 << e;
-                    info = xg | ((ny & 1) << 4) | (sign << 8);
-                } else if (!sk && st.kind == ST_PROJ_BR) {
-                    int keep = 0, xr = 0;
-                    for (int e = 0; e < G; ++e) {
-                        int o = 0;
-                        for (int j = 0; j < st.k; ++j) o |= ((e >> st.pos[j]) & 1) << j;
-                        if (o == sel) keep |= 1 << e;
-                    }
-                    if (st.reset)
-                        for (int j = 0; j < st.k; ++j)
-                            if ((sel >> j) & 1) xr |= 1 << st.pos[j];
-                    info = keep | (xr << 16);
-                }
-                if (lane == 0) {
                     w_sel[s] = sel;
-                    w_packed[s] = info;
+                    w_scale[s] = scale;
                 }
-                if ((!sk || st.kind == ST_DENSE) && (st.kind == ST_DENSE || st.kind == ST_DENSE_BR)) {
+                skipmask |= (uint64_t)__ballot_sync(0xffffffffu, sk) << s0;
+            }
+            __syncwarp();
+            // matrices: lanes over a stage's entries
+            for (int s = 0; s < p.n_stages; ++s) {
+                const Stage& st = p.st[s];
+                if (st.kind == ST_DENSE ? !first : ((skipmask >> s) & 1)) continue;
+                if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
                     const int D2 = 1 << (2 * st.k);
-                    const R* src = pool + st.off + (st.kind == ST_DENSE_BR ? (int64_t)sel * st.stride : 0);
-                    const R sc = (R)scale;
+                    const R* src = pool + st.off + (st.kind == ST_DENSE_BR ? (int64_t)w_sel[s] * st.stride : 0);
+                    const R sc = (R)w_scale[s];
                     for (int e = lane; e < D2; e += 32) {
                         T m;
                         m.x = src[2 * e] * sc;
@@ -1313,9 +1380,9 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                         if (shape == 2 && src[3] == 0 && src[5] == 0) shape |= 4;
                         w_packed[s] = shape;
                     }
-                } else if (!sk && st.kind == ST_PROJ_BR && lane == 0) {
+                } else if (st.kind == ST_PROJ_BR && lane == 0) {
                     T m;
-                    m.x = (R)scale;
+                    m.x = (R)w_scale[s];
                     m.y = 0;
                     mats[st.mat] = m;
                 }
@@ -1331,6 +1398,25 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                 }
             }
             __syncwarp();
+            if constexpr (sizeof(T) == 8) {
+                if (p.fold) {
+                    // lane c < G runs the stages on the unit vector e_c: its
+                    // result is column c of the pass's matrix for this branch
+                    T col[G];
+#pragma unroll
+                    for (int e = 0; e < G; ++e) {
+                        col[e].x = e == lane ? (R)1 : (R)0;
+                        col[e].y = 0;
+                    }
+                    apply_stages(col);
+                    if (lane < G)
+#pragma unroll
+                        for (int r = 0; r < G; ++r)
+                            fold_m[r * G + lane] = make_ulonglong2(pk2((float)col[r].x, (float)col[r].x),
+                                                                   pk2((float)col[r].y, (float)col[r].y));
+                    __syncwarp();
+                }
+            }
             cur_b = b;
         }
         Acc<R> acc[REG_MAX_RED];
@@ -1380,70 +1466,53 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
 #pragma unroll
                 for (int e = 0; e < G; ++e) v[e] = g[off(e)];
             }
-            for (int s = 0; s < p.n_stages; ++s) {
-                if ((skipmask >> s) & 1) continue;
-                const Stage& st = p.st[s];
-                if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
-                    if (st.k == 1) {
-                        const int shape = w_packed[s];
-                        if (shape) reg_apply1s_dyn<T, G>(v, st.pos[0], mats + st.mat, shape);
-                        else reg_apply1_dyn<T, G>(v, st.pos[0], mats + st.mat);
-                    } else if (const int mi = w_packed[s]) {
-                        reg_mono_dyn<T, G>(v, st.pos[0], st.pos[1], mi, mats + st.mat);
-                    } else {
-                        if constexpr (sizeof(T) == 8)
-                            reg_apply2x_dyn<G>(reinterpret_cast<float2*>(v), st.pos[0], st.pos[1], matx + st.mat);
-                        else
-                            reg_apply2_dyn<T, G>(v, st.pos[0], st.pos[1], mats + st.mat);
-                    }
-                } else if (st.kind == ST_PAULI_BR) {
-                    // out[e] = (-i)^ny (-1)^popcount(z & e) in[e ^ x]
-                    const int info = w_packed[s];
-                    reg_xor_mask<T, G>(v, info & 15);
-                    const bool rot = (info >> 4) & 1;
-                    const int sign = info >> 8;
+            bool folded = false;
+            if constexpr (sizeof(T) == 8) {
+                if (p.fold) {
+                    // the pass's stages folded into one G x G matrix (row r,
+                    // column c at fold_m[r * G + c] as ((re, re), (im, im)));
+                    // a folded pass has no reduction, so each pair of output
+                    // rows is stored as soon as it is formed
+#pragma unroll 1
+                    for (int r = 0; r < G; r += 2) {
+                        unsigned long long P0 = 0ull, Q0 = 0ull, P1 = 0ull, Q1 = 0ull;
 #pragma unroll
-                    for (int e = 0; e < G; ++e) {
-                        T t = v[e];
-                        if (rot) {
-                            const R x = t.x;
-                            t.x = t.y;
-                            t.y = -x;
+                        for (int c2 = 0; c2 < G; ++c2) {
+                            const unsigned long long vp = pk2(v[c2].x, v[c2].y);
+                            const ulonglong2 m0 = fold_m[r * G + c2], m1 = fold_m[(r + 1) * G + c2];
+                            P0 = fma2(m0.x, vp, P0);
+                            Q0 = fma2(m0.y, vp, Q0);
+                            P1 = fma2(m1.x, vp, P1);
+                            Q1 = fma2(m1.y, vp, Q1);
                         }
-                        if ((sign >> e) & 1) {
-                            t.x = -t.x;
-                            t.y = -t.y;
-                        }
-                        v[e] = t;
-                    }
-                } else {  // ST_PROJ_BR
-                    const int info = w_packed[s];
-                    const R sc = mats[st.mat].x;
-#pragma unroll
-                    for (int e = 0; e < G; ++e) {
-                        if ((info >> e) & 1) {
-                            v[e].x *= sc;
-                            v[e].y *= sc;
+                        const float2 p0 = upk2(P0), q0 = upk2(Q0), p1 = upk2(P1), q1 = upk2(Q1);
+                        const float2 o0 = make_float2(p0.x - q0.y, p0.y + q0.x);
+                        const float2 o1 = make_float2(p1.x - q1.y, p1.y + q1.x);
+                        if constexpr (PAIRED) {
+                            *reinterpret_cast<float4*>(g + off(r)) = make_float4(o0.x, o0.y, o1.x, o1.y);
                         } else {
-                            v[e].x = 0;
-                            v[e].y = 0;
+                            g[off(r)] = o0;
+                            g[off(r + 1)] = o1;
                         }
                     }
-                    reg_xor_mask<T, G>(v, (info >> 16) & 15);
+                    folded = true;
                 }
             }
-            if (p.red_kind == RED_FORMS)
-                reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - 8 * p.red_R, p.red_R, acc);
-            else if (p.red_kind == RED_DIAG)
-                reg_diag<R, G>(v, p, acc);
-            if (p.store) {
-                if constexpr (sizeof(T) == 8 && PAIRED) {
+            if (!folded) {
+                apply_stages(v);
+                if (p.red_kind == RED_FORMS)
+                    reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - 8 * p.red_R, p.red_R, acc);
+                else if (p.red_kind == RED_DIAG)
+                    reg_diag<R, G>(v, p, acc);
+                if (p.store) {
+                    if constexpr (sizeof(T) == 8 && PAIRED) {
 #pragma unroll
-                    for (int e = 0; e < G; e += 2)
-                        *reinterpret_cast<float4*>(g + off(e)) = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
-                } else {
+                        for (int e = 0; e < G; e += 2)
+                            *reinterpret_cast<float4*>(g + off(e)) = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
+                    } else {
 #pragma unroll
-                    for (int e = 0; e < G; ++e) g[off(e)] = v[e];
+                        for (int e = 0; e < G; ++e) g[off(e)] = v[e];
+                    }
                 }
             }
         }
@@ -2384,7 +2453,8 @@ size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads) {
     const size_t c = prec ? 16 : 8;
     const size_t nw = threads / 32;
     const size_t m = (size_t)((p.mat_elems + 1) & ~1);
-    return nw * (m * c + 2 * MAX_STAGES * 4) + (prec ? 0 : nw * m * 16);
+    const size_t g = (size_t)1 << p.reg_wp;
+    return nw * (m * c + 4 * MAX_STAGES * 4) + (prec ? 0 : nw * m * 16) + (p.fold && !prec ? nw * g * g * 16 : 0);
 }
 
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s) {

@@ -150,6 +150,7 @@ struct sv_batch_s {
     // recorded circuits: a pass takes a dependency-closed subset of the
     // pending stages, so stages on other qubits can wait for a later pass
     bool commute = true;
+    bool fold = true;  // SV_OPT_FOLD
     std::vector<Launch>* rec = nullptr;
     bool started = false;
     uint32_t last_random = 0xffffffffu;
@@ -391,6 +392,39 @@ struct RedSpec {
     int q[MAX_STAGE_Q] = {};
 };
 
+// Rough per-group instruction counts of the register kernel (a group is
+// G = 2^wp amplitudes of one lane): every stage costs a dispatch plus its
+// arithmetic; a folded pass costs G x G complex products (two packed FMAs
+// and one shared-memory load each) and one composition per branch.
+int stage_group_cost(sv_batch b, const PendStage& ps, int G) {
+    int c = 40;  // stage dispatch: descriptor loads, skip test, switch
+    if (ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) {
+        const double* m = ps.kind == ST_DENSE ? &b->pool[ps.off] : nullptr;
+        auto z = [&](int e) { return m[2 * e] == 0 && m[2 * e + 1] == 0; };
+        if (ps.k == 1) {
+            const bool shaped = m && ((z(1) && z(2)) || (z(0) && z(3)));
+            c += shaped ? 2 * G : (m ? 8 * G : 4 * G);
+        } else {
+            int nz = 0;
+            if (m)
+                for (int e = 0; e < 16; ++e) nz += !z(e);
+            c += nz == 4 ? 2 * G : 12 * G;
+        }
+    } else if (ps.kind == ST_PAULI_BR) {
+        c += 3 * G;
+    } else {
+        c += 2 * G;
+    }
+    return c;
+}
+
+bool fold_pays(sv_batch b, const std::vector<const PendStage*>& ss, int wp) {
+    const int G = 1 << wp;
+    int64_t c = 0;
+    for (const PendStage* ps : ss) c += stage_group_cost(b, *ps, G);
+    return c * 4 > 5 * (int64_t)(3 * G * G + 60);
+}
+
 // can a pass run in registers (k_pass_reg)?  its qubits plus qubit 0 <= 4,
 // dense stages <= 2 qubits, and no reduction or <= 4 one-qubit forms
 int reg_width(sv_batch b, const RedSpec& red, uint64_t act, const std::vector<const PendStage*>& ss) {
@@ -539,6 +573,10 @@ sv_status emit_stages(sv_batch b, const std::vector<int>& idx, const RedSpec& re
     if (p.red_kind == RED_FORMS) mat += 2 * (red.R << (2 * red.k));
     else if (p.red_kind == RED_DIAG) mat += 2 * (red.R << red.k);
     p.mat_elems = mat;
+    if (wp > 0 && b->fold && b->prec == SV_C64 && red.kind == RED_NONE && p.store && fold_pays(b, ss, wp)) {
+        p.fold = 1;
+        if (pass_reg_smem_bytes(0, p, pass_reg_threads(0)) > 48 * 1024) p.fold = 0;
+    }
     // the rest of the queue stays pending
     std::vector<PendStage> rest;
     std::vector<char> taken(b->pend.size(), 0);
@@ -1807,6 +1845,7 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
     case SV_OPT_CHAIN_DECIDES: b->chain = v != 0; return SV_OK;
     case SV_OPT_PREDRAW_PAULI: b->predraw = v != 0; return SV_OK;
     case SV_OPT_COMMUTE: b->commute = v != 0; return SV_OK;
+    case SV_OPT_FOLD: b->fold = v != 0; return SV_OK;
     case SV_OPT_SLOT_LIMIT:
         if (v < 0) return fail(SV_EINVAL, "slot limit must be >= 0");
         if (v && b->branch && v < b->n_psets) return fail(SV_EINVAL, "fewer slots than parameter sets");

@@ -529,3 +529,24 @@ def test_commuting_passes_qft_match_oracle(kraus):
     compare_shots(c, 4, a, range(120), sv.SV_C64)
     rops = [op for op in c.random_ops() if c.ops[op].kind != W.FINAL]
     check_branch_tree(a["tree"], _oracle_outcomes(c, 4, a, 120, sv.SV_C64), rops)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("case", ["qft13", "brick9_w3"])
+def test_folded_passes_match_oracle(case, mode):
+    # Register passes with many stages and no reduction compose their stages
+    # per branch into one 2^w x 2^w matrix (SV_OPT_FOLD): QFT passes on 13
+    # qubits hold up to ~30 one- and two-qubit ops on 4 qubits; a 9-qubit
+    # brickwork at fusion width 3 folds 8 x 8 matrices.  Folded and
+    # stage-by-stage runs give the oracle's shots and the same states.
+    if case == "qft13":
+        c, opts = W.qft(13, 0.02, seed=133), {}
+    else:
+        c, opts = W.brickwork(9, 10, 0.02, 0.05, seed=134), {sv.SV_OPT_MAX_ACTIVE: 3}
+    amps = [0, 77, 149]
+    a = run_gpu(c, 6, 150, mode, sv.SV_C64, opts=opts, want_amps=amps)
+    b = run_gpu(c, 6, 150, mode, sv.SV_C64, opts=dict(opts, **{sv.SV_OPT_FOLD: 0}), want_amps=amps)
+    compare_shots(c, 6, a, range(150), sv.SV_C64)
+    compare_shots(c, 6, b, range(0, 150, 10), sv.SV_C64, check_amps=False)
+    for s in amps:
+        np.testing.assert_allclose(a["amps"][s], b["amps"][s], atol=2e-6)
