@@ -1173,22 +1173,19 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
     constexpr int G = 1 << WP;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    // per-warp shared memory: matrices | stage choice | stage packed | stage scale
+    // shared memory, each region one slice per warp: matrices | stage
+    // choice, packed form, scale (4 x MAX_STAGES words) | complex64 only:
+    // the matrices expanded for packed FMAs | the folded matrix (G x G)
     const int mat_stride = (p.mat_elems + 1) & ~1;
-    T* mats = reinterpret_cast<T*>(smem_raw) + (size_t)warp * mat_stride;
-    int* w_sel = reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) + (size_t)nwarps * mat_stride) +
-                 warp * 4 * MAX_STAGES;
+    T* const mats_all = reinterpret_cast<T*>(smem_raw);
+    int* const words_all = reinterpret_cast<int*>(mats_all + (size_t)nwarps * mat_stride);
+    ulonglong2* const matx_all = reinterpret_cast<ulonglong2*>(words_all + (size_t)nwarps * 4 * MAX_STAGES);
+    T* mats = mats_all + (size_t)warp * mat_stride;
+    int* w_sel = words_all + (size_t)warp * 4 * MAX_STAGES;
     int* w_packed = w_sel + MAX_STAGES;
     double* w_scale = reinterpret_cast<double*>(w_sel + 2 * MAX_STAGES);
-    // complex64 only: expanded copies of the stages' matrices for packed FMAs
-    ulonglong2* matx = reinterpret_cast<ulonglong2*>(reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) +
-                                                                            (size_t)nwarps * mat_stride) +
-                                                     nwarps * 4 * MAX_STAGES) +
-                       (size_t)warp * mat_stride;
-
-    // complex64 passes with many stages: the stages folded into one matrix
-    // per branch, after the expanded matrices
-    ulonglong2* fold_m = matx + (size_t)nwarps * mat_stride + (size_t)warp * G * G;
+    ulonglong2* matx = matx_all + (size_t)warp * mat_stride;
+    ulonglong2* fold_m = matx_all + (size_t)nwarps * mat_stride + (size_t)warp * G * G;
     uint64_t skipmask = 0;
     // every stage of the pass, in op order, on one group of G amplitudes
     auto apply_stages = [&](T (&v)[G]) {

@@ -440,7 +440,8 @@ int reg_width(sv_batch b, const RedSpec& red, uint64_t act, const std::vector<co
     // the per-warp matrix copies must fit the default 48 KB of dynamic
     // shared memory of the register kernels; longer stage lists take tiles
     PassDesc probe;
-    probe.mat_elems = 0;
+    memset(&probe, 0, sizeof(probe));
+    probe.reg_wp = wp;
     for (const PendStage* ps : ss)
         probe.mat_elems += (ps->kind == ST_DENSE || ps->kind == ST_DENSE_BR) ? 1 << (2 * ps->k)
                                                                             : (ps->kind == ST_PROJ_BR ? 1 : 0);
