@@ -545,7 +545,7 @@ def test_folded_passes_match_oracle(case, mode):
         c, opts = W.brickwork(9, 10, 0.02, 0.05, seed=134), {sv.SV_OPT_MAX_ACTIVE: 3}
     amps = [0, 77, 149]
     a = run_gpu(c, 6, 150, mode, sv.SV_C64, opts=opts, want_amps=amps)
-    b = run_gpu(c, 6, 150, mode, sv.SV_C64, opts=dict(opts, **{sv.SV_OPT_FOLD: 0}), want_amps=amps)
+    b = run_gpu(c, 6, 150, mode, sv.SV_C64, opts={**opts, sv.SV_OPT_FOLD: 0}, want_amps=amps)
     compare_shots(c, 6, a, range(150), sv.SV_C64)
     compare_shots(c, 6, b, range(0, 150, 10), sv.SV_C64, check_amps=False)
     for s in amps:
