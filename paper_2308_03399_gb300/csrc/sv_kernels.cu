@@ -1166,7 +1166,7 @@ template <> struct RegCta<double> { static constexpr int threads = 256, min_bloc
 
 int pass_reg_threads(int prec) { return prec ? RegCta<double>::threads : RegCta<float>::threads; }
 
-template <class R, int WP, int PAIRED>
+template <class R, int WP, int PAIRED, int FOLD>
 __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
     k_pass_reg(DevBatch d, const __grid_constant__ PassDesc p) {
     using T = typename Cplx<R>::T;
@@ -1395,24 +1395,22 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                 }
             }
             __syncwarp();
-            if constexpr (sizeof(T) == 8) {
-                if (p.fold) {
-                    // lane c < G runs the stages on the unit vector e_c: its
-                    // result is column c of the pass's matrix for this branch
-                    T col[G];
+            if constexpr (FOLD && sizeof(T) == 8) {
+                // lane c < G runs the stages on the unit vector e_c: its
+                // result is column c of the pass's matrix for this branch
+                T col[G];
 #pragma unroll
-                    for (int e = 0; e < G; ++e) {
-                        col[e].x = e == lane ? (R)1 : (R)0;
-                        col[e].y = 0;
-                    }
-                    apply_stages(col);
-                    if (lane < G)
-#pragma unroll
-                        for (int r = 0; r < G; ++r)
-                            fold_m[r * G + lane] = make_ulonglong2(pk2((float)col[r].x, (float)col[r].x),
-                                                                   pk2((float)col[r].y, (float)col[r].y));
-                    __syncwarp();
+                for (int e = 0; e < G; ++e) {
+                    col[e].x = e == lane ? (R)1 : (R)0;
+                    col[e].y = 0;
                 }
+                apply_stages(col);
+                if (lane < G)
+#pragma unroll
+                    for (int r = 0; r < G; ++r)
+                        fold_m[r * G + lane] = make_ulonglong2(pk2((float)col[r].x, (float)col[r].x),
+                                                               pk2((float)col[r].y, (float)col[r].y));
+                __syncwarp();
             }
             cur_b = b;
         }
@@ -1463,39 +1461,34 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
 #pragma unroll
                 for (int e = 0; e < G; ++e) v[e] = g[off(e)];
             }
-            bool folded = false;
-            if constexpr (sizeof(T) == 8) {
-                if (p.fold) {
-                    // the pass's stages folded into one G x G matrix (row r,
-                    // column c at fold_m[r * G + c] as ((re, re), (im, im)));
-                    // a folded pass has no reduction, so each pair of output
-                    // rows is stored as soon as it is formed
+            if constexpr (FOLD && sizeof(T) == 8) {
+                // the pass's stages folded into one G x G matrix (row r,
+                // column c at fold_m[r * G + c] as ((re, re), (im, im)));
+                // a folded pass has no reduction, so each pair of output
+                // rows is stored as soon as it is formed
 #pragma unroll 1
-                    for (int r = 0; r < G; r += 2) {
-                        unsigned long long P0 = 0ull, Q0 = 0ull, P1 = 0ull, Q1 = 0ull;
+                for (int r = 0; r < G; r += 2) {
+                    unsigned long long P0 = 0ull, Q0 = 0ull, P1 = 0ull, Q1 = 0ull;
 #pragma unroll
-                        for (int c2 = 0; c2 < G; ++c2) {
-                            const unsigned long long vp = pk2(v[c2].x, v[c2].y);
-                            const ulonglong2 m0 = fold_m[r * G + c2], m1 = fold_m[(r + 1) * G + c2];
-                            P0 = fma2(m0.x, vp, P0);
-                            Q0 = fma2(m0.y, vp, Q0);
-                            P1 = fma2(m1.x, vp, P1);
-                            Q1 = fma2(m1.y, vp, Q1);
-                        }
-                        const float2 p0 = upk2(P0), q0 = upk2(Q0), p1 = upk2(P1), q1 = upk2(Q1);
-                        const float2 o0 = make_float2(p0.x - q0.y, p0.y + q0.x);
-                        const float2 o1 = make_float2(p1.x - q1.y, p1.y + q1.x);
-                        if constexpr (PAIRED) {
-                            *reinterpret_cast<float4*>(g + off(r)) = make_float4(o0.x, o0.y, o1.x, o1.y);
-                        } else {
-                            g[off(r)] = o0;
-                            g[off(r + 1)] = o1;
-                        }
+                    for (int c2 = 0; c2 < G; ++c2) {
+                        const unsigned long long vp = pk2(v[c2].x, v[c2].y);
+                        const ulonglong2 m0 = fold_m[r * G + c2], m1 = fold_m[(r + 1) * G + c2];
+                        P0 = fma2(m0.x, vp, P0);
+                        Q0 = fma2(m0.y, vp, Q0);
+                        P1 = fma2(m1.x, vp, P1);
+                        Q1 = fma2(m1.y, vp, Q1);
                     }
-                    folded = true;
+                    const float2 p0 = upk2(P0), q0 = upk2(Q0), p1 = upk2(P1), q1 = upk2(Q1);
+                    const float2 o0 = make_float2(p0.x - q0.y, p0.y + q0.x);
+                    const float2 o1 = make_float2(p1.x - q1.y, p1.y + q1.x);
+                    if constexpr (PAIRED) {
+                        *reinterpret_cast<float4*>(g + off(r)) = make_float4(o0.x, o0.y, o1.x, o1.y);
+                    } else {
+                        g[off(r)] = o0;
+                        g[off(r + 1)] = o1;
+                    }
                 }
-            }
-            if (!folded) {
+            } else {
                 apply_stages(v);
                 if (p.red_kind == RED_FORMS)
                     reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - 8 * p.red_R, p.red_R, acc);
@@ -2409,36 +2402,36 @@ cudaError_t init_kernels() {
     return e;
 }
 
-template <class R, int WP, int PAIRED> const void* reg_fn() { return (const void*)k_pass_reg<R, WP, PAIRED>; }
+template <class R, int WP, int PAIRED, int FOLD> const void* reg_fn() {
+    return (const void*)k_pass_reg<R, WP, PAIRED, FOLD>;
+}
 
-const void* pass_reg_fn(int prec, int wp, int paired) {
-    if (prec) {
-        switch (wp) {
-        case 1: return reg_fn<double, 1, 0>();
-        case 2: return reg_fn<double, 2, 0>();
-        case 3: return reg_fn<double, 3, 0>();
-        default: return reg_fn<double, 4, 0>();
-        }
-    }
-    if (paired) {
-        switch (wp) {
-        case 1: return reg_fn<float, 1, 1>();
-        case 2: return reg_fn<float, 2, 1>();
-        case 3: return reg_fn<float, 3, 1>();
-        default: return reg_fn<float, 4, 1>();
-        }
-    }
+template <int PAIRED, int FOLD> const void* reg_fn_c64(int wp) {
     switch (wp) {
-    case 1: return reg_fn<float, 1, 0>();
-    case 2: return reg_fn<float, 2, 0>();
-    case 3: return reg_fn<float, 3, 0>();
-    default: return reg_fn<float, 4, 0>();
+    case 1: return reg_fn<float, 1, PAIRED, FOLD>();
+    case 2: return reg_fn<float, 2, PAIRED, FOLD>();
+    case 3: return reg_fn<float, 3, PAIRED, FOLD>();
+    default: return reg_fn<float, 4, PAIRED, FOLD>();
     }
 }
 
-int pass_reg_blocks_per_sm(int prec, int wp, int paired, size_t smem) {
+// folded passes exist for complex64 only
+const void* pass_reg_fn(int prec, int wp, int paired, int fold) {
+    if (prec) {
+        switch (wp) {
+        case 1: return reg_fn<double, 1, 0, 0>();
+        case 2: return reg_fn<double, 2, 0, 0>();
+        case 3: return reg_fn<double, 3, 0, 0>();
+        default: return reg_fn<double, 4, 0, 0>();
+        }
+    }
+    if (paired) return fold ? reg_fn_c64<1, 1>(wp) : reg_fn_c64<1, 0>(wp);
+    return fold ? reg_fn_c64<0, 1>(wp) : reg_fn_c64<0, 0>(wp);
+}
+
+int pass_reg_blocks_per_sm(int prec, int wp, int paired, int fold, size_t smem) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pass_reg_fn(prec, wp, paired), pass_reg_threads(prec),
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pass_reg_fn(prec, wp, paired, fold), pass_reg_threads(prec),
                                                       smem) != cudaSuccess) {
         cudaGetLastError();
         n = 1;
@@ -2458,7 +2451,7 @@ cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int thre
     if (p.reg_wp > 0) {
         const int threads = pass_reg_threads(prec);
         const size_t smem = pass_reg_smem_bytes(prec, p, threads);
-        const void* f = pass_reg_fn(prec, p.reg_wp, p.reg_paired && !prec);
+        const void* f = pass_reg_fn(prec, p.reg_wp, p.reg_paired && !prec, p.fold && !prec);
         void* args[] = {(void*)&d, (void*)&p};
         return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
     }

@@ -241,11 +241,11 @@ int pass_grid(sv_batch b, const PassDesc& p) {
     if (p.reg_wp > 0) {
         const int prec = b->prec == SV_C128;
         const size_t smem = pass_reg_smem_bytes(prec, p, pass_reg_threads(prec));
-        const int key = (p.reg_wp * 2 + prec) * 2 + p.reg_paired;
+        const int key = ((p.reg_wp * 2 + prec) * 2 + p.reg_paired) * 2 + p.fold;
         auto it = b->reg_occ.find(key * 4096 + (int)(smem / 64));
         int per_sm;
         if (it == b->reg_occ.end()) {
-            per_sm = pass_reg_blocks_per_sm(prec, p.reg_wp, p.reg_paired, smem);
+            per_sm = pass_reg_blocks_per_sm(prec, p.reg_wp, p.reg_paired, p.fold, smem);
             b->reg_occ[key * 4096 + (int)(smem / 64)] = per_sm;
         } else {
             per_sm = it->second;
