@@ -1185,7 +1185,7 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
     int* w_packed = w_sel + MAX_STAGES;
     double* w_scale = reinterpret_cast<double*>(w_sel + 2 * MAX_STAGES);
     ulonglong2* matx = matx_all + (size_t)warp * mat_stride;
-    ulonglong2* fold_m = matx_all + (size_t)nwarps * mat_stride + (size_t)warp * G * G;
+    float4* fold_m = reinterpret_cast<float4*>(matx_all + (size_t)nwarps * mat_stride) + (size_t)warp * (G / 2) * G;
     uint64_t skipmask = 0;
     // every stage of the pass, in op order, on one group of G amplitudes
     auto apply_stages = [&](T (&v)[G]) {
@@ -1405,11 +1405,12 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                     col[e].y = 0;
                 }
                 apply_stages(col);
+                // rows r and r + 1 of column c side by side: one 128-bit
+                // load per column serves two output rows
                 if (lane < G)
 #pragma unroll
-                    for (int r = 0; r < G; ++r)
-                        fold_m[r * G + lane] = make_ulonglong2(pk2((float)col[r].x, (float)col[r].x),
-                                                               pk2((float)col[r].y, (float)col[r].y));
+                    for (int r = 0; r < G; r += 2)
+                        fold_m[(r / 2) * G + lane] = make_float4(col[r].x, col[r].y, col[r + 1].x, col[r + 1].y);
                 __syncwarp();
             }
             cur_b = b;
@@ -1462,25 +1463,22 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                 for (int e = 0; e < G; ++e) v[e] = g[off(e)];
             }
             if constexpr (FOLD && sizeof(T) == 8) {
-                // the pass's stages folded into one G x G matrix (row r,
-                // column c at fold_m[r * G + c] as ((re, re), (im, im)));
-                // a folded pass has no reduction, so each pair of output
-                // rows is stored as soon as it is formed
+                // the pass's stages folded into one G x G matrix (rows r and
+                // r + 1 of column c at fold_m[(r / 2) * G + c]); a folded pass
+                // has no reduction, so each pair of output rows is stored as
+                // soon as it is formed
 #pragma unroll 1
                 for (int r = 0; r < G; r += 2) {
-                    unsigned long long P0 = 0ull, Q0 = 0ull, P1 = 0ull, Q1 = 0ull;
+                    float2 o0 = make_float2(0.f, 0.f), o1 = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int c2 = 0; c2 < G; ++c2) {
-                        const unsigned long long vp = pk2(v[c2].x, v[c2].y);
-                        const ulonglong2 m0 = fold_m[r * G + c2], m1 = fold_m[(r + 1) * G + c2];
-                        P0 = fma2(m0.x, vp, P0);
-                        Q0 = fma2(m0.y, vp, Q0);
-                        P1 = fma2(m1.x, vp, P1);
-                        Q1 = fma2(m1.y, vp, Q1);
+                        const float4 m = fold_m[(r / 2) * G + c2];
+                        const float2 a = v[c2];
+                        o0.x = fmaf(m.x, a.x, fmaf(-m.y, a.y, o0.x));
+                        o0.y = fmaf(m.x, a.y, fmaf(m.y, a.x, o0.y));
+                        o1.x = fmaf(m.z, a.x, fmaf(-m.w, a.y, o1.x));
+                        o1.y = fmaf(m.z, a.y, fmaf(m.w, a.x, o1.y));
                     }
-                    const float2 p0 = upk2(P0), q0 = upk2(Q0), p1 = upk2(P1), q1 = upk2(Q1);
-                    const float2 o0 = make_float2(p0.x - q0.y, p0.y + q0.x);
-                    const float2 o1 = make_float2(p1.x - q1.y, p1.y + q1.x);
                     if constexpr (PAIRED) {
                         *reinterpret_cast<float4*>(g + off(r)) = make_float4(o0.x, o0.y, o1.x, o1.y);
                     } else {
@@ -2444,7 +2442,7 @@ size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads) {
     const size_t nw = threads / 32;
     const size_t m = (size_t)((p.mat_elems + 1) & ~1);
     const size_t g = (size_t)1 << p.reg_wp;
-    return nw * (m * c + 4 * MAX_STAGES * 4) + (prec ? 0 : nw * m * 16) + (p.fold && !prec ? nw * g * g * 16 : 0);
+    return nw * (m * c + 4 * MAX_STAGES * 4) + (prec ? 0 : nw * m * 16) + (p.fold && !prec ? nw * g * g * 8 : 0);
 }
 
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s) {

@@ -394,8 +394,10 @@ struct RedSpec {
 
 // Rough per-group instruction counts of the register kernel (a group is
 // G = 2^wp amplitudes of one lane): every stage costs a dispatch plus its
-// arithmetic; a folded pass costs G x G complex products (two packed FMAs
-// and one shared-memory load each) and one composition per branch.
+// arithmetic; a folded pass costs G x G complex products (four FMAs each,
+// one shared-memory load per two) and one composition per branch.  The
+// folded product is bound by delivering its matrix from shared memory, so
+// it has to save half the estimated work to pay.
 int stage_group_cost(sv_batch b, const PendStage& ps, int G) {
     int c = 40;  // stage dispatch: descriptor loads, skip test, switch
     if (ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) {
@@ -422,7 +424,7 @@ bool fold_pays(sv_batch b, const std::vector<const PendStage*>& ss, int wp) {
     const int G = 1 << wp;
     int64_t c = 0;
     for (const PendStage* ps : ss) c += stage_group_cost(b, *ps, G);
-    return c * 4 > 5 * (int64_t)(3 * G * G + 60);
+    return c * 2 > 3 * (int64_t)(3 * G * G + 60);
 }
 
 // can a pass run in registers (k_pass_reg)?  its qubits plus qubit 0 <= 4,
