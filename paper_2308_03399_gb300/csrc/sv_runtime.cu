@@ -236,6 +236,14 @@ int pclass(LType t) {
     }
 }
 
+// threads of a tile-path CTA: the batch's setting, at least one per form of
+// the pass's reduction (each thread writes one form's partial)
+int tile_threads(sv_batch b, const PassDesc& p) {
+    int t = b->threads;
+    while (t < 256 && t < p.red_R) t *= 2;
+    return t;
+}
+
 int pass_grid(sv_batch b, const PassDesc& p) {
     if (b->grid_pass > 0) return b->grid_pass;
     if (p.reg_wp > 0) {
@@ -252,10 +260,11 @@ int pass_grid(sv_batch b, const PassDesc& p) {
         }
         return b->n_sm * per_sm;
     }
-    // k_pass is register-bound at two CTAs of 256 threads per SM; shared
-    // memory (tile + matrices + accumulators) may allow fewer
-    const size_t smem = pass_smem_bytes(b->prec == SV_C128, p, b->threads) + 2048;
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(b->threads == 128 ? 4 : 2, (227 * 1024) / smem));
+    // k_pass is register-bound at 512 threads per SM (two CTAs of 256);
+    // shared memory (tile ring + matrices + accumulators) may allow fewer
+    const int threads = tile_threads(b, p);
+    const size_t smem = pass_smem_bytes(b->prec == SV_C128, p, threads) + 2048;
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(512 / threads, (227 * 1024) / smem));
     return b->n_sm * per_sm;
 }
 
@@ -264,7 +273,7 @@ cudaError_t exec_one(sv_batch b, const Launch& L) {
     switch (L.type) {
     case L_INIT: return launch_init(b->dev, prec, L.a0, b->n_sm * 4, b->stream);
     case L_RESET: return launch_reset(b->dev, L.a0, L.a1, L.a2, b->n_sm * 2, b->stream);
-    case L_PASS: return launch_pass(b->dev, prec, L.pass, b->threads, pass_grid(b, L.pass), b->stream);
+    case L_PASS: return launch_pass(b->dev, prec, L.pass, tile_threads(b, L.pass), pass_grid(b, L.pass), b->stream);
     case L_DECIDE: return launch_decide(b->dev, L.dec, b->n_sm, b->stream, b->side, b->ev_fork, b->ev_join);
     case L_ALLOC: return cudaSuccess;
     case L_COPY: return launch_copy(b->dev, prec, b->n_sm * 4, b->stream);
@@ -1829,7 +1838,7 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
         return SV_OK;
     case SV_OPT_MAX_STAGES: b->max_stages = v ? (int)std::min<int64_t>(std::max<int64_t>(v, 1), MAX_STAGES) : MAX_STAGES; return SV_OK;
     case SV_OPT_THREADS:
-        if (v && v != 128 && v != 256) return fail(SV_EINVAL, "threads must be 128 or 256");
+        if (v && v != 32 && v != 64 && v != 128 && v != 256) return fail(SV_EINVAL, "threads must be 32, 64, 128 or 256");
         b->threads = v ? (int)v : 256;
         return SV_OK;
     case SV_OPT_GRID: b->grid_pass = (int)std::max<int64_t>(0, v); return SV_OK;

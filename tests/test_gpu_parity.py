@@ -550,3 +550,14 @@ def test_folded_passes_match_oracle(case, mode):
     compare_shots(c, 6, b, range(0, 150, 10), sv.SV_C64, check_amps=False)
     for s in amps:
         np.testing.assert_allclose(a["amps"][s], b["amps"][s], atol=2e-6)
+
+
+@pytest.mark.parametrize("threads", [32, 64])
+@pytest.mark.parametrize("name", list(SMALL))
+def test_small_tile_ctas_match_oracle(name, threads):
+    # one- and two-warp CTAs on whole-state tiles: block barriers are warp
+    # barriers, reductions with as many forms as threads or more move to a
+    # wider CTA
+    c = SMALL[name]()
+    gpu = run_gpu(c, 12, 200, sv.SV_BATCH, sv.SV_C64, opts={sv.SV_OPT_THREADS: threads}, want_amps=[0, 199])
+    compare_shots(c, 12, gpu, range(200), sv.SV_C64)
