@@ -238,9 +238,10 @@ def leg(torch, flush_buf, name, steps, warmup, mode="branch", prec="c64", graph=
 
 
 def cfg1_smem(torch, flush_buf):
-    """Config 1 batched in complex64: every state is one shared-memory tile
-    (2^10 amplitudes), so the passes are bound by shared memory or the FP32
-    pipe, not HBM.  Algorithmic work per gate and state (every gate acts on
+    """Config 1 batched in complex64: 1000 states of 8 KB sit in L2 and each
+    pass holds its part of a state on chip (registers, or a shared-memory
+    tile), so the passes are bound by on-chip bandwidth or the FP32 pipe,
+    not HBM.  Algorithmic work per gate and state (every gate acts on
     every shot in batch mode): a k-qubit dense stage reads and writes each
     of the 2^n amplitudes once in shared memory (2 x 8 B) and does 2^k
     complex multiply-adds per amplitude (8 x 2^k flop).  Both are divided by
@@ -257,7 +258,7 @@ def cfg1_smem(torch, flush_buf):
         smem_frac = smem_b / t / 1e9 / pk["smem_gbs"]
         alu_frac = flop / t / 1e12 / pk["fp32_tflops"]
         res["roofline"] = {
-            "bound": "smem" if smem_frac >= alu_frac else "alu", "kernel": "k_pass (whole-state tiles)",
+            "bound": "smem" if smem_frac >= alu_frac else "alu", "kernel": "pass kernels (library defaults)",
             "smem": {"achieved": smem_b / t / 1e9, "peak": pk["smem_gbs"], "unit": "GB/s", "frac": smem_frac,
                      "algorithmic_bytes_per_step": smem_b},
             "fp32": {"achieved": flop / t / 1e12, "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": alu_frac,

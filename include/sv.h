@@ -106,12 +106,13 @@ typedef struct {
 typedef enum {
     SV_OPT_LOG = 0,         /* 1: record per-shot outcomes, thresholds and fork events */
     SV_OPT_TILE_BITS = 1,   /* amplitudes per CTA tile = 2^value (0 = default)          */
-    SV_OPT_MAX_ACTIVE = 2,  /* most distinct qubits fused into one pass (0 = default:
-                               all when the state fits one tile, else 4; a later
-                               SV_OPT_TILE_BITS recomputes the default)             */
+    SV_OPT_MAX_ACTIVE = 2,  /* most distinct qubits fused into one pass (0 = default 4:
+                               register passes; wider passes use shared-memory
+                               tiles)                                               */
     SV_OPT_MAX_STAGES = 3,  /* most ops fused into one pass (0 = default)               */
     SV_OPT_THREADS = 4,     /* threads per CTA of the tile pass kernel: 32, 64, 128 or
-                               256 (0 = default 256)                                  */
+                               256 (0 = default: 128 when a tile holds the whole
+                               state, else 256)                                     */
     SV_OPT_GRID = 5,        /* CTAs of the persistent kernels (0 = default)             */
     SV_OPT_PROFILE = 6,     /* 1: time every launch class with CUDA events              */
     SV_OPT_SLOT_LIMIT = 7,  /* cap on state slots (0 = as many as fit); forces waiting  */

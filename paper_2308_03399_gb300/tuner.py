@@ -30,9 +30,9 @@ DEFAULT = dict(mode="branch", max_active=0, path=0, joint=1, tile=0)  # the libr
 
 
 def candidates():
-    """Batch or branch mode x fusion width (0: the library's default, all
-    qubits when the state is one tile, else 4) x pass path x joint Kraus
-    decisions x tile size (0: 2^11 amplitudes for complex64; 10: 2^10)."""
+    """Batch or branch mode x fusion width (0: the library's default, 4
+    qubits in registers) x pass path x joint Kraus decisions x tile size
+    (0: 2^11 amplitudes for complex64; 10: 2^10)."""
     out = []
     for mode, fuse, path, joint, tile in itertools.product(("batch", "branch"), (0, 3, 5, 8), (0, 1), (1, 0),
                                                            (0, 10)):
@@ -78,7 +78,7 @@ def encode(cfg, n_qubits):
     tile size in effect for an n-qubit complex64 state, pass path, joint
     decisions."""
     tb = min(n_qubits, cfg.get("tile", 0) or 11)
-    width = cfg["max_active"] or (n_qubits if n_qubits <= tb else 4)
+    width = cfg["max_active"] or 4
     return np.array([1.0 if cfg["mode"] == "branch" else 0.0, width / 8.0, float(cfg["path"]),
                      float(cfg["joint"]), tb / 11.0], np.float32)
 
