@@ -42,6 +42,11 @@ def workload(name):
         return W.config3(), 10_000, 3
     if name == "cfg5":
         return W.config5(), 2000, 5
+    # the paper's QFT with 1% depolarizing noise: qft<n> (Pauli), qftk<n> (Kraus)
+    for pre, kraus in (("qftk", True), ("qft", False)):
+        if name.startswith(pre) and name[len(pre):].isdigit():
+            n = int(name[len(pre):])
+            return W.qft(n, 0.01, seed=n, kraus=kraus), 4000, n
     raise SystemExit(f"unknown workload {name}")
 
 

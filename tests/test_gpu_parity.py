@@ -10,7 +10,8 @@ import pytest
 from oracle import oracle as O
 from paper_2308_03399_gb300 import sv
 from paper_2308_03399_gb300 import workloads as W
-from tests.parity import canonical_tree_records, check_branch_tree, compare_shots, gpu_tree_records, run_gpu
+from tests.parity import (canonical_tree_records, check_branch_tree, compare_shots, gpu_tree_records, oracle_refs,
+                          run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -295,21 +296,40 @@ def test_config1_all_shots_complex128():
 
 
 def test_config2_sampled_shots_and_tree():
+    # the full 10^4-shot run: 200 seeded shots draw by draw against the oracle
+    # (run side by side), two of them with their final states
     c = W.config2()
     n_shots = 10_000
     gpu = run_gpu(c, 2, n_shots, sv.SV_BRANCH, sv.SV_C64, want_amps=[0, 4321])
     rng = np.random.default_rng(0)
-    shots = sorted(set(rng.choice(n_shots, 12, replace=False).tolist()) | {0, 4321})
-    compare_shots(c, 2, gpu, shots, sv.SV_C64)
+    shots = sorted(set(rng.choice(n_shots, 198, replace=False).tolist()) | {0, 4321})
+    refs = oracle_refs(c, 2, shots, state_shots=(0, 4321))
+    compare_shots(c, 2, gpu, shots, sv.SV_C64, refs=refs)
     rops = [op for op in c.random_ops() if c.ops[op].kind != W.FINAL]
     assert gpu_tree_records(gpu["forks"]) == canonical_tree_records(gpu["sel"], rops, n_shots)
 
 
+def test_config2_circuit_tree_matches_oracle():
+    # the same circuit at 1000 shots: every shot against the oracle, and the
+    # branch tree with shot sets against the oracle's canonical tree
+    c = W.config2()
+    n_shots = 1000
+    gpu = run_gpu(c, 2, n_shots, sv.SV_BRANCH, sv.SV_C64)
+    refs = oracle_refs(c, 2, range(n_shots))
+    outs = {}
+    compare_shots(c, 2, gpu, range(n_shots), sv.SV_C64, check_amps=False, outcomes_out=outs, refs=refs)
+    rops = [op for op in c.random_ops() if c.ops[op].kind != W.FINAL]
+    check_branch_tree(gpu["tree"], np.stack([outs[s] for s in range(n_shots)]), rops)
+
+
 def test_config3_sampled_shots():
+    # 20 qubits, 30 rounds of mid-circuit measurements: 16 shots side by side
     c = W.config3()
     n_shots = 256
     gpu = run_gpu(c, 3, n_shots, sv.SV_BRANCH, sv.SV_C64, want_amps=[0])
-    compare_shots(c, 3, gpu, [0, 101, 255], sv.SV_C64)
+    shots = list(range(0, 256, 17))
+    refs = oracle_refs(c, 3, shots, state_shots=(0,))
+    compare_shots(c, 3, gpu, shots, sv.SV_C64, refs=refs)
 
 
 def test_run_circuits_one_graph_matches_separate_runs():
