@@ -111,8 +111,7 @@ typedef enum {
                                tiles)                                               */
     SV_OPT_MAX_STAGES = 3,  /* most ops fused into one pass (0 = default)               */
     SV_OPT_THREADS = 4,     /* threads per CTA of the tile pass kernel: 32, 64, 128 or
-                               256 (0 = default: 128 when a tile holds the whole
-                               state, else 256)                                     */
+                               256 (0 = default 128)                                */
     SV_OPT_GRID = 5,        /* CTAs of the persistent kernels (0 = default)             */
     SV_OPT_PROFILE = 6,     /* 1: time every launch class with CUDA events              */
     SV_OPT_SLOT_LIMIT = 7,  /* cap on state slots (0 = as many as fit); forces waiting  */

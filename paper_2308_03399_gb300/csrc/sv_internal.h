@@ -199,7 +199,8 @@ cudaError_t launch_copy(const DevBatch& d, int prec, int grid, cudaStream_t s);
 cudaError_t launch_final(const DevBatch& d, int prec, const FinalDesc& f, int grid, cudaStream_t s);
 size_t pass_smem_bytes(int prec, const PassDesc& p, int threads);
 size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads);
-int pass_reg_blocks_per_sm(int prec, int wp, int paired, int fold, size_t smem);
+int pass_reg_blocks_per_sm(int prec, int wp, int paired, int var, size_t smem);
+int pass_reg_variant(int prec, const PassDesc& p);
 int pass_reg_threads(int prec);  // CTA size of the register path
 cudaError_t init_kernels();
 // density-matrix method (sv_dm.cu): diagonal, running sums, one key per shot

@@ -1106,6 +1106,7 @@ __device__ __forceinline__ void reg_forms1_dyn(const typename Cplx<R>::T* v, int
 }
 
 constexpr int REG_MAX_RED = 4;
+constexpr int REG_MAX_BINS = 16;  // measurement outcomes a register pass reduces (k <= 4)
 
 // Diagonal forms (sum_r w_f[r] |v_r|^2 over the 2^k amplitudes of the
 // reduced qubits) are linear in the 2^k bins of |v|^2, so a unit only
@@ -1166,9 +1167,14 @@ template <> struct RegCta<double> { static constexpr int threads = 256, min_bloc
 
 int pass_reg_threads(int prec) { return prec ? RegCta<double>::threads : RegCta<float>::threads; }
 
-template <class R, int WP, int PAIRED, int FOLD>
+// register-kernel variants: stage by stage, folded (no reduction), and
+// stage by stage with measurement bins (complex64)
+constexpr int REG_PLAIN = 0, REG_FOLD = 1, REG_BINS = 2;
+
+template <class R, int WP, int PAIRED, int VAR>
 __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
     k_pass_reg(DevBatch d, const __grid_constant__ PassDesc p) {
+    constexpr bool FOLD = VAR == REG_FOLD, BINS = VAR == REG_BINS;
     using T = typename Cplx<R>::T;
     constexpr int G = 1 << WP;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1186,6 +1192,21 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
     double* w_scale = reinterpret_cast<double*>(w_sel + 2 * MAX_STAGES);
     ulonglong2* matx = matx_all + (size_t)warp * mat_stride;
     float4* fold_m = reinterpret_cast<float4*>(matx_all + (size_t)nwarps * mat_stride) + (size_t)warp * (G / 2) * G;
+    // measurement bins (RED_BINS): per warp, bin r of lane l at bins[r * 32 + l]
+    // (float-float pairs for complex64), after the folded matrices (none in
+    // a pass with a reduction) and, for complex64, the expanded matrices
+    using AS = typename AccSlot<R>::T;
+    AS* const bins_all = reinterpret_cast<AS*>(reinterpret_cast<unsigned char*>(matx_all) +
+                                               (sizeof(T) == 8 ? (size_t)nwarps * mat_stride * 16 : 0));
+    AS* bins = bins_all + (size_t)warp * REG_MAX_BINS * 32;
+    // bin of each group element: 4 bits per element
+    uint64_t binmap = 0;
+    if constexpr (BINS)
+        for (int e = 0; e < G; ++e) {
+            uint64_t bi = 0;
+            for (int j = 0; j < p.red_k; ++j) bi |= (uint64_t)((e >> p.red_pos[j]) & 1) << j;
+            binmap |= bi << (4 * e);
+        }
     uint64_t skipmask = 0;
     // every stage of the pass, in op order, on one group of G amplitudes
     auto apply_stages = [&](T (&v)[G]) {
@@ -1418,6 +1439,8 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
         Acc<R> acc[REG_MAX_RED];
 #pragma unroll
         for (int r = 0; r < REG_MAX_RED; ++r) acc[r].zero();
+        if constexpr (BINS)
+            for (int r = 0; r < (1 << p.red_k); ++r) bins[r * 32 + lane] = AS{};
         T* gstate = states + (int64_t)slot * d.dim;
         for (int64_t gi = lane; gi < gpu; gi += 32) {
             // base: the group index with zeros inserted at the group qubits
@@ -1492,6 +1515,16 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                     reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - 8 * p.red_R, p.red_R, acc);
                 else if (p.red_kind == RED_DIAG)
                     reg_diag<R, G>(v, p, acc);
+                if constexpr (BINS) {
+                    // each lane owns its column of the bins: no races
+#pragma unroll
+                    for (int e = 0; e < G; ++e) {
+                        const int bi = (int)((binmap >> (4 * e)) & 15);
+                        const R x = v[e].x * v[e].x + v[e].y * v[e].y;
+                        if constexpr (sizeof(R) == 4) acc_add(&bins[bi * 32 + lane], x);
+                        else bins[bi * 32 + lane] += x;
+                    }
+                }
                 if (p.store) {
                     if constexpr (sizeof(T) == 8 && PAIRED) {
 #pragma unroll
@@ -1523,6 +1556,16 @@ __global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
                 for (int r = 0; r < 4; ++r)
                     if (r < D) part += diag_weight(W, p.red_R, p.red_k, lane, r) * bin[r];
                 d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED + lane] = part;
+            }
+        } else if (BINS) {
+            // every outcome's bin: a fixed float64 shuffle tree over the lanes
+            for (int r = 0; r < (1 << p.red_k); ++r) {
+                const AS a = bins[r * 32 + lane];
+                double x;
+                if constexpr (sizeof(R) == 4) x = (double)a.x + (double)a.y;
+                else x = a;
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0) d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED + r] = x;
             }
         } else if (red) {
 #pragma unroll
@@ -2400,21 +2443,27 @@ cudaError_t init_kernels() {
     return e;
 }
 
-template <class R, int WP, int PAIRED, int FOLD> const void* reg_fn() {
-    return (const void*)k_pass_reg<R, WP, PAIRED, FOLD>;
+template <class R, int WP, int PAIRED, int VAR> const void* reg_fn() {
+    return (const void*)k_pass_reg<R, WP, PAIRED, VAR>;
 }
 
-template <int PAIRED, int FOLD> const void* reg_fn_c64(int wp) {
+template <int PAIRED, int VAR> const void* reg_fn_c64(int wp) {
+    if constexpr (VAR == REG_BINS) return reg_fn<float, 4, PAIRED, VAR>();  // bins: 4-qubit groups only
     switch (wp) {
-    case 1: return reg_fn<float, 1, PAIRED, FOLD>();
-    case 2: return reg_fn<float, 2, PAIRED, FOLD>();
-    case 3: return reg_fn<float, 3, PAIRED, FOLD>();
-    default: return reg_fn<float, 4, PAIRED, FOLD>();
+    case 1: return reg_fn<float, 1, PAIRED, VAR>();
+    case 2: return reg_fn<float, 2, PAIRED, VAR>();
+    case 3: return reg_fn<float, 3, PAIRED, VAR>();
+    default: return reg_fn<float, 4, PAIRED, VAR>();
     }
 }
 
-// folded passes exist for complex64 only
-const void* pass_reg_fn(int prec, int wp, int paired, int fold) {
+int pass_reg_variant(int prec, const PassDesc& p) {
+    if (prec) return REG_PLAIN;
+    return p.fold ? REG_FOLD : (p.red_kind == RED_BINS ? REG_BINS : REG_PLAIN);
+}
+
+// folded and measurement-bin passes exist for complex64 only
+const void* pass_reg_fn(int prec, int wp, int paired, int var) {
     if (prec) {
         switch (wp) {
         case 1: return reg_fn<double, 1, 0, 0>();
@@ -2423,13 +2472,16 @@ const void* pass_reg_fn(int prec, int wp, int paired, int fold) {
         default: return reg_fn<double, 4, 0, 0>();
         }
     }
-    if (paired) return fold ? reg_fn_c64<1, 1>(wp) : reg_fn_c64<1, 0>(wp);
-    return fold ? reg_fn_c64<0, 1>(wp) : reg_fn_c64<0, 0>(wp);
+    if (paired)
+        return var == REG_FOLD ? reg_fn_c64<1, REG_FOLD>(wp)
+                               : (var == REG_BINS ? reg_fn_c64<1, REG_BINS>(wp) : reg_fn_c64<1, REG_PLAIN>(wp));
+    return var == REG_FOLD ? reg_fn_c64<0, REG_FOLD>(wp)
+                           : (var == REG_BINS ? reg_fn_c64<0, REG_BINS>(wp) : reg_fn_c64<0, REG_PLAIN>(wp));
 }
 
-int pass_reg_blocks_per_sm(int prec, int wp, int paired, int fold, size_t smem) {
+int pass_reg_blocks_per_sm(int prec, int wp, int paired, int var, size_t smem) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pass_reg_fn(prec, wp, paired, fold), pass_reg_threads(prec),
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pass_reg_fn(prec, wp, paired, var), pass_reg_threads(prec),
                                                       smem) != cudaSuccess) {
         cudaGetLastError();
         n = 1;
@@ -2442,14 +2494,15 @@ size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads) {
     const size_t nw = threads / 32;
     const size_t m = (size_t)((p.mat_elems + 1) & ~1);
     const size_t g = (size_t)1 << p.reg_wp;
-    return nw * (m * c + 4 * MAX_STAGES * 4) + (prec ? 0 : nw * m * 16) + (p.fold && !prec ? nw * g * g * 8 : 0);
+    return nw * (m * c + 4 * MAX_STAGES * 4) + (prec ? 0 : nw * m * 16) + (p.fold && !prec ? nw * g * g * 8 : 0) +
+           (p.red_kind == RED_BINS ? nw * REG_MAX_BINS * 32 * 8 : 0);
 }
 
 cudaError_t launch_pass(const DevBatch& d, int prec, const PassDesc& p, int threads, int grid, cudaStream_t s) {
     if (p.reg_wp > 0) {
         const int threads = pass_reg_threads(prec);
         const size_t smem = pass_reg_smem_bytes(prec, p, threads);
-        const void* f = pass_reg_fn(prec, p.reg_wp, p.reg_paired && !prec, p.fold && !prec);
+        const void* f = pass_reg_fn(prec, p.reg_wp, p.reg_paired && !prec, pass_reg_variant(prec, p));
         void* args[] = {(void*)&d, (void*)&p};
         return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
     }

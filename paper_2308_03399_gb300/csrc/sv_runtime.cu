@@ -237,13 +237,13 @@ int pclass(LType t) {
     }
 }
 
-// threads of a tile-path CTA: the batch's setting (default: 128 when a
-// tile holds the whole state, where a CTA's stages wait on each other's
-// barriers and more, smaller CTAs keep more states in flight; else 256),
-// at least one per form of the pass's reduction (each thread writes one
-// form's partial)
+// threads of a tile-path CTA: the batch's setting (default 128: a CTA's
+// stages wait on each other's barriers, and more, smaller CTAs keep more
+// tiles in flight; measured faster than 256 on whole-state and on 20-qubit
+// tiles), at least one per form of the pass's reduction (each thread
+// writes one form's partial)
 int tile_threads(sv_batch b, const PassDesc& p) {
-    int t = b->threads_set ? b->threads : (p.tb >= b->n ? 128 : 256);
+    int t = b->threads_set ? b->threads : 128;
     while (t < 256 && t < p.red_R) t *= 2;
     return t;
 }
@@ -253,11 +253,12 @@ int pass_grid(sv_batch b, const PassDesc& p) {
     if (p.reg_wp > 0) {
         const int prec = b->prec == SV_C128;
         const size_t smem = pass_reg_smem_bytes(prec, p, pass_reg_threads(prec));
-        const int key = ((p.reg_wp * 2 + prec) * 2 + p.reg_paired) * 2 + p.fold;
+        const int var = pass_reg_variant(prec, p);
+        const int key = ((p.reg_wp * 2 + prec) * 2 + p.reg_paired) * 3 + var;
         auto it = b->reg_occ.find(key * 4096 + (int)(smem / 64));
         int per_sm;
         if (it == b->reg_occ.end()) {
-            per_sm = pass_reg_blocks_per_sm(prec, p.reg_wp, p.reg_paired, p.fold, smem);
+            per_sm = pass_reg_blocks_per_sm(prec, p.reg_wp, p.reg_paired, var, smem);
             b->reg_occ[key * 4096 + (int)(smem / 64)] = per_sm;
         } else {
             per_sm = it->second;
@@ -445,15 +446,18 @@ bool fold_pays(sv_batch b, const std::vector<const PendStage*>& ss, int wp) {
     return c * 2 > 3 * (int64_t)(3 * G * G + 60);
 }
 
-// can a pass run in registers (k_pass_reg)?  its qubits plus qubit 0 <= 4,
-// dense stages <= 2 qubits, and no reduction or <= 4 one-qubit forms
+// can a pass run in registers (k_pass_reg)?  at most 4 qubits, dense stages
+// of at most 2 qubits, and no reduction, diagonal forms, <= 4 one-qubit
+// forms, or the outcome bins of a measurement of at most 4 qubits
 int reg_width(sv_batch b, const RedSpec& red, uint64_t act, const std::vector<const PendStage*>& ss) {
     if (b->pass_path == 1) return 0;
     const int wp = __builtin_popcountll(act);
     if (wp > 4 || wp < 1) return 0;
     for (const PendStage* ps : ss)
         if ((ps->kind == ST_DENSE || ps->kind == ST_DENSE_BR) && ps->k > 2) return 0;
-    if (red.kind == RED_BINS) return 0;
+    // measurement bins: complex64 groups of exactly 4 qubits (the kernel
+    // variant exists for that shape only)
+    if (red.kind == RED_BINS && (wp != 4 || b->prec == SV_C128)) return 0;
     // diagonal forms reduce to 2^k bins (any number of forms); general
     // forms take one accumulator each (at most 4, one qubit)
     if (red.kind == RED_FORMS && red.diag_off < 0 && (red.R > 4 || red.k != 1)) return 0;
@@ -462,6 +466,7 @@ int reg_width(sv_batch b, const RedSpec& red, uint64_t act, const std::vector<co
     PassDesc probe;
     memset(&probe, 0, sizeof(probe));
     probe.reg_wp = wp;
+    probe.red_kind = red.kind;
     for (const PendStage* ps : ss)
         probe.mat_elems += (ps->kind == ST_DENSE || ps->kind == ST_DENSE_BR) ? 1 << (2 * ps->k)
                                                                             : (ps->kind == ST_PROJ_BR ? 1 : 0);
