@@ -123,8 +123,12 @@ def pass_traffic(args, alg_bytes_per_launch):
     if not os.path.exists(path) or args.shots:
         return None
     rec = dict(ln.split(None, 1) for ln in open(path).read().strip().splitlines())
-    src = os.path.join(ROOT, "paper_2308_03399_gb300", "csrc", "sv_kernels.cu")
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    # the pass kernels' sources: the kernel file and the headers holding the
+    # register kernel and the shared device helpers, hashed in this order
+    h = hashlib.sha1()
+    for f in ("sv_kernels.cu", "sv_pass_reg.cuh", "sv_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2308_03399_gb300", "csrc", f), "rb").read())
+    sha = h.hexdigest()
     if rec.get("source_sha1") != sha or rec.get("workload") != f"{args.workload}:{args.mode}:{args.prec}":
         return None
     ratio = float(rec["dram_bytes_per_step"]) / float(rec["algorithmic_bytes_per_step"])

@@ -201,6 +201,11 @@ size_t pass_smem_bytes(int prec, const PassDesc& p, int threads);
 size_t pass_reg_smem_bytes(int prec, const PassDesc& p, int threads);
 int pass_reg_blocks_per_sm(int prec, int wp, int paired, int var, size_t smem);
 int pass_reg_variant(int prec, const PassDesc& p);
+// register pass kernel instantiations (one translation unit per group)
+const void* reg_kernel_plain_c64(int wp, int paired);
+const void* reg_kernel_fold_c64(int wp, int paired);
+const void* reg_kernel_bins_c64(int paired);
+const void* reg_kernel_c128(int wp);
 int pass_reg_threads(int prec);  // CTA size of the register path
 cudaError_t init_kernels();
 // density-matrix method (sv_dm.cu): diagonal, running sums, one key per shot

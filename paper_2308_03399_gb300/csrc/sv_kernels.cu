@@ -34,121 +34,10 @@
 
 #include <cstdint>
 
-#include "sv_internal.h"
-#include "sv_sample.cuh"
+#include "sv_common.cuh"
+#include "sv_pass_reg.cuh"
 
 namespace sv {
-
-constexpr int PASS_NBUF_H = 4;  // ring buffers of k_pass (PASS_NBUF below)
-
-template <class R> struct Cplx;
-template <> struct Cplx<float> { using T = float2; };
-template <> struct Cplx<double> { using T = double2; };
-
-template <class T> __device__ __forceinline__ T cmul(T a, T b) {
-    T r;
-    r.x = a.x * b.x - a.y * b.y;
-    r.y = a.x * b.y + a.y * b.x;
-    return r;
-}
-template <class T> __device__ __forceinline__ void cfma(T& acc, T a, T b) {
-    acc.x += a.x * b.x - a.y * b.y;
-    acc.y += a.x * b.y + a.y * b.x;
-}
-
-// Packed float32x2 arithmetic (Blackwell fma.rn.f32x2): a complex
-// multiply-accumulate acc += m v is two packed FMAs,
-// acc += (m.re, m.re) * (v.re, v.im) and acc += (-m.im, m.im) * (v.im, v.re).
-__device__ __forceinline__ unsigned long long pk2(float a, float b) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float2 upk2(unsigned long long r) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-    return make_float2(a, b);
-}
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-// Accumulators.  complex128 states sum in float64.  complex64 states sum in
-// float-float (an unevaluated pair hi + lo updated with Knuth's TwoSum), which
-// carries about 48 bits of precision using only float32 arithmetic; the
-// squares of float32 amplitudes are formed in float32 and summed this way.
-template <class R> struct Acc;
-template <> struct Acc<double> {
-    double s;
-    __device__ __forceinline__ void zero() { s = 0.0; }
-    __device__ __forceinline__ void add(double x) { s += x; }
-    __device__ __forceinline__ double get() const { return s; }
-};
-template <> struct Acc<float> {
-    float hi, lo;
-    __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
-    __device__ __forceinline__ void add(float x) {
-        float s = __fadd_rn(hi, x);
-        float bp = __fsub_rn(s, hi);
-        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
-        hi = s;
-        lo = __fadd_rn(lo, e);
-    }
-    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
-};
-
-// Philox4x32-10 draws keyed by (seed; shot, op): svs::philox_k53 /
-// svs::philox_uniform (sv_sample.cuh), shared with sv_noalloc.cu
-using svs::philox_k53;
-using svs::philox_uniform;
-
-// Selection in the integer domain: for u = k * 2^-53, u < c exactly when
-// k < ceil(c * 2^53) (the scaling by 2^53 is exact), so a branch turns its
-// cumulative table into integer thresholds once and each shot compares
-// integers.  Past the last threshold (a table summing to just under 1) the
-// choice is the last term with nonzero probability.
-__device__ __forceinline__ uint64_t cum_threshold(double c) {
-    return c > 0.0 ? __double2ull_ru(c * 0x1.0p53) : 0ull;
-}
-__device__ __forceinline__ int select_k(uint64_t k, const uint64_t* thr, const double* cum, int R) {
-    for (int t = 0; t < R; ++t)
-        if (k < thr[t]) return t;
-    for (int t = R - 1; t >= 0; --t) {
-        const double prev = t ? cum[t - 1] : 0.0;
-        if (cum[t] > prev) return t;
-    }
-    return R - 1;
-}
-
-__device__ __forceinline__ void set_err(const DevBatch& d, int code, int info) {
-    if (atomicCAS(&d.ctl[CTL_ERR], 0, code) == 0) d.ctl[CTL_ERR_INFO] = info;
-}
-
-// insert a zero bit at each of the K ascending positions sp[]
-template <int K> __device__ __forceinline__ int insert_zeros(int g, const int* sp) {
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const int p = sp[j];
-        g = ((g >> p) << (p + 1)) | (g & ((1 << p) - 1));
-    }
-    return g;
-}
-
-template <int K> __device__ __forceinline__ void sorted_pos(const int32_t* pos, int* sp) {
-#pragma unroll
-    for (int j = 0; j < K; ++j) sp[j] = pos[j];
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-#pragma unroll
-        for (int j = 0; j + 1 < K - i; ++j)
-            if (sp[j] > sp[j + 1]) {
-                const int t = sp[j];
-                sp[j] = sp[j + 1];
-                sp[j + 1] = t;
-            }
-}
 
 // ---------------------------------------------------------------------------
 // stage application on a shared-memory tile of 2^tb amplitudes.  Each thread
@@ -170,38 +59,6 @@ template <int K> struct GroupIdx {
         }
     }
 };
-
-// the monomial structure of a 4x4 matrix m (row-major), or 0 when it is not
-// monomial; phases go to ph[0..3]
-template <class T>
-__device__ __forceinline__ int mono_info(const T* m, T* ph) {
-    int pi[4];
-    for (int q = 0; q < 4; ++q) {
-        pi[q] = -1;
-        for (int c = 0; c < 4; ++c)
-            if (m[q * 4 + c].x != 0 || m[q * 4 + c].y != 0) {
-                if (pi[q] >= 0) return 0;
-                pi[q] = c;
-            }
-        if (pi[q] < 0) return 0;
-    }
-    if ((pi[0] ^ pi[1] ^ pi[2] ^ pi[3]) != 0 || pi[0] == pi[1] || pi[0] == pi[2] || pi[0] == pi[3] ||
-        pi[1] == pi[2] || pi[1] == pi[3] || pi[2] == pi[3])
-        return 0;
-    const int b = pi[0], a1 = pi[1] ^ b, a2 = pi[2] ^ b;
-    if ((a1 ^ a2) != (pi[3] ^ b)) return 0;  // not affine (never for 4 points, kept as a guard)
-    int word = -1;
-    const int tab[6][2] = {{1, 2}, {3, 2}, {1, 3}, {3, 1}, {2, 3}, {2, 1}};
-    for (int w = 0; w < 6; ++w)
-        if (tab[w][0] == a1 && tab[w][1] == a2) word = w;
-    if (word < 0) return 0;
-    int unit = 1;
-    for (int q = 0; q < 4; ++q) {
-        ph[q] = m[q * 4 + pi[q]];
-        if (ph[q].x != 1 || ph[q].y != 0) unit = 0;
-    }
-    return 1 | (unit << 1) | (b << 2) | (word << 4) | (pi[0] << 8) | (pi[1] << 10) | (pi[2] << 12) | (pi[3] << 14);
-}
 
 // a monomial 4x4 matrix (see mono_info) on a tile: out[q] = ph[q] in[pi(q)]
 template <class R>
@@ -338,64 +195,6 @@ __device__ __forceinline__ void stage_dispatch(typename Cplx<R>::T* tile, int tb
     }
 }
 
-// Per-thread accumulators live in shared memory (acc[r * blockDim + tid]):
-// float-float pairs for complex64 states, float64 for complex128.
-template <class R> struct AccSlot;
-template <> struct AccSlot<float> { using T = float2; };
-template <> struct AccSlot<double> { using T = double; };
-
-__device__ __forceinline__ void acc_add(float2* a, float x) {
-    Acc<float> t;
-    t.hi = a->x;
-    t.lo = a->y;
-    t.add(x);
-    a->x = t.hi;
-    a->y = t.lo;
-}
-__device__ __forceinline__ void acc_add(double* a, double x) { *a += x; }
-// a term far below the pair's rounding unit goes straight to the low word
-__device__ __forceinline__ void acc_add_lo(float2* a, float x) { a->y = __fadd_rn(a->y, x); }
-__device__ __forceinline__ void acc_add_lo(double* a, double x) { *a += x; }
-__device__ __forceinline__ double acc_get(float2 a) { return (double)a.x + (double)a.y; }
-__device__ __forceinline__ double acc_get(double a) { return a; }
-
-// Fixed-order combination of the 32 lanes' accumulators (result in lane 0).
-// Float-float pairs are added as pairs (Knuth's TwoSum of the high parts,
-// the low parts folded into the error, then Dekker's Fast2Sum to
-// renormalise), so complex64 reductions stay on the FP32 pipe until the
-// one conversion of the total.
-__device__ __forceinline__ double warp_combine(float2 a) {
-    float hi = a.x, lo = a.y;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float bh = __shfl_down_sync(0xffffffffu, hi, o);
-        const float bl = __shfl_down_sync(0xffffffffu, lo, o);
-        const float s = __fadd_rn(hi, bh);
-        const float bp = __fsub_rn(s, hi);
-        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(bh, bp));
-        e = __fadd_rn(e, __fadd_rn(lo, bl));
-        hi = __fadd_rn(s, e);
-        lo = __fsub_rn(e, __fsub_rn(hi, s));
-    }
-    return (double)hi + (double)lo;
-}
-__device__ __forceinline__ double warp_combine(double a) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    return a;
-}
-
-// shared-memory layout of k_pass: ring buffers | matrices | accumulators |
-// run offsets | mbarriers
-__host__ __device__ inline size_t pass_bytes_before_bars(const PassDesc& p, int threads, size_t amp) {
-    const size_t acc = p.red_kind != RED_NONE ? (size_t)p.red_R * threads * 8 : 0;
-    return (size_t)PASS_NBUF_H * ((size_t)1 << p.tb) * amp + (size_t)p.mat_elems * amp + acc +
-           ((size_t)1 << (p.tb - p.run_bits)) * 4;
-}
-
-// Kraus probabilities: quadratic forms v^dagger F_i v over groups of the
-// Kraus qubits, F_i = K_i^dagger K_i (Section III-B-2 / IV-A-4).  F holds the
-// Rn forms, then their float32 residuals (complex64: each form is hi + lo)
 template <class R, int K>
 __device__ __noinline__ void reduce_forms(const typename Cplx<R>::T* tile, int tb, const int32_t* pos, int Rn,
                                           const typename Cplx<R>::T* F, typename AccSlot<R>::T* acc) {
@@ -461,14 +260,6 @@ __device__ __noinline__ void reduce_bins(const typename Cplx<R>::T* tile, int tb
         }
         acc[r * 32 + lane] = a;
     }
-}
-
-// the weight of diagonal form f on bin r in float64: the pool's value
-// (float32 for complex64) plus its float32 residual
-template <class T>
-__device__ __forceinline__ double diag_weight(const T* W, int R, int k, int f, int r) {
-    const double w = (double)W[(f << k) + r].x;
-    return sizeof(T) == 8 ? w + (double)W[(R << k) + (f << k) + r].x : w;
 }
 
 template <class R>
@@ -785,800 +576,6 @@ __global__ void __launch_bounds__(256, 2) k_pass(DevBatch d, const __grid_consta
         }
     }
     if (warp == 0) bulk_wait_all();
-}
-
-// ---------------------------------------------------------------------------
-// k_pass_reg: register-resident variant for passes whose qubits (plus qubit
-// 0) number WP <= 4.  Each lane holds whole groups of 2^WP amplitudes (the
-// amplitudes that differ only in the pass's qubits), loads them straight
-// from HBM as 128-bit pairs (qubit 0 is group bit 0), applies every fused
-// stage in registers, accumulates the reduction in registers, and stores.
-// One warp owns a (branch, chunk) unit; a unit's partial is combined by
-// warp shuffles in a fixed order, so no block barrier is needed.
-// Stage and reduction positions are group-bit indices (0..WP-1); runtime
-// positions are mapped onto compile-time register indices by a switch.
-// ---------------------------------------------------------------------------
-template <class T, int G, int J>
-__device__ __forceinline__ void reg_apply1(T* v, const T* M) {
-#pragma unroll
-    for (int r = 0; r < G; ++r) {
-        if (r & (1 << J)) continue;
-        const int r1 = r | (1 << J);
-        const T a = v[r], b = v[r1];
-        T x, y;
-        x.x = M[0].x * a.x - M[0].y * a.y + M[1].x * b.x - M[1].y * b.y;
-        x.y = M[0].x * a.y + M[0].y * a.x + M[1].x * b.y + M[1].y * b.x;
-        y.x = M[2].x * a.x - M[2].y * a.y + M[3].x * b.x - M[3].y * b.y;
-        y.y = M[2].x * a.y + M[2].y * a.x + M[3].x * b.y + M[3].y * b.x;
-        v[r] = x;
-        v[r1] = y;
-    }
-}
-
-// 2-qubit matrix, matrix bit 0 on group bit J0, matrix bit 1 on group bit J1
-template <class T, int G, int J0, int J1>
-__device__ __forceinline__ void reg_apply2(T* v, const T* M) {
-    const T* m = M;  // shared memory, read per use (keeps registers for the group)
-#pragma unroll
-    for (int r = 0; r < G; ++r) {
-        if (r & ((1 << J0) | (1 << J1))) continue;
-        const int i[4] = {r, r | (1 << J0), r | (1 << J1), r | (1 << J0) | (1 << J1)};
-        T a[4], o[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) a[c] = v[i[c]];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            T acc;
-            acc.x = 0;
-            acc.y = 0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) cfma(acc, m[q * 4 + c], a[c]);
-            o[q] = acc;
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) v[i[c]] = o[c];
-    }
-}
-
-// structured one-qubit matrices: shape 1 diagonal, 2 anti-diagonal, +4 when
-// the two nonzero entries are real (amplitude damping terms scaled by
-// 1/sqrt(p)): a real diagonal costs two multiplies per amplitude
-template <class T, int G, int J, int SHAPE>
-__device__ __forceinline__ void reg_apply1_shape(T* v, const T* M) {
-    const T m0 = (SHAPE & 3) == 1 ? M[0] : M[1], m1 = (SHAPE & 3) == 1 ? M[3] : M[2];
-#pragma unroll
-    for (int r = 0; r < G; ++r) {
-        if (r & (1 << J)) continue;
-        const int r1 = r | (1 << J);
-        const T a = (SHAPE & 3) == 1 ? v[r] : v[r1], b = (SHAPE & 3) == 1 ? v[r1] : v[r];
-        if (SHAPE & 4) {
-            v[r].x = m0.x * a.x;
-            v[r].y = m0.x * a.y;
-            v[r1].x = m1.x * b.x;
-            v[r1].y = m1.x * b.y;
-        } else {
-            v[r] = cmul(m0, a);
-            v[r1] = cmul(m1, b);
-        }
-    }
-}
-
-template <class T, int G, int J>
-__device__ __forceinline__ void reg_apply1_shaped(T* v, const T* M, int shape) {
-    switch (shape) {
-    case 1: reg_apply1_shape<T, G, J, 1>(v, M); break;
-    case 2: reg_apply1_shape<T, G, J, 2>(v, M); break;
-    case 5: reg_apply1_shape<T, G, J, 5>(v, M); break;
-    default: reg_apply1_shape<T, G, J, 6>(v, M); break;
-    }
-}
-
-template <class T, int G>
-__device__ __forceinline__ void reg_apply1s_dyn(T* v, int j, const T* M, int shape) {
-    switch (j) {
-    case 0: reg_apply1_shaped<T, G, 0>(v, M, shape); break;
-    case 1: if constexpr (G > 2) reg_apply1_shaped<T, G, 1>(v, M, shape); break;
-    case 2: if constexpr (G > 4) reg_apply1_shaped<T, G, 2>(v, M, shape); break;
-    default: if constexpr (G > 8) reg_apply1_shaped<T, G, 3>(v, M, shape); break;
-    }
-}
-
-// complex64 2-qubit matrix with packed FMAs; MX holds every entry expanded as
-// ((re, re), (-im, im))
-template <int G, int J0, int J1>
-__device__ __forceinline__ void reg_apply2_f32x2(float2* v, const ulonglong2* MX) {
-#pragma unroll
-    for (int r = 0; r < G; ++r) {
-        if (r & ((1 << J0) | (1 << J1))) continue;
-        const int i[4] = {r, r | (1 << J0), r | (1 << J1), r | (1 << J0) | (1 << J1)};
-        unsigned long long ap[4], as[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            ap[c] = pk2(v[i[c]].x, v[i[c]].y);
-            as[c] = pk2(v[i[c]].y, v[i[c]].x);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            unsigned long long acc = 0ull;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const ulonglong2 m = MX[q * 4 + c];
-                acc = fma2(m.x, ap[c], acc);
-                acc = fma2(m.y, as[c], acc);
-            }
-            v[i[q]] = upk2(acc);
-        }
-    }
-}
-
-template <int G>
-__device__ __forceinline__ void reg_apply2x_dyn(float2* v, int j0, int j1, const ulonglong2* MX) {
-    const int code = j0 * 4 + j1;
-    switch (code) {
-    case 1: if constexpr (G > 2) reg_apply2_f32x2<G, 0, 1>(v, MX); break;
-    case 4: if constexpr (G > 2) reg_apply2_f32x2<G, 1, 0>(v, MX); break;
-    case 2: if constexpr (G > 4) reg_apply2_f32x2<G, 0, 2>(v, MX); break;
-    case 8: if constexpr (G > 4) reg_apply2_f32x2<G, 2, 0>(v, MX); break;
-    case 6: if constexpr (G > 4) reg_apply2_f32x2<G, 1, 2>(v, MX); break;
-    case 9: if constexpr (G > 4) reg_apply2_f32x2<G, 2, 1>(v, MX); break;
-    case 3: if constexpr (G > 8) reg_apply2_f32x2<G, 0, 3>(v, MX); break;
-    case 12: if constexpr (G > 8) reg_apply2_f32x2<G, 3, 0>(v, MX); break;
-    case 7: if constexpr (G > 8) reg_apply2_f32x2<G, 1, 3>(v, MX); break;
-    case 13: if constexpr (G > 8) reg_apply2_f32x2<G, 3, 1>(v, MX); break;
-    case 11: if constexpr (G > 8) reg_apply2_f32x2<G, 2, 3>(v, MX); break;
-    default: if constexpr (G > 8) reg_apply2_f32x2<G, 3, 2>(v, MX); break;
-    }
-}
-
-// A monomial 2-qubit matrix (one nonzero per row and column: CX, SWAP, CZ,
-// controlled phases, ...) is applied as a gather plus phases:
-// out[q] = M[q][pi(q)] in[pi(q)].  Every permutation pi of the 4 indices is
-// affine over GF(2), pi(q) = A q xor b, and A is a word of at most three
-// elementary maps E01: (q0, q1) -> (q0, q1 xor q0) and E10: (q0, q1) ->
-// (q0 xor q1, q1), each a swap of register pairs.  Words of A by index:
-// I, E01, E10, E01.E10, E10.E01, E01.E10.E01 (the swap of the two bits).
-template <class T, int G, int J>
-__device__ __forceinline__ void reg_flip_t(T* v) {
-#pragma unroll
-    for (int r = 0; r < G; ++r) {
-        if (r & (1 << J)) continue;
-        const T t = v[r];
-        v[r] = v[r | (1 << J)];
-        v[r | (1 << J)] = t;
-    }
-}
-
-// v[r] <-> v[r | T] for every r with bit C set and bit T clear: the gather
-// of an elementary map with control bit C and target bit T
-template <class T, int G, int C, int TB>
-__device__ __forceinline__ void reg_cswap(T* v) {
-#pragma unroll
-    for (int r = 0; r < G; ++r) {
-        if (!(r & (1 << C)) || (r & (1 << TB))) continue;
-        const T t = v[r];
-        v[r] = v[r | (1 << TB)];
-        v[r | (1 << TB)] = t;
-    }
-}
-
-// info: bit 1 unit phases, bits 2-3 b, bits 4-6 the word of A; ph[q] the
-// phase of output q (matrix bit 0 on group bit J0, bit 1 on J1)
-template <class T, int G, int J0, int J1>
-__device__ __forceinline__ void reg_mono(T* v, int info, const T* ph) {
-    const int b = (info >> 2) & 3, word = (info >> 4) & 7;
-    if (b & 1) reg_flip_t<T, G, J0>(v);
-    if (b & 2) reg_flip_t<T, G, J1>(v);
-    switch (word) {  // E01 = reg_cswap<J0, J1>, E10 = reg_cswap<J1, J0>, applied left to right
-    case 1: reg_cswap<T, G, J0, J1>(v); break;
-    case 2: reg_cswap<T, G, J1, J0>(v); break;
-    case 3: reg_cswap<T, G, J0, J1>(v); reg_cswap<T, G, J1, J0>(v); break;
-    case 4: reg_cswap<T, G, J1, J0>(v); reg_cswap<T, G, J0, J1>(v); break;
-    case 5: reg_cswap<T, G, J0, J1>(v); reg_cswap<T, G, J1, J0>(v); reg_cswap<T, G, J0, J1>(v); break;
-    default: break;
-    }
-    if (!(info & 2)) {
-#pragma unroll
-        for (int e = 0; e < G; ++e) v[e] = cmul(ph[((e >> J0) & 1) | (((e >> J1) & 1) << 1)], v[e]);
-    }
-}
-
-template <class T, int G>
-__device__ __forceinline__ void reg_mono_dyn(T* v, int j0, int j1, int info, const T* ph) {
-    switch (j0 * 4 + j1) {
-    case 1: if constexpr (G > 2) reg_mono<T, G, 0, 1>(v, info, ph); break;
-    case 4: if constexpr (G > 2) reg_mono<T, G, 1, 0>(v, info, ph); break;
-    case 2: if constexpr (G > 4) reg_mono<T, G, 0, 2>(v, info, ph); break;
-    case 8: if constexpr (G > 4) reg_mono<T, G, 2, 0>(v, info, ph); break;
-    case 6: if constexpr (G > 4) reg_mono<T, G, 1, 2>(v, info, ph); break;
-    case 9: if constexpr (G > 4) reg_mono<T, G, 2, 1>(v, info, ph); break;
-    case 3: if constexpr (G > 8) reg_mono<T, G, 0, 3>(v, info, ph); break;
-    case 12: if constexpr (G > 8) reg_mono<T, G, 3, 0>(v, info, ph); break;
-    case 7: if constexpr (G > 8) reg_mono<T, G, 1, 3>(v, info, ph); break;
-    case 13: if constexpr (G > 8) reg_mono<T, G, 3, 1>(v, info, ph); break;
-    case 11: if constexpr (G > 8) reg_mono<T, G, 2, 3>(v, info, ph); break;
-    default: if constexpr (G > 8) reg_mono<T, G, 3, 2>(v, info, ph); break;
-    }
-}
-
-template <class T, int G, int J>
-__device__ __forceinline__ void reg_flip(T* v) {
-#pragma unroll
-    for (int r = 0; r < G; ++r) {
-        if (r & (1 << J)) continue;
-        const T t = v[r];
-        v[r] = v[r | (1 << J)];
-        v[r | (1 << J)] = t;
-    }
-}
-
-template <class T, int G>
-__device__ __forceinline__ void reg_flip_dyn(T* v, int j) {
-    switch (j) {
-    case 0: reg_flip<T, G, 0>(v); break;
-    case 1: if constexpr (G > 2) reg_flip<T, G, 1>(v); break;
-    case 2: if constexpr (G > 4) reg_flip<T, G, 2>(v); break;
-    default: if constexpr (G > 8) reg_flip<T, G, 3>(v); break;
-    }
-}
-
-// v[e] <- v[e ^ x] for a group-bit mask x
-template <class T, int G>
-__device__ __forceinline__ void reg_xor_mask(T* v, int x) {
-    if (x & 1) reg_flip<T, G, 0>(v);
-    if constexpr (G > 2)
-        if (x & 2) reg_flip<T, G, 1>(v);
-    if constexpr (G > 4)
-        if (x & 4) reg_flip<T, G, 2>(v);
-    if constexpr (G > 8)
-        if (x & 8) reg_flip<T, G, 3>(v);
-}
-
-template <class T, int G>
-__device__ __forceinline__ void reg_apply1_dyn(T* v, int j, const T* M) {
-    switch (j) {
-    case 0: reg_apply1<T, G, 0>(v, M); break;
-    case 1: if constexpr (G > 2) reg_apply1<T, G, 1>(v, M); break;
-    case 2: if constexpr (G > 4) reg_apply1<T, G, 2>(v, M); break;
-    default: if constexpr (G > 8) reg_apply1<T, G, 3>(v, M); break;
-    }
-}
-
-template <class T, int G>
-__device__ __forceinline__ void reg_apply2_dyn(T* v, int j0, int j1, const T* M) {
-    const int code = j0 * 4 + j1;
-    switch (code) {
-    case 1: if constexpr (G > 2) reg_apply2<T, G, 0, 1>(v, M); break;
-    case 4: if constexpr (G > 2) reg_apply2<T, G, 1, 0>(v, M); break;
-    case 2: if constexpr (G > 4) reg_apply2<T, G, 0, 2>(v, M); break;
-    case 8: if constexpr (G > 4) reg_apply2<T, G, 2, 0>(v, M); break;
-    case 6: if constexpr (G > 4) reg_apply2<T, G, 1, 2>(v, M); break;
-    case 9: if constexpr (G > 4) reg_apply2<T, G, 2, 1>(v, M); break;
-    case 3: if constexpr (G > 8) reg_apply2<T, G, 0, 3>(v, M); break;
-    case 12: if constexpr (G > 8) reg_apply2<T, G, 3, 0>(v, M); break;
-    case 7: if constexpr (G > 8) reg_apply2<T, G, 1, 3>(v, M); break;
-    case 13: if constexpr (G > 8) reg_apply2<T, G, 3, 1>(v, M); break;
-    case 11: if constexpr (G > 8) reg_apply2<T, G, 2, 3>(v, M); break;
-    default: if constexpr (G > 8) reg_apply2<T, G, 3, 2>(v, M); break;
-    }
-}
-
-// quadratic forms of one-qubit Kraus terms over the pairs along group bit J
-template <class R, int G, int J>
-__device__ __forceinline__ void reg_forms1(const typename Cplx<R>::T* v, const typename Cplx<R>::T* F, int Rn,
-                                           Acc<R>* acc) {
-#pragma unroll
-    for (int r = 0; r < G; ++r) {
-        if (r & (1 << J)) continue;
-        const auto a = v[r], b = v[r | (1 << J)];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            if (f >= Rn) break;
-            const auto* Ff = F + 4 * f;
-            // Re(conj(a)(F00 a + F01 b) + conj(b)(F10 a + F11 b))
-            const R fa_x = Ff[0].x * a.x - Ff[0].y * a.y + Ff[1].x * b.x - Ff[1].y * b.y;
-            const R fa_y = Ff[0].x * a.y + Ff[0].y * a.x + Ff[1].x * b.y + Ff[1].y * b.x;
-            const R fb_x = Ff[2].x * a.x - Ff[2].y * a.y + Ff[3].x * b.x - Ff[3].y * b.y;
-            const R fb_y = Ff[2].x * a.y + Ff[2].y * a.x + Ff[3].x * b.y + Ff[3].y * b.x;
-            acc[f].add(a.x * fa_x + a.y * fa_y + b.x * fb_x + b.y * fb_y);
-            if constexpr (sizeof(R) == 4) {
-                // the same form with the residual coefficients: far below an
-                // ulp of the term, so it joins the accumulator's low word
-                const auto* Fl = F + 4 * (Rn + f);
-                const R la_x = Fl[0].x * a.x - Fl[0].y * a.y + Fl[1].x * b.x - Fl[1].y * b.y;
-                const R la_y = Fl[0].x * a.y + Fl[0].y * a.x + Fl[1].x * b.y + Fl[1].y * b.x;
-                const R lb_x = Fl[2].x * a.x - Fl[2].y * a.y + Fl[3].x * b.x - Fl[3].y * b.y;
-                const R lb_y = Fl[2].x * a.y + Fl[2].y * a.x + Fl[3].x * b.y + Fl[3].y * b.x;
-                acc[f].lo += a.x * la_x + a.y * la_y + b.x * lb_x + b.y * lb_y;
-            }
-        }
-    }
-}
-
-template <class R, int G>
-__device__ __forceinline__ void reg_forms1_dyn(const typename Cplx<R>::T* v, int j, const typename Cplx<R>::T* F,
-                                               int Rn, Acc<R>* acc) {
-    switch (j) {
-    case 0: reg_forms1<R, G, 0>(v, F, Rn, acc); break;
-    case 1: if constexpr (G > 2) reg_forms1<R, G, 1>(v, F, Rn, acc); break;
-    case 2: if constexpr (G > 4) reg_forms1<R, G, 2>(v, F, Rn, acc); break;
-    default: if constexpr (G > 8) reg_forms1<R, G, 3>(v, F, Rn, acc); break;
-    }
-}
-
-constexpr int REG_MAX_RED = 4;
-constexpr int REG_MAX_BINS = 16;  // measurement outcomes a register pass reduces (k <= 4)
-
-// Diagonal forms (sum_r w_f[r] |v_r|^2 over the 2^k amplitudes of the
-// reduced qubits) are linear in the 2^k bins of |v|^2, so a unit only
-// accumulates the bins: every group collects |v|^2 into the bins of the
-// reduced qubits (compile-time bin of each amplitude, float32 within the
-// group) and adds them to the float-float bin accumulators.  The weights
-// are applied once per unit, in float64 (any number of forms, weights at
-// full precision).
-template <class R, int G, int J0, int J1>
-__device__ __forceinline__ void reg_diag_bins(const typename Cplx<R>::T* v, R* q) {
-#pragma unroll
-    for (int e = 0; e < G; ++e) {
-        const int idx = ((e >> J0) & 1) | (J1 >= 0 ? ((e >> (J1 < 0 ? 0 : J1)) & 1) << 1 : 0);
-        q[idx] += v[e].x * v[e].x + v[e].y * v[e].y;
-    }
-}
-
-template <class R, int G>
-__device__ __forceinline__ void reg_diag(const typename Cplx<R>::T* v, const PassDesc& p, Acc<R>* acc) {
-    R q[4] = {0, 0, 0, 0};
-    if (p.red_k == 1) {
-        switch (p.red_pos[0]) {
-        case 0: reg_diag_bins<R, G, 0, -1>(v, q); break;
-        case 1: if constexpr (G > 2) reg_diag_bins<R, G, 1, -1>(v, q); break;
-        case 2: if constexpr (G > 4) reg_diag_bins<R, G, 2, -1>(v, q); break;
-        default: if constexpr (G > 8) reg_diag_bins<R, G, 3, -1>(v, q); break;
-        }
-    } else {
-        switch (p.red_pos[0] * 4 + p.red_pos[1]) {
-        case 1: if constexpr (G > 2) reg_diag_bins<R, G, 0, 1>(v, q); break;
-        case 4: if constexpr (G > 2) reg_diag_bins<R, G, 1, 0>(v, q); break;
-        case 2: if constexpr (G > 4) reg_diag_bins<R, G, 0, 2>(v, q); break;
-        case 8: if constexpr (G > 4) reg_diag_bins<R, G, 2, 0>(v, q); break;
-        case 6: if constexpr (G > 4) reg_diag_bins<R, G, 1, 2>(v, q); break;
-        case 9: if constexpr (G > 4) reg_diag_bins<R, G, 2, 1>(v, q); break;
-        case 3: if constexpr (G > 8) reg_diag_bins<R, G, 0, 3>(v, q); break;
-        case 12: if constexpr (G > 8) reg_diag_bins<R, G, 3, 0>(v, q); break;
-        case 7: if constexpr (G > 8) reg_diag_bins<R, G, 1, 3>(v, q); break;
-        case 13: if constexpr (G > 8) reg_diag_bins<R, G, 3, 1>(v, q); break;
-        case 11: if constexpr (G > 8) reg_diag_bins<R, G, 2, 3>(v, q); break;
-        default: if constexpr (G > 8) reg_diag_bins<R, G, 3, 2>(v, q); break;
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-        if (r < (1 << p.red_k)) acc[r].add(q[r]);
-}
-
-// CTA shape of the register path: complex64 at 128 threads and up to 96
-// registers (five CTAs, 20 warps per SM; the pass is latency-bound, so
-// resident warps matter more than a few spilled words); complex128 at 256
-// threads, where the same cap would spill kilobytes
-constexpr int REG_PREFETCH = 1;  // groups ahead of a lane's loads that go to L2
-
-template <class R> struct RegCta;
-template <> struct RegCta<float> { static constexpr int threads = 128, min_blocks = 5; };
-template <> struct RegCta<double> { static constexpr int threads = 256, min_blocks = 1; };
-
-int pass_reg_threads(int prec) { return prec ? RegCta<double>::threads : RegCta<float>::threads; }
-
-// register-kernel variants: stage by stage, folded (no reduction), and
-// stage by stage with measurement bins (complex64)
-constexpr int REG_PLAIN = 0, REG_FOLD = 1, REG_BINS = 2;
-
-template <class R, int WP, int PAIRED, int VAR>
-__global__ void __launch_bounds__(RegCta<R>::threads, RegCta<R>::min_blocks)
-    k_pass_reg(DevBatch d, const __grid_constant__ PassDesc p) {
-    constexpr bool FOLD = VAR == REG_FOLD, BINS = VAR == REG_BINS;
-    using T = typename Cplx<R>::T;
-    constexpr int G = 1 << WP;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    // shared memory, each region one slice per warp: matrices | stage
-    // choice, packed form, scale (4 x MAX_STAGES words) | complex64 only:
-    // the matrices expanded for packed FMAs | the folded matrix (G x G)
-    const int mat_stride = (p.mat_elems + 1) & ~1;
-    T* const mats_all = reinterpret_cast<T*>(smem_raw);
-    int* const words_all = reinterpret_cast<int*>(mats_all + (size_t)nwarps * mat_stride);
-    ulonglong2* const matx_all = reinterpret_cast<ulonglong2*>(words_all + (size_t)nwarps * 4 * MAX_STAGES);
-    T* mats = mats_all + (size_t)warp * mat_stride;
-    int* w_sel = words_all + (size_t)warp * 4 * MAX_STAGES;
-    int* w_packed = w_sel + MAX_STAGES;
-    double* w_scale = reinterpret_cast<double*>(w_sel + 2 * MAX_STAGES);
-    ulonglong2* matx = matx_all + (size_t)warp * mat_stride;
-    float4* fold_m = reinterpret_cast<float4*>(matx_all + (size_t)nwarps * mat_stride) + (size_t)warp * (G / 2) * G;
-    // measurement bins (RED_BINS): per warp, bin r of lane l at bins[r * 32 + l]
-    // (float-float pairs for complex64), after the folded matrices (none in
-    // a pass with a reduction) and, for complex64, the expanded matrices
-    using AS = typename AccSlot<R>::T;
-    AS* const bins_all = reinterpret_cast<AS*>(reinterpret_cast<unsigned char*>(matx_all) +
-                                               (sizeof(T) == 8 ? (size_t)nwarps * mat_stride * 16 : 0));
-    AS* bins = bins_all + (size_t)warp * REG_MAX_BINS * 32;
-    // bin of each group element: 4 bits per element
-    uint64_t binmap = 0;
-    if constexpr (BINS)
-        for (int e = 0; e < G; ++e) {
-            uint64_t bi = 0;
-            for (int j = 0; j < p.red_k; ++j) bi |= (uint64_t)((e >> p.red_pos[j]) & 1) << j;
-            binmap |= bi << (4 * e);
-        }
-    uint64_t skipmask = 0;
-    // every stage of the pass, in op order, on one group of G amplitudes
-    auto apply_stages = [&](T (&v)[G]) {
-        for (int s = 0; s < p.n_stages; ++s) {
-            if ((skipmask >> s) & 1) continue;
-            const Stage& st = p.st[s];
-            if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
-                if (st.k == 1) {
-                    const int shape = w_packed[s];
-                    if (shape) reg_apply1s_dyn<T, G>(v, st.pos[0], mats + st.mat, shape);
-                    else reg_apply1_dyn<T, G>(v, st.pos[0], mats + st.mat);
-                } else if (const int mi = w_packed[s]) {
-                    reg_mono_dyn<T, G>(v, st.pos[0], st.pos[1], mi, mats + st.mat);
-                } else {
-                    if constexpr (sizeof(T) == 8)
-                        reg_apply2x_dyn<G>(reinterpret_cast<float2*>(v), st.pos[0], st.pos[1], matx + st.mat);
-                    else
-                        reg_apply2_dyn<T, G>(v, st.pos[0], st.pos[1], mats + st.mat);
-                }
-            } else if (st.kind == ST_PAULI_BR) {
-                // out[e] = (-i)^ny (-1)^popcount(z & e) in[e ^ x]
-                const int info = w_packed[s];
-                reg_xor_mask<T, G>(v, info & 15);
-                const bool rot = (info >> 4) & 1;
-                const int sign = info >> 8;
-#pragma unroll
-                for (int e = 0; e < G; ++e) {
-                    T t = v[e];
-                    if (rot) {
-                        const R x = t.x;
-                        t.x = t.y;
-                        t.y = -x;
-                    }
-                    if ((sign >> e) & 1) {
-                        t.x = -t.x;
-                        t.y = -t.y;
-                    }
-                    v[e] = t;
-                }
-            } else {  // ST_PROJ_BR
-                const int info = w_packed[s];
-                const R sc = mats[st.mat].x;
-#pragma unroll
-                for (int e = 0; e < G; ++e) {
-                    if ((info >> e) & 1) {
-                        v[e].x *= sc;
-                        v[e].y *= sc;
-                    } else {
-                        v[e].x = 0;
-                        v[e].y = 0;
-                    }
-                }
-                reg_xor_mask<T, G>(v, (info >> 16) & 15);
-            }
-        }
-    };
-
-    const int n_br = d.ctl[CTL_NBR];
-    if (blockIdx.x == 0 && threadIdx.x == 0 && d.pass_log) {
-        const int i = atomicAdd(&d.ctl[CTL_NPASS], 1);
-        if (i < d.pass_log_cap) d.pass_log[i] = n_br;
-    }
-    // group offsets: element e of a group sits at base + off[e]
-    // element e of a group sits at base + sum of stride[j] over its set bits
-    int stride[WP];
-#pragma unroll
-    for (int j = 0; j < WP; ++j) stride[j] = 1 << p.tile_q[j];
-    const int64_t units = (int64_t)n_br * p.chunks;
-    const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, tw = (int64_t)gridDim.x * nwarps;
-    const int64_t u0 = units * gw / tw, u1 = units * (gw + 1) / tw;
-    const int64_t gpu = (d.dim >> WP) / p.chunks;  // groups per unit
-    const bool red = p.red_kind != RED_NONE;
-    T* const states = reinterpret_cast<T*>(d.states);
-    const R* pool = reinterpret_cast<const R*>(d.pool);
-    int cur_b = -1;
-    for (int64_t u = u0; u < u1; ++u) {
-        const int b = (int)(u / p.chunks);
-        const int c = (int)(u % p.chunks);
-        const int slot = d.br_slot[b];
-        if (slot < 0 || slot >= d.n_slots) {
-            if (lane == 0) set_err(d, ERR_SLOT, b);
-            continue;
-        }
-        if (b != cur_b) {
-            const uint64_t clb = d.br_clbits[b];
-            // the shared gates' matrices (and the reduction's coefficients)
-            // are loaded for the warp's first branch only; a branch's own
-            // stages (choices, parameter sets) on every branch change
-            const bool first = cur_b < 0;
-            __syncwarp();
-            // each lane takes its stages' choices: the loads of different
-            // stages overlap instead of forming one chain per stage
-            skipmask = 0;
-            for (int s0 = 0; s0 < p.n_stages; s0 += 32) {
-                const int s = s0 + lane;
-                int sk = 0;
-                if (s < p.n_stages) {
-                    const Stage& st = p.st[s];
-                    int sel = 0, packed = 0;
-                    double scale = 1.0;
-                    if (st.cond_clbit >= 0 && (int)((clb >> st.cond_clbit) & 1ull) != st.cond_val) sk = 1;
-                    if (st.kind == ST_DENSE) {
-                        // only its condition is per branch
-                    } else if (st.pre) {  // batch mode: the branch's one shot, pre-drawn
-                        sel = d.pre_sel[(int64_t)st.pend * d.cap_br + d.perm[d.br_start[b]]];
-                        packed = d.ipool[st.off + sel];
-                        if ((packed & 0xff) == 0) sk = 1;
-                    } else if (st.pend == PEND_PSET) {  // the branch's parameter set
-                        sel = d.br_pset[b];
-                    } else {
-                        sel = d.br_sel[(int64_t)st.pend * d.cap_br + b];
-                        scale = d.br_scale[(int64_t)st.pend * d.cap_br + b];
-                        if (sel < 0) sk = 1;
-                        if (st.kind == ST_PAULI_BR && !sk) {
-                            packed = d.ipool[st.off + sel];
-                            if ((packed & 0xff) == 0) sk = 1;
-                        }
-                    }
-                    // Pauli and projection stages in group form, once per
-                    // branch: Pauli: bits 0-3 flip mask, bit 4 the (-i)
-                    // factor, bits 8+ the sign of each group element;
-                    // projection: bits 0-15 the kept elements, bits 16-19 the
-                    // flips of a reset
-                    if (!sk && st.kind == ST_PAULI_BR) {
-                        const int xm = packed & 15, zm = (packed >> 4) & 15, ny = (packed >> 8) & 3;
-                        int xg = 0, zg = 0;
-                        for (int j = 0; j < st.k; ++j) {
-                            if ((xm >> j) & 1) xg |= 1 << st.pos[j];
-                            if ((zm >> j) & 1) zg |= 1 << st.pos[j];
-                        }
-                        int sign = 0;
-                        for (int e = 0; e < G; ++e)
-                            if ((((ny >> 1) & 1) ^ (__popc(zg & e) & 1)) != 0) sign |= 1 << e;
-                        w_packed[s] = xg | ((ny & 1) << 4) | (sign << 8);
-                    } else if (!sk && st.kind == ST_PROJ_BR) {
-                        int keep = 0, xr = 0;
-                        for (int e = 0; e < G; ++e) {
-                            int o = 0;
-                            for (int j = 0; j < st.k; ++j) o |= ((e >> st.pos[j]) & 1) << j;
-                            if (o == sel) keep |= 1 << e;
-                        }
-                        if (st.reset)
-                            for (int j = 0; j < st.k; ++j)
-                                if ((sel >> j) & 1) xr |= 1 << st.pos[j];
-                        w_packed[s] = keep | (xr << 16);
-                    }
-                    w_sel[s] = sel;
-                    w_scale[s] = scale;
-                }
-                skipmask |= (uint64_t)__ballot_sync(0xffffffffu, sk) << s0;
-            }
-            __syncwarp();
-            // matrices: lanes over a stage's entries
-            for (int s = 0; s < p.n_stages; ++s) {
-                const Stage& st = p.st[s];
-                if (st.kind == ST_DENSE ? !first : ((skipmask >> s) & 1)) continue;
-                if (st.kind == ST_DENSE || st.kind == ST_DENSE_BR) {
-                    const int D2 = 1 << (2 * st.k);
-                    const R* src = pool + st.off + (st.kind == ST_DENSE_BR ? (int64_t)w_sel[s] * st.stride : 0);
-                    const R sc = (R)w_scale[s];
-                    for (int e = lane; e < D2; e += 32) {
-                        T m;
-                        m.x = src[2 * e] * sc;
-                        m.y = src[2 * e + 1] * sc;
-                        mats[st.mat + e] = m;
-                        if constexpr (sizeof(T) == 8)
-                            matx[st.mat + e] = make_ulonglong2(pk2((float)m.x, (float)m.x), pk2(-(float)m.y, (float)m.y));
-                    }
-                    if (st.k == 2) {
-                        // a monomial matrix (permutation times phases) moves
-                        // registers instead of multiplying: its structure to
-                        // w_packed, its phases over the matrix's first entries
-                        __syncwarp();
-                        if (lane == 0) {
-                            T m[16], ph[4];
-                            for (int e = 0; e < 16; ++e) m[e] = mats[st.mat + e];
-                            const int mi = mono_info(m, ph);
-                            if (mi)
-                                for (int q = 0; q < 4; ++q) mats[st.mat + q] = ph[q];
-                            w_packed[s] = mi;
-                        }
-                    }
-                    if (st.k == 1 && lane == 0) {
-                        // structure of a one-qubit matrix: 1 diagonal, 2 anti-diagonal, +4 real
-                        const bool off0 = src[2] == 0 && src[3] == 0 && src[4] == 0 && src[5] == 0;
-                        const bool diag0 = src[0] == 0 && src[1] == 0 && src[6] == 0 && src[7] == 0;
-                        int shape = off0 ? 1 : (diag0 ? 2 : 0);
-                        if (shape == 1 && src[1] == 0 && src[7] == 0) shape |= 4;
-                        if (shape == 2 && src[3] == 0 && src[5] == 0) shape |= 4;
-                        w_packed[s] = shape;
-                    }
-                } else if (st.kind == ST_PROJ_BR && lane == 0) {
-                    T m;
-                    m.x = (R)w_scale[s];
-                    m.y = 0;
-                    mats[st.mat] = m;
-                }
-            }
-            if (first && (p.red_kind == RED_FORMS || p.red_kind == RED_DIAG)) {  // coefficients, then residuals
-                const int E2 = 2 * (p.red_kind == RED_FORMS ? 4 * p.red_R : p.red_R << p.red_k);
-                const R* src = pool + p.red_off;
-                for (int e = lane; e < E2; e += 32) {
-                    T m;
-                    m.x = src[2 * e];
-                    m.y = src[2 * e + 1];
-                    mats[p.mat_elems - E2 + e] = m;
-                }
-            }
-            __syncwarp();
-            if constexpr (FOLD && sizeof(T) == 8) {
-                // lane c < G runs the stages on the unit vector e_c: its
-                // result is column c of the pass's matrix for this branch
-                T col[G];
-#pragma unroll
-                for (int e = 0; e < G; ++e) {
-                    col[e].x = e == lane ? (R)1 : (R)0;
-                    col[e].y = 0;
-                }
-                apply_stages(col);
-                // rows r and r + 1 of column c side by side: one 128-bit
-                // load per column serves two output rows
-                if (lane < G)
-#pragma unroll
-                    for (int r = 0; r < G; r += 2)
-                        fold_m[(r / 2) * G + lane] = make_float4(col[r].x, col[r].y, col[r + 1].x, col[r + 1].y);
-                __syncwarp();
-            }
-            cur_b = b;
-        }
-        Acc<R> acc[REG_MAX_RED];
-#pragma unroll
-        for (int r = 0; r < REG_MAX_RED; ++r) acc[r].zero();
-        if constexpr (BINS)
-            for (int r = 0; r < (1 << p.red_k); ++r) bins[r * 32 + lane] = AS{};
-        T* gstate = states + (int64_t)slot * d.dim;
-        for (int64_t gi = lane; gi < gpu; gi += 32) {
-            // base: the group index with zeros inserted at the group qubits
-            // (32-bit: a state has at most 2^30 amplitudes)
-            auto group_base = [&](int64_t gidx) {
-                uint32_t bb = (uint32_t)gidx;
-#pragma unroll
-                for (int j = 0; j < WP; ++j) {
-                    const uint32_t lowm = (uint32_t)stride[j] - 1u;
-                    bb = ((bb & ~lowm) << 1) | (bb & lowm);
-                }
-                return bb;
-            };
-            const uint32_t base = group_base(c * gpu + gi);
-            T* g = gstate + base;
-            auto off = [&](int e) {
-                int o = 0;
-#pragma unroll
-                for (int j = 0; j < WP; ++j)
-                    if ((e >> j) & 1) o += stride[j];
-                return o;
-            };
-            // the lane's next group goes to L2 ahead of its loads (no
-            // registers held): the pass is latency-bound at 20 warps per SM
-            if (gi + 32 * REG_PREFETCH < gpu) {
-                const T* gn = gstate + group_base(c * gpu + gi + 32 * REG_PREFETCH);
-#pragma unroll
-                for (int e = 0; e < G; e += (sizeof(T) == 8 && PAIRED) ? 2 : 1)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(gn + off(e)));
-            }
-            T v[G];
-            if constexpr (sizeof(T) == 8 && PAIRED) {
-#pragma unroll
-                for (int e = 0; e < G; e += 2) {
-                    const float4 x = *reinterpret_cast<const float4*>(g + off(e));
-                    v[e].x = x.x;
-                    v[e].y = x.y;
-                    v[e + 1].x = x.z;
-                    v[e + 1].y = x.w;
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < G; ++e) v[e] = g[off(e)];
-            }
-            if constexpr (FOLD && sizeof(T) == 8) {
-                // the pass's stages folded into one G x G matrix (rows r and
-                // r + 1 of column c at fold_m[(r / 2) * G + c]); a folded pass
-                // has no reduction, so each pair of output rows is stored as
-                // soon as it is formed
-#pragma unroll 1
-                for (int r = 0; r < G; r += 2) {
-                    float2 o0 = make_float2(0.f, 0.f), o1 = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int c2 = 0; c2 < G; ++c2) {
-                        const float4 m = fold_m[(r / 2) * G + c2];
-                        const float2 a = v[c2];
-                        o0.x = fmaf(m.x, a.x, fmaf(-m.y, a.y, o0.x));
-                        o0.y = fmaf(m.x, a.y, fmaf(m.y, a.x, o0.y));
-                        o1.x = fmaf(m.z, a.x, fmaf(-m.w, a.y, o1.x));
-                        o1.y = fmaf(m.z, a.y, fmaf(m.w, a.x, o1.y));
-                    }
-                    if constexpr (PAIRED) {
-                        *reinterpret_cast<float4*>(g + off(r)) = make_float4(o0.x, o0.y, o1.x, o1.y);
-                    } else {
-                        g[off(r)] = o0;
-                        g[off(r + 1)] = o1;
-                    }
-                }
-            } else {
-                apply_stages(v);
-                if (p.red_kind == RED_FORMS)
-                    reg_forms1_dyn<R, G>(v, p.red_pos[0], mats + p.mat_elems - 8 * p.red_R, p.red_R, acc);
-                else if (p.red_kind == RED_DIAG)
-                    reg_diag<R, G>(v, p, acc);
-                if constexpr (BINS) {
-                    // each lane owns its column of the bins: no races
-#pragma unroll
-                    for (int e = 0; e < G; ++e) {
-                        const int bi = (int)((binmap >> (4 * e)) & 15);
-                        const R x = v[e].x * v[e].x + v[e].y * v[e].y;
-                        if constexpr (sizeof(R) == 4) acc_add(&bins[bi * 32 + lane], x);
-                        else bins[bi * 32 + lane] += x;
-                    }
-                }
-                if (p.store) {
-                    if constexpr (sizeof(T) == 8 && PAIRED) {
-#pragma unroll
-                        for (int e = 0; e < G; e += 2)
-                            *reinterpret_cast<float4*>(g + off(e)) = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < G; ++e) g[off(e)] = v[e];
-                    }
-                }
-            }
-        }
-        if (red && p.red_kind == RED_DIAG) {
-            // the unit's bins (fixed shuffle tree, float64), then every form
-            // from them: lane f writes form f
-            const int D = 1 << p.red_k;
-            double bin[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                double x = r < D ? acc[r].get() : 0.0;
-                if (r < D)
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                bin[r] = x;
-            }
-            if (lane < p.red_R) {
-                const T* W = mats + p.mat_elems - 2 * (p.red_R << p.red_k);
-                double part = 0.0;
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    if (r < D) part += diag_weight(W, p.red_R, p.red_k, lane, r) * bin[r];
-                d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED + lane] = part;
-            }
-        } else if (BINS) {
-            // every outcome's bin: a fixed float64 shuffle tree over the lanes
-            for (int r = 0; r < (1 << p.red_k); ++r) {
-                const AS a = bins[r * 32 + lane];
-                double x;
-                if constexpr (sizeof(R) == 4) x = (double)a.x + (double)a.y;
-                else x = a;
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-                if (lane == 0) d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED + r] = x;
-            }
-        } else if (red) {
-#pragma unroll
-            for (int r = 0; r < REG_MAX_RED; ++r) {
-                if (r >= p.red_R) break;
-                // a unit is short: a float64 shuffle tree costs less here
-                // than float-float pairs
-                double x = acc[r].get();
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-                if (lane == 0) d.partials[((int64_t)slot * d.max_chunks + c) * MAX_RED + r] = x;
-            }
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -2443,40 +1440,20 @@ cudaError_t init_kernels() {
     return e;
 }
 
-template <class R, int WP, int PAIRED, int VAR> const void* reg_fn() {
-    return (const void*)k_pass_reg<R, WP, PAIRED, VAR>;
-}
-
-template <int PAIRED, int VAR> const void* reg_fn_c64(int wp) {
-    if constexpr (VAR == REG_BINS) return reg_fn<float, 4, PAIRED, VAR>();  // bins: 4-qubit groups only
-    switch (wp) {
-    case 1: return reg_fn<float, 1, PAIRED, VAR>();
-    case 2: return reg_fn<float, 2, PAIRED, VAR>();
-    case 3: return reg_fn<float, 3, PAIRED, VAR>();
-    default: return reg_fn<float, 4, PAIRED, VAR>();
-    }
-}
+int pass_reg_threads(int prec) { return prec ? RegCta<double>::threads : RegCta<float>::threads; }
 
 int pass_reg_variant(int prec, const PassDesc& p) {
     if (prec) return REG_PLAIN;
     return p.fold ? REG_FOLD : (p.red_kind == RED_BINS ? REG_BINS : REG_PLAIN);
 }
 
+// the instantiations live in sv_reg_c64.cu, sv_reg_c64x.cu and sv_reg_c128.cu;
 // folded and measurement-bin passes exist for complex64 only
 const void* pass_reg_fn(int prec, int wp, int paired, int var) {
-    if (prec) {
-        switch (wp) {
-        case 1: return reg_fn<double, 1, 0, 0>();
-        case 2: return reg_fn<double, 2, 0, 0>();
-        case 3: return reg_fn<double, 3, 0, 0>();
-        default: return reg_fn<double, 4, 0, 0>();
-        }
-    }
-    if (paired)
-        return var == REG_FOLD ? reg_fn_c64<1, REG_FOLD>(wp)
-                               : (var == REG_BINS ? reg_fn_c64<1, REG_BINS>(wp) : reg_fn_c64<1, REG_PLAIN>(wp));
-    return var == REG_FOLD ? reg_fn_c64<0, REG_FOLD>(wp)
-                           : (var == REG_BINS ? reg_fn_c64<0, REG_BINS>(wp) : reg_fn_c64<0, REG_PLAIN>(wp));
+    if (prec) return reg_kernel_c128(wp);
+    if (var == REG_FOLD) return reg_kernel_fold_c64(wp, paired);
+    if (var == REG_BINS) return reg_kernel_bins_c64(paired);
+    return reg_kernel_plain_c64(wp, paired);
 }
 
 int pass_reg_blocks_per_sm(int prec, int wp, int paired, int var, size_t smem) {
