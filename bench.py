@@ -725,8 +725,8 @@ def main():
         line["plain_vs_batched"] = plain_vs_batched(torch, flush_buf)
     b.close()
     if rank == 0 and world == 1 and not args.no_legs and args.workload == "cfg2":
-        # the metric's other sizes: 10 qubits (shared-memory bound), 20 and 28
-        # qubits (the HBM-roofline target), each with its own clocks
+        # the metric's other sizes: 10 qubits (states in L2, passes on chip),
+        # 20 and 28 qubits (the HBM-roofline target), each with its own clocks
         legs = {"cfg1_smem": lambda: cfg1_smem(torch, flush_buf),
                 "cfg3": lambda: leg(torch, flush_buf, "cfg3", steps=2, warmup=1)[0],
                 "cfg5": lambda: leg(torch, flush_buf, "cfg5", steps=2, warmup=1)[0]}
