@@ -140,11 +140,16 @@ typedef enum {
                                and wait for a later pass (a reduction waits only for
                                what it does not commute with), so passes fill up to
                                the fusion width; 0: every pass takes the whole queue */
-    SV_OPT_FOLD = 15          /* 1 (default): a complex64 register pass with no
+    SV_OPT_FOLD = 15,         /* 1 (default): a complex64 register pass with no
                                reduction whose stages cost clearly more per group
                                of 2^w amplitudes than one 2^w x 2^w matrix
                                composes them, per branch, into that matrix and
                                applies it once; 0: stage by stage               */
+    SV_OPT_WHOLE_STATE = 16   /* 1: complex64 states of 9 or 10 qubits run their
+                               passes without a reduction as whole-state warp
+                               passes (one warp per branch, every stage in
+                               registers, any qubits); 0 (default): passes of at
+                               most the fusion width                            */
 } sv_option;
 
 /* Allocate a batch of n_shots shots of an n_qubits register.

@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsv.so")
 SOURCES = ["sv_kernels.cu", "sv_reg_c64.cu", "sv_reg_c64x.cu", "sv_reg_c128.cu", "sv_runtime.cu", "sv_noalloc.cu",
            "sv_mlp.cu", "sv_dm.cu"]
-HEADERS = ["sv_internal.h", "sv_sample.cuh", os.path.join("..", "..", "include", "sv.h"), "sv_common.cuh", "sv_pass_reg.cuh"]
+HEADERS = ["sv_internal.h", "sv_sample.cuh", os.path.join("..", "..", "include", "sv.h"), "sv_common.cuh", "sv_pass_reg.cuh", "sv_pass_whole.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -78,6 +78,7 @@ struct PassDesc {
     int32_t reg_paired;        // register path: qubit 0 is group bit 0 (128-bit pairs)
     int32_t fold;              // register path, complex64: the stages composed into one
                                // 2^reg_wp x 2^reg_wp matrix per branch, applied once per group
+    int32_t whole;             // whole-state warp pass (k_pass_whole): one warp per branch
     Stage st[MAX_STAGES];
 };
 
@@ -206,6 +207,10 @@ const void* reg_kernel_plain_c64(int wp, int paired);
 const void* reg_kernel_fold_c64(int wp, int paired);
 const void* reg_kernel_bins_c64(int paired);
 const void* reg_kernel_c128(int wp);
+// whole-state warp passes (complex64, 9 or 10 qubits, no reduction)
+size_t pass_whole_smem_bytes(const PassDesc& p);
+int pass_whole_blocks_per_sm(int n);
+cudaError_t launch_pass_whole(const DevBatch& d, const PassDesc& p, int grid, cudaStream_t s);
 int pass_reg_threads(int prec);  // CTA size of the register path
 cudaError_t init_kernels();
 // density-matrix method (sv_dm.cu): diagonal, running sums, one key per shot

@@ -152,6 +152,7 @@ struct sv_batch_s {
     // pending stages, so stages on other qubits can wait for a later pass
     bool commute = true;
     bool fold = true;  // SV_OPT_FOLD
+    bool whole = false;  // SV_OPT_WHOLE_STATE
     std::vector<Launch>* rec = nullptr;
     bool started = false;
     uint32_t last_random = 0xffffffffu;
@@ -250,6 +251,7 @@ int tile_threads(sv_batch b, const PassDesc& p) {
 
 int pass_grid(sv_batch b, const PassDesc& p) {
     if (b->grid_pass > 0) return b->grid_pass;
+    if (p.whole) return b->n_sm * pass_whole_blocks_per_sm(b->n);
     if (p.reg_wp > 0) {
         const int prec = b->prec == SV_C128;
         const size_t smem = pass_reg_smem_bytes(prec, p, pass_reg_threads(prec));
@@ -278,7 +280,9 @@ cudaError_t exec_one(sv_batch b, const Launch& L) {
     switch (L.type) {
     case L_INIT: return launch_init(b->dev, prec, L.a0, b->n_sm * 4, b->stream);
     case L_RESET: return launch_reset(b->dev, L.a0, L.a1, L.a2, b->n_sm * 2, b->stream);
-    case L_PASS: return launch_pass(b->dev, prec, L.pass, tile_threads(b, L.pass), pass_grid(b, L.pass), b->stream);
+    case L_PASS:
+        if (L.pass.whole) return launch_pass_whole(b->dev, L.pass, pass_grid(b, L.pass), b->stream);
+        return launch_pass(b->dev, prec, L.pass, tile_threads(b, L.pass), pass_grid(b, L.pass), b->stream);
     case L_DECIDE: return launch_decide(b->dev, L.dec, b->n_sm, b->stream, b->side, b->ev_fork, b->ev_join);
     case L_ALLOC: return cudaSuccess;
     case L_COPY: return launch_copy(b->dev, prec, b->n_sm * 4, b->stream);
@@ -398,6 +402,8 @@ int pool_matrix(sv_batch b, const double* m, int k, double scale = 1.0) {
 // tiles.  Measured on GB300 over 28 circuits of 6-11 qubits, width 4 took
 // 30.2 ms in batch mode against 34.7 ms for whole-state tiles.
 constexpr int DEFAULT_MAX_ACTIVE = 4;
+
+bool whole_active(sv_batch b);
 int local_pos(const int* tile_q, int tb, int q) {
     for (int i = 0; i < tb; ++i)
         if (tile_q[i] == q) return i;
@@ -517,8 +523,27 @@ sv_status emit_stages(sv_batch b, const std::vector<int>& idx, const RedSpec& re
     uint64_t act = 0;
     for (const PendStage* ps : ss) act |= stage_mask(*ps);
     for (int j = 0; j < red.k; ++j) act |= 1ull << red.q[j];
-    const int wp = reg_width(b, red, act, ss);
-    if (wp > 0) {
+    // a whole-state warp pass: no reduction, stages of at most 4 qubits
+    // (dense ones of at most 2), its matrices within 48 KB per CTA
+    bool whole = whole_active(b) && red.kind == RED_NONE && !ss.empty();
+    if (whole) {
+        int m = 0;
+        for (const PendStage* ps : ss) {
+            if (ps->k > 4 || ((ps->kind == ST_DENSE || ps->kind == ST_DENSE_BR) && ps->k > 2)) whole = false;
+            m += (ps->kind == ST_DENSE || ps->kind == ST_DENSE_BR) ? 1 << (2 * ps->k) : (ps->kind == ST_PROJ_BR ? 1 : 0);
+        }
+        PassDesc probe;
+        memset(&probe, 0, sizeof(probe));
+        probe.mat_elems = m;
+        if (pass_whole_smem_bytes(probe) > 48 * 1024) whole = false;
+    }
+    const int wp = whole ? 0 : reg_width(b, red, act, ss);
+    if (whole) {
+        // every qubit, in order: stage positions are the logical qubits
+        act = b->n >= 64 ? ~0ull : (1ull << b->n) - 1;
+        p.tb = b->n;
+        p.whole = 1;
+    } else if (wp > 0) {
         // register group: exactly the pass's qubits; with qubit 0 among them
         // complex64 amplitudes move as 128-bit pairs
         p.tb = wp;
@@ -580,8 +605,8 @@ sv_status emit_stages(sv_batch b, const std::vector<int>& idx, const RedSpec& re
         if (ps.kind == ST_DENSE || ps.kind == ST_DENSE_BR) {
             st.mat = mat;
             mat += 1 << (2 * ps.k);
-        } else if (ps.kind == ST_PROJ_BR && wp > 0) {
-            st.mat = mat;  // the register path keeps the scale here
+        } else if (ps.kind == ST_PROJ_BR && (wp > 0 || p.whole)) {
+            st.mat = mat;  // the register and whole-state paths keep the scale here
             mat += 1;
         }
     }
@@ -779,8 +804,13 @@ int alloc_col(sv_batch b) {
     return -1;
 }
 
-// qubits of a pass fit one tile (which always holds qubit 0)
+// whole-state warp passes apply (complex64 states of 9 or 10 qubits)
+bool whole_active(sv_batch b) { return b->whole && b->prec == SV_C64 && (b->n == 9 || b->n == 10); }
+
+// qubits of a pass fit one tile (which always holds qubit 0); with
+// whole-state passes a pass may take every qubit
 bool fits(sv_batch b, uint64_t act) {
+    if (whole_active(b)) return true;
     return __builtin_popcountll(act | 1ull) <= b->tb && __builtin_popcountll(act) <= b->max_active;
 }
 
@@ -1873,6 +1903,7 @@ static sv_status set_option(sv_batch b, sv_option opt, int64_t v) {
     case SV_OPT_PREDRAW_PAULI: b->predraw = v != 0; return SV_OK;
     case SV_OPT_COMMUTE: b->commute = v != 0; return SV_OK;
     case SV_OPT_FOLD: b->fold = v != 0; return SV_OK;
+    case SV_OPT_WHOLE_STATE: b->whole = v != 0; return SV_OK;
     case SV_OPT_SLOT_LIMIT:
         if (v < 0) return fail(SV_EINVAL, "slot limit must be >= 0");
         if (v && b->branch && v < b->n_psets) return fail(SV_EINVAL, "fewer slots than parameter sets");

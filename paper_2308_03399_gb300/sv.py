@@ -20,7 +20,8 @@ SV_PLAIN, SV_BATCH, SV_BRANCH, SV_BATCH_BRANCH = 0, 1, 2, 3
 SV_NOISE_PAULI, SV_NOISE_KRAUS = 0, 1
 (SV_OPT_LOG, SV_OPT_TILE_BITS, SV_OPT_MAX_ACTIVE, SV_OPT_MAX_STAGES, SV_OPT_THREADS, SV_OPT_GRID,
  SV_OPT_PROFILE, SV_OPT_SLOT_LIMIT, SV_OPT_UPLOAD, SV_OPT_PASS_PATH, SV_OPT_JOINT_KRAUS,
- SV_OPT_SHOT_BASE, SV_OPT_CHAIN_DECIDES, SV_OPT_PREDRAW_PAULI, SV_OPT_COMMUTE, SV_OPT_FOLD) = range(16)
+ SV_OPT_SHOT_BASE, SV_OPT_CHAIN_DECIDES, SV_OPT_PREDRAW_PAULI, SV_OPT_COMMUTE, SV_OPT_FOLD,
+ SV_OPT_WHOLE_STATE) = range(17)
 SV_TREE_WORDS = 9
 PROFILE_CLASSES = ("pass", "decide", "alloc", "copy", "final", "init", "other", "total")
 

@@ -581,3 +581,23 @@ def test_small_tile_ctas_match_oracle(name, threads):
     c = SMALL[name]()
     gpu = run_gpu(c, 12, 200, sv.SV_BATCH, sv.SV_C64, opts={sv.SV_OPT_THREADS: threads}, want_amps=[0, 199])
     compare_shots(c, 12, gpu, range(200), sv.SV_C64)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("case", ["brick9", "brick10", "qft10", "mid10"])
+def test_whole_state_passes_match_oracle(case, mode):
+    # SV_OPT_WHOLE_STATE: complex64 states of 9 or 10 qubits held by one
+    # warp; passes without a reduction take any qubits (bits exchanged
+    # between registers and lanes), passes with one keep the other paths
+    c = {"brick9": lambda: W.brickwork(9, 8, 0.02, 0.05, seed=141),
+         "brick10": lambda: W.brickwork(10, 8, 0.02, 0.05, seed=142),
+         "qft10": lambda: W.qft(10, 0.02, seed=143),
+         "mid10": lambda: W.midcircuit_measure(10, 3, 0.02, [0, 7], seed=144)}[case]()
+    amps = [0, 99, 199]
+    a = run_gpu(c, 8, 200, mode, sv.SV_C64, opts={sv.SV_OPT_WHOLE_STATE: 1}, want_amps=amps)
+    b = run_gpu(c, 8, 200, mode, sv.SV_C64, want_amps=amps)
+    if case.startswith("brick"):
+        assert a["stats"]["passes"] < b["stats"]["passes"]
+    compare_shots(c, 8, a, range(200), sv.SV_C64)
+    for s in amps:
+        np.testing.assert_allclose(a["amps"][s], b["amps"][s], atol=2e-6)
