@@ -566,6 +566,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the config-1 plain-vs-batched comparison")
     ap.add_argument("--max-active", type=int, default=0, help="fusion width (qubits per pass), 0 = library default")
     ap.add_argument("--threads", type=int, default=0, help="threads per tile-pass CTA, 0 = library default")
+    ap.add_argument("--whole-state", action="store_true", help="whole-state warp passes (9 or 10 qubits, complex64)")
     ap.add_argument("--autotune", action="store_true", help="config 4: also run the autotuner's picks")
     ap.add_argument("--compare", action="store_true", help="config 4: also run the fixed policies")
     ap.add_argument("--no-legs", action="store_true", help="skip the config 1 / 3 / 5 legs of the default run")
@@ -614,6 +615,8 @@ def main():
         b.set_option(sv.SV_OPT_MAX_ACTIVE, args.max_active)
     if args.threads:
         b.set_option(sv.SV_OPT_THREADS, args.threads)
+    if args.whole_state:
+        b.set_option(sv.SV_OPT_WHOLE_STATE, 1)
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):
