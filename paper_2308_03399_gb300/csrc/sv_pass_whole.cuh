@@ -153,9 +153,6 @@ __device__ __forceinline__ void ws_restore(float2* v, WsPerm& P, int n, int lane
     }
 }
 
-}  // namespace sv
-
-namespace sv {
 
 // one stage on a 16-amplitude register group with explicit positions (< 4);
 // Pauli and projection masks are formed here from the raw choice
@@ -219,9 +216,6 @@ __device__ __forceinline__ void ws_apply_one(T* v, const Stage& st, const int* p
     }
 }
 
-}  // namespace sv
-
-namespace sv {
 
 // k_pass_whole: a pass over a whole n-qubit state (n = NREG + 5) held by one
 // warp; no reduction.  Shared memory as k_pass_reg (matrices, stage words,
