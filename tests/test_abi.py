@@ -33,3 +33,18 @@ def test_no_cpu_fallback_in_the_binding():
     # the binding loads libsv and nothing else: no import of the oracle
     src = open(os.path.join(ROOT, "paper_2308_03399_gb300", "sv.py")).read()
     assert "oracle" not in src.replace("no import of the oracle", "")
+
+
+def test_binding_constants_match_the_header():
+    # every enum value the header defines has the same value in the binding
+    import re
+
+    from paper_2308_03399_gb300 import sv
+    header = open(os.path.join(ROOT, "include", "sv.h")).read()
+    pairs = re.findall(r"\b(SV_(?:OPT|OP|C64|C128|PLAIN|BATCH|BRANCH|BATCH_BRANCH|NOISE)\w*)\s*=\s*(\d+)", header)
+    assert len(pairs) >= 20
+    for name, value in pairs:
+        if hasattr(sv, name):
+            assert getattr(sv, name) == int(value), name
+    opts = [n for n, _ in pairs if n.startswith("SV_OPT_")]
+    assert all(hasattr(sv, n) for n in opts), [n for n in opts if not hasattr(sv, n)]
