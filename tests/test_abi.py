@@ -48,3 +48,12 @@ def test_binding_constants_match_the_header():
             assert getattr(sv, name) == int(value), name
     opts = [n for n, _ in pairs if n.startswith("SV_OPT_")]
     assert all(hasattr(sv, n) for n in opts), [n for n in opts if not hasattr(sv, n)]
+
+
+def test_op_kinds_match_the_header():
+    # the circuit writer's op kinds are the header's SV_OP_* codes
+    from paper_2308_03399_gb300 import workloads as W
+    header = open(os.path.join(ROOT, "include", "sv.h")).read()
+    codes = dict((n, int(v)) for n, v in re.findall(r"\bSV_OP_(\w+)\s*=\s*(\d+)", header))
+    assert codes == {"GATE": W.GATE, "PAULI": W.PAULI, "KRAUS": W.KRAUS, "MEASURE": W.MEASURE, "FINAL": W.FINAL,
+                     "PGATE": W.PGATE}
